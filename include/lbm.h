@@ -1,0 +1,199 @@
+/*
+ * lbm.h -- C ABI of the GB300 enthalpy-based MRT lattice Boltzmann solver for
+ * solid-liquid phase change in metal foams under local thermal
+ * non-equilibrium (Liu, He & Li, arXiv 1701.00702).
+ *
+ * One call advances a run by whole time steps of the paper's fused
+ * three-lattice update (Sec. III): a D2Q9 MRT flow lattice under the
+ * generalized non-Darcy model (Eqs. 1-4, 12-27) with the volumetric solid
+ * scheme (Eq. 20), and two MRT thermal lattices (D2Q5 of App. B by default,
+ * or the D2Q9 of Sec. III B) for the PCM enthalpy (Eqs. 28-40) and the metal
+ * foam internal energy (Eqs. 41-49), coupled by interstitial heat exchange
+ * with its time-derivative correction (Eqs. 36, 47, Remark III).  The liquid
+ * fraction follows from the enthalpy without iteration (Eqs. 37-39).  Walls
+ * use non-equilibrium extrapolation (Eq. 52).
+ *
+ * Conventions shared by every entry point
+ *  - Lattice units: delta_x = delta_t = c = 1, rho_l = 1, c_pl = c_ps = c_pm = 1
+ *    (Sec. IV).  Grid nodes are (x, y), 0 <= x < nx, 0 <= y < ny; gravity
+ *    points along -y.
+ *  - Array layout at the boundary: every field is row-major [ny][nx] (x fastest);
+ *    distribution arrays are [q][ny][nx] with the velocity order of Eq. 11
+ *    (D2Q9: rest, +x, +y, -x, -y, (+,+), (-,+), (-,-), (+,-); D2Q5: the first
+ *    five).  Element type is double for LBM_F64 runs and float for LBM_F32 runs.
+ *  - Status: every int-returning call returns LBM_OK (0) or a negative
+ *    LBM_ERR_* code.  lbm_strerror() names it.  No call aborts the process.
+ *  - Streams: work is enqueued on the cudaStream_t given at creation; calls
+ *    that hand results to the host synchronise that stream first.
+ *  - Threads: one handle must not be used from two threads at once; separate
+ *    handles are independent.
+ */
+#ifndef PAPER_1701_00702_LBM_H
+#define PAPER_1701_00702_LBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---- */
+#define LBM_OK             0
+#define LBM_ERR_ARG       (-1)  /* bad argument: grid, porosity, null pointer, mask ... */
+#define LBM_ERR_STABILITY (-2)  /* a derived relaxation rate or exchange rate is outside its stable range */
+#define LBM_ERR_OOM       (-3)  /* device allocation failed */
+#define LBM_ERR_CUDA      (-4)  /* a CUDA runtime call failed */
+#define LBM_ERR_UNSTABLE  (-5)  /* the kernel saw a non-finite state or |u| > 0.3 (sticky) */
+#define LBM_ERR_TIMEOUT   (-6)  /* a bounded device wait expired */
+#define LBM_ERR_STATE     (-7)  /* handle already failed, or call out of order */
+
+/* ---- storage precision (lbm_params.precision) ---- */
+#define LBM_F64 0
+#define LBM_F32 1
+
+/* ---- wall kinds (lbm_params.wall_kind[side]) ---- */
+#define LBM_WALL_DIRICHLET 0    /* T_f = T_m = wall_T[side] on the wall nodes */
+#define LBM_WALL_ADIABATIC 1    /* T copied from the inward neighbour (zero normal gradient) */
+
+/* sides, index of wall_kind / wall_T */
+#define LBM_SIDE_LEFT   0       /* x = 0      */
+#define LBM_SIDE_RIGHT  1       /* x = nx - 1 */
+#define LBM_SIDE_BOTTOM 2       /* y = 0      */
+#define LBM_SIDE_TOP    3       /* y = ny - 1 */
+
+/* ---- field selection for lbm_fields (bit i selects dst[i]) ---- */
+#define LBM_FIELD_T_F  (1 << 0)  /* PCM temperature T_f, Eq. 38 */
+#define LBM_FIELD_T_S  (1 << 1)  /* metal-foam temperature T_m, Eq. 48 */
+#define LBM_FIELD_F_L  (1 << 2)  /* liquid fraction f_l, Eq. 39 */
+#define LBM_FIELD_U_X  (1 << 3)  /* velocity, Eq. 23 (0 on wall nodes) */
+#define LBM_FIELD_U_Y  (1 << 4)
+#define LBM_FIELD_RHO  (1 << 5)  /* density, Eq. 21 (1 when the flow lattice is off) */
+#define LBM_FIELD_H_F  (1 << 6)  /* PCM enthalpy, Eq. 37 */
+#define LBM_NUM_FIELDS 7
+
+/*
+ * Run description.  The non-dimensional groups are those of Eq. 54; their
+ * map to lattice units (ν_f = Pr k_f, gβ = Ra ν_f k_f /(ΔT L³), K = Da L²,
+ * k_m = λ k_f, ρ_m = σ̂, L_a = ΔT/Ste, h_v = Nu_i k_f / d_p², d_p = (d_p/L) L,
+ * α_f,ref = k_f / c_f,ref, α_m,ref = k_m /(ρ_m c_m,ref)) and the relaxation
+ * rates of Sec. III C and App. B are computed by lbm_derive().
+ */
+typedef struct lbm_params {
+    int32_t nx, ny;            /* grid nodes; >= 3 in a direction that has walls */
+    int32_t thermal_q;         /* 5 (App. B) or 9 (Sec. III B) */
+    int32_t precision;         /* LBM_F64 or LBM_F32 */
+    int32_t flow;              /* 1: flow lattice on; 0: u = 0 everywhere (Sec. IV A) */
+    int32_t periodic_x;        /* 1: periodic in x; 0: wall nodes at x = 0 and x = nx-1 */
+    int32_t periodic_y;        /* 1: periodic in y; 0: wall nodes at y = 0 and y = ny-1 */
+    int32_t wall_kind[4];      /* LBM_WALL_* per side (ignored on periodic sides) */
+    double  wall_T[4];         /* Dirichlet wall temperatures per side */
+    double  porosity;          /* φ, in (0, 1) */
+    double  Ra, Pr, Da;        /* Rayleigh, Prandtl, Darcy numbers (Eq. 54) */
+    double  Ste;               /* Stefan number St = c_pl ΔT / L_a */
+    double  cond_ratio;        /* λ = k_m / k_f */
+    double  Nu_i;              /* interstitial number H_v = h_v d_p² / k_f */
+    double  J;                 /* ν_e / ν_f (paper: 1) */
+    double  F_phi;             /* Forchheimer coefficient (paper: 0.068) */
+    double  sigma_hat;         /* (ρc_p)_m / (ρc_p)_f (paper: 1) */
+    double  dp_over_L;         /* pore size d_p / L (paper: 0.0135) */
+    double  k_f;               /* PCM conductivity in lattice units (= α_f) */
+    double  cfref_over_cpl;    /* c_f,ref / c_pl */
+    double  cmref_over_cpm;    /* c_m,ref / c_pm */
+    double  T_hot, T_cold;     /* ΔT = T_hot - T_cold (enters Ra and Ste) */
+    double  T_init;            /* uniform initial temperature of both phases */
+    double  T_ref0;            /* Boussinesq reference T_0 (Eq. 7) */
+    double  T_solidus, T_liquidus;  /* T_fs <= T_fl (Eqs. 38-39) */
+    double  L_char;            /* characteristic length L in lattice units */
+    double  varpi;             /* ϖ of App. B, in (0, 1); used when thermal_q = 5 */
+} lbm_params;
+
+/* Lattice-unit constants derived from lbm_params (output of lbm_derive). */
+typedef struct lbm_derived {
+    double nu_f, nu_e, gbeta, K, k_m, rho_m, L_a, d_p, h_v;
+    double alpha_f, alpha_fref, alpha_mref, c_fref, c_mref, csT2;
+    double H_fs, H_fl;         /* enthalpies at solidus and liquidus, Eqs. 38-39 */
+    double l0, l1;             /* Eq. 25 */
+    double exchange_rate;      /* h_v [1/(φ ρ_l) + 1/((1-φ) ρ_m)], must be < 1 */
+    double s[9];               /* flow relaxation rates, Eq. 16 / Sec. III C */
+    double zeta[9];            /* PCM rates Θ (first thermal_q entries) */
+    double eta[9];             /* metal rates Q (first thermal_q entries) */
+    double H_wall[4];          /* enthalpy of each Dirichlet wall, inverse of Eq. 38 */
+} lbm_derived;
+
+typedef struct lbm_handle lbm_handle;
+
+/* Allocation hooks: alloc returns 256-byte aligned device memory or NULL. */
+typedef void* (*lbm_alloc_fn)(size_t bytes, void* ctx);
+typedef void  (*lbm_free_fn)(void* ptr, void* ctx);
+
+/* Fills p with the Sec. IV B square-cavity set-up on 150 x 150 (Ra = 1e6,
+ * φ = 0.8, λ = 1e3, D2Q5 thermal lattices, FP32 storage).  Never fails. */
+void lbm_params_default(lbm_params* p);
+
+/* Validates p and computes the lattice constants (host only, no GPU needed).
+ * Returns LBM_ERR_ARG for malformed input and LBM_ERR_STABILITY when a
+ * relaxation rate leaves (0, 2), c_ref breaks Remark I (c_f,ref < 9/5 c_pf for
+ * D2Q9, ϖ c_f,ref < c_pf for D2Q5; same for the metal) or the explicit
+ * exchange rate reaches 1.  d may be NULL. */
+int lbm_derive(const lbm_params* p, lbm_derived* d);
+
+/* Device bytes a run will hold (two copies of the distributions, the exchange
+ * history and small scratch).  -1 if p is invalid. */
+int64_t lbm_state_bytes(const lbm_params* p);
+
+/* Creates a run, allocates its device state (through alloc/release when
+ * given, else the CUDA stream-ordered allocator) and enqueues the uniform
+ * initial state f = f^eq(1, 0), g = g^eq(H(T_init), T_init, 0),
+ * h = h^eq(T_init) on cuda_stream (a cudaStream_t; NULL = legacy default
+ * stream).  On failure *out is NULL and nothing stays allocated. */
+int lbm_create(const lbm_params* p, void* cuda_stream, lbm_handle** out);
+int lbm_create_ex(const lbm_params* p, void* cuda_stream, lbm_alloc_fn alloc,
+                  lbm_free_fn release, void* ctx, lbm_handle** out);
+
+/* Enqueues nsteps >= 0 time steps (Sec. III: stream, walls, enthalpy, blend,
+ * velocity, three collisions).  Asynchronous: returns the sticky status known
+ * on the host (LBM_ERR_UNSTABLE after any synchronising call saw the device
+ * flag).  Large nsteps are replayed from a captured CUDA graph. */
+int lbm_step(lbm_handle* h, int64_t nsteps);
+
+/* Macroscopic fields at the current time level.  dst[i] receives field i of
+ * LBM_FIELD_* when bit i of mask is set (nx*ny elements of the run's type,
+ * [ny][nx]); dst_on_device selects device or host pointers.  Synchronises. */
+int lbm_fields(lbm_handle* h, int32_t mask, void* const* dst, int32_t dst_on_device);
+
+/* FP64 reductions at the current time level: melt fraction (mean f_l over all
+ * nodes, Fig. 9), hot-wall Nusselt number (left-wall heat flux of both phases
+ * by a second-order one-sided difference, times L/(k_e ΔT), k_e = φk_f+(1-φ)k_m),
+ * total enthalpy Σ[φ ρ_l H_f + (1-φ) ρ_m c_pm T_m] and mass Σρ.  Any pointer
+ * may be NULL.  Synchronises.  The reduction order is fixed, so equal states
+ * give bit-equal results. */
+int lbm_diag(lbm_handle* h, double* melt_frac, double* nu_hot, double* enthalpy, double* mass);
+
+/* Copies the raw state out or in: f (9 planes; ignored when flow = 0), g and
+ * hm (thermal_q planes each) hold the post-collision populations of the last
+ * step, dT ([ny][nx]) the exchange history T_m - T_f of the last step.
+ * on_device selects device or host pointers.  Synchronises. */
+int lbm_get_state(lbm_handle* h, void* f, void* g, void* hm, void* dT, int32_t on_device);
+int lbm_set_state(lbm_handle* h, const void* f, const void* g, const void* hm, const void* dT,
+                  int32_t on_device);
+
+/* Synchronises the handle's stream and returns the sticky status. */
+int lbm_status(lbm_handle* h);
+
+/* Time steps taken so far. */
+int64_t lbm_steps_done(const lbm_handle* h);
+
+/* Copies the run's parameters and derived constants (either may be NULL). */
+int lbm_describe(const lbm_handle* h, lbm_params* p, lbm_derived* d);
+
+/* Synchronises, frees everything the handle owns.  NULL is a no-op. */
+int lbm_destroy(lbm_handle* h);
+
+/* Static string naming a status code. */
+const char* lbm_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PAPER_1701_00702_LBM_H */

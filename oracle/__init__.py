@@ -92,6 +92,8 @@ def lib():
             getattr(L, name).argtypes = [cp, ctypes.c_double]
             getattr(L, name).restype = ctypes.c_double
         L.orc_velocity.argtypes = [cp] + [ctypes.c_double] * 4 + [dp]
+        ip = np.ctypeslib.ndpointer(dtype=np.int32, flags="C_CONTIGUOUS")
+        L.orc_step_nodes.argtypes = [cp, dp, dp, dp, dp, ip, ip, ctypes.c_int, dp, dp, dp, dp]
         L.orc_set_threads.argtypes = [ctypes.c_int]
         L.orc_threads.restype = ctypes.c_int
         _lib = L
@@ -217,6 +219,20 @@ class Oracle:
             self.cur = b
             self.steps += 1
         return self
+
+    def step_nodes(self, xs, ys):
+        """Post-collision values of one step at the listed nodes only (state unchanged).
+        Returns (f [n,9] or None, g [n,qt], h [n,qt], dT [n])."""
+        xs = np.ascontiguousarray(xs, dtype=np.int32)
+        ys = np.ascontiguousarray(ys, dtype=np.int32)
+        n, qt = xs.size, self.lc["qt"]
+        fo, go, ho, dTo = np.zeros((n, 9)), np.zeros((n, qt)), np.zeros((n, qt)), np.zeros(n)
+        c = self.cur
+        rc = self._L.orc_step_nodes(ctypes.byref(self.cfg), self.F[c], self.G[c], self.H[c], self.dT,
+                                    xs, ys, n, fo, go, ho, dTo)
+        if rc != 0:
+            raise RuntimeError("oracle step_nodes failed")
+        return (fo if self.lc["flow"] else None), go, ho, dTo
 
     def fields(self) -> dict:
         nx, ny = self.lc["nx"], self.lc["ny"]

@@ -588,3 +588,25 @@ double orc_H_of_T(const orc_cfg* c, double T) { return H_of_T(c, T); }
 void orc_velocity(const orc_cfg* c, double rho, double jx, double jy, double Gy, double* u) {
     velocity(c, rho, jx, jy, Gy, &u[0], &u[1]);
 }
+
+/* One time step evaluated only at the listed nodes (for sampled checks of
+ * large grids): outputs are [n][9] (flow), [n][qt] (PCM, metal) and [n]. */
+int orc_step_nodes(const orc_cfg* c, const double* F, const double* G, const double* Hh,
+                   const double* dT, const int* xs, const int* ys, int n,
+                   double* fo, double* go, double* ho, double* dTo) {
+    tables t;
+    if (orc_check(c) || make_tables(&t)) return -1;
+    #pragma omp parallel for schedule(static)
+    for (int k = 0; k < n; ++k) {
+        int x = xs[k], y = ys[k];
+        if (x < 0 || x >= c->nx || y < 0 || y >= c->ny) continue;
+        node nd;
+        double fs[9], gs[9], hs[9], dTn;
+        node_state(c, &t, F, G, Hh, x, y, &nd);
+        collide(c, &t, &nd, dT[(size_t)y * c->nx + x], fs, gs, hs, &dTn);
+        if (c->flow) for (int i = 0; i < 9; ++i) fo[(size_t)k * 9 + i] = fs[i];
+        for (int i = 0; i < c->qt; ++i) { go[(size_t)k * c->qt + i] = gs[i]; ho[(size_t)k * c->qt + i] = hs[i]; }
+        dTo[k] = dTn;
+    }
+    return 0;
+}

@@ -1,0 +1,606 @@
+// Host runtime behind the C ABI of include/lbm.h: parameter map and checks,
+// device state, graph-replayed stepping, fields, diagnostics, state I/O.
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <new>
+
+#include "lbm.h"
+#include "lbm_launch.cuh"
+
+namespace {
+
+constexpr int kGraphSteps = 64;          // steps per captured graph (even: the graph starts and ends on buffer 0)
+constexpr size_t kAlign = 256;
+
+size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+
+bool finite(double v) { return std::isfinite(v); }
+
+// Inverse of Eq. 38: T <= T_fs is solid, T >= T_fl (above T_fs) liquid, else mushy.
+double enthalpy_of_T(const lbm_params& p, double L_a, double T) {
+    const double c_ps = 1.0, c_pl = 1.0;
+    const double Hfs = c_ps * p.T_solidus, Hfl = c_pl * p.T_liquidus + L_a;
+    if (T <= p.T_solidus) return c_ps * T;
+    if (T >= p.T_liquidus) return Hfl + c_pl * (T - p.T_liquidus);
+    return Hfs + (T - p.T_solidus) / (p.T_liquidus - p.T_solidus) * (Hfl - Hfs);
+}
+
+int derive_impl(const lbm_params* pp, lbm_derived* out) {
+    if (!pp) return LBM_ERR_ARG;
+    const lbm_params& p = *pp;
+    if (p.nx < 1 || p.ny < 1 || p.nx > 65536 || p.ny > 65536) return LBM_ERR_ARG;
+    if ((int64_t)p.nx * p.ny > (int64_t(1) << 30)) return LBM_ERR_ARG;
+    if ((p.periodic_x != 0 && p.periodic_x != 1) || (p.periodic_y != 0 && p.periodic_y != 1)) return LBM_ERR_ARG;
+    if (!p.periodic_x && p.nx < 3) return LBM_ERR_ARG;
+    if (!p.periodic_y && p.ny < 3) return LBM_ERR_ARG;
+    if (p.thermal_q != 5 && p.thermal_q != 9) return LBM_ERR_ARG;
+    if (p.precision != LBM_F64 && p.precision != LBM_F32) return LBM_ERR_ARG;
+    if (p.flow != 0 && p.flow != 1) return LBM_ERR_ARG;
+    for (int s = 0; s < 4; ++s) {
+        if (p.wall_kind[s] != LBM_WALL_DIRICHLET && p.wall_kind[s] != LBM_WALL_ADIABATIC) return LBM_ERR_ARG;
+        if (!finite(p.wall_T[s])) return LBM_ERR_ARG;
+    }
+    const double vals[] = {p.porosity, p.Ste, p.cond_ratio, p.Nu_i, p.sigma_hat, p.dp_over_L, p.k_f,
+                           p.cfref_over_cpl, p.cmref_over_cpm, p.T_hot, p.T_cold, p.T_init, p.T_ref0,
+                           p.T_solidus, p.T_liquidus, p.L_char};
+    for (double v : vals)
+        if (!finite(v)) return LBM_ERR_ARG;
+    if (!(p.porosity > 0.0 && p.porosity < 1.0)) return LBM_ERR_ARG;
+    if (!(p.Ste > 0.0) || !(p.k_f > 0.0) || !(p.L_char > 0.0) || !(p.dp_over_L > 0.0)) return LBM_ERR_ARG;
+    if (!(p.cfref_over_cpl > 0.0) || !(p.cmref_over_cpm > 0.0) || !(p.sigma_hat > 0.0)) return LBM_ERR_ARG;
+    if (!(p.cond_ratio > 0.0) || !(p.Nu_i >= 0.0)) return LBM_ERR_ARG;
+    if (!(p.T_liquidus >= p.T_solidus) || p.T_hot == p.T_cold) return LBM_ERR_ARG;
+    if (p.thermal_q == 5 && !(p.varpi > 0.0 && p.varpi < 1.0)) return LBM_ERR_ARG;
+    if (p.flow) {
+        const double fv[] = {p.Ra, p.Pr, p.Da, p.J, p.F_phi};
+        for (double v : fv)
+            if (!finite(v)) return LBM_ERR_ARG;
+        if (!(p.Pr > 0.0) || !(p.Da > 0.0) || !(p.J > 0.0) || !(p.F_phi >= 0.0) || !(p.Ra >= 0.0)) return LBM_ERR_ARG;
+    }
+
+    // Eq. 54 with delta_x = delta_t = c = 1, rho_l = 1, c_pl = c_ps = c_pm = 1.
+    lbm_derived d;
+    std::memset(&d, 0, sizeof d);
+    const double rho_l = 1.0, c_pl = 1.0, c_pm = 1.0;
+    const double L = p.L_char, dT = p.T_hot - p.T_cold, phi = p.porosity;
+    d.alpha_f = p.k_f / (rho_l * c_pl);
+    d.nu_f = p.flow ? p.Pr * d.alpha_f : 0.0;
+    d.nu_e = p.flow ? p.J * d.nu_f : 0.0;
+    d.gbeta = p.flow ? p.Ra * d.nu_f * d.alpha_f / (dT * L * L * L) : 0.0;
+    d.K = p.flow ? p.Da * L * L : 0.0;
+    d.k_m = p.cond_ratio * p.k_f;
+    d.rho_m = p.sigma_hat * rho_l * c_pl / c_pm;
+    d.L_a = c_pl * dT / p.Ste;
+    if (!(d.L_a > 0.0)) return LBM_ERR_ARG;   // needs T_hot > T_cold
+    d.d_p = p.dp_over_L * L;
+    d.h_v = p.Nu_i * p.k_f / (d.d_p * d.d_p);
+    d.c_fref = p.cfref_over_cpl * c_pl;
+    d.c_mref = p.cmref_over_cpm * c_pm;
+    d.alpha_fref = p.k_f / (rho_l * d.c_fref);
+    d.alpha_mref = d.k_m / (d.rho_m * d.c_mref);
+    const double cs2 = 1.0 / 3.0;
+    d.csT2 = p.thermal_q == 9 ? cs2 : 0.5 * p.varpi;
+    d.H_fs = 1.0 * p.T_solidus;
+    d.H_fl = c_pl * p.T_liquidus + d.L_a;
+    d.exchange_rate = d.h_v * (1.0 / (phi * rho_l) + 1.0 / ((1.0 - phi) * d.rho_m));
+
+    const double s_v = p.flow ? 1.0 / (0.5 + d.nu_e / cs2) : 1.0;
+    const double za = 1.0 / (0.5 + d.alpha_fref / d.csT2);
+    const double ea = 1.0 / (0.5 + d.alpha_mref / d.csT2);
+    const double ze = 2.0 - za;                        // Eq. 53
+    const double s9[9] = {1.0, 1.1, 1.1, 1.0, 1.2, 1.0, 1.2, s_v, s_v};
+    std::memcpy(d.s, s9, sizeof s9);
+    if (p.thermal_q == 9) {
+        const double z9[9] = {1.0, ze, ze, za, za, za, za, 1.2, 1.2};
+        const double e9[9] = {1.0, 1.1, 1.1, ea, ea, ea, ea, 1.2, 1.2};
+        std::memcpy(d.zeta, z9, sizeof z9);
+        std::memcpy(d.eta, e9, sizeof e9);
+    } else {
+        const double z5[5] = {1.0, za, za, ze, 1.2};   // App. B: Theta = diag(z0, za, za, ze, z_eps)
+        const double e5[5] = {1.0, ea, ea, 1.1, 1.2};
+        std::memcpy(d.zeta, z5, sizeof z5);
+        std::memcpy(d.eta, e5, sizeof e5);
+    }
+    if (p.flow) {
+        d.l0 = 0.5 * (1.0 + phi * 0.5 * d.nu_f / d.K);  // Eq. 25
+        d.l1 = phi * 0.5 * p.F_phi / std::sqrt(d.K);
+    }
+    for (int s = 0; s < 4; ++s) d.H_wall[s] = enthalpy_of_T(p, d.L_a, p.wall_T[s]);
+
+    // stability ranges
+    auto in02 = [](double r) { return r > 0.0 && r < 2.0; };
+    if (p.flow && (!in02(s_v) || !(d.l0 > 0.0))) return LBM_ERR_STABILITY;
+    if (!in02(za) || !in02(ea) || !in02(ze)) return LBM_ERR_STABILITY;
+    const double cap = p.thermal_q == 9 ? 9.0 / 5.0 : 1.0 / p.varpi;   // Remark I (and its D2Q5 analogue)
+    if (!(d.c_fref < cap * c_pl) || !(d.c_mref < cap * c_pm)) return LBM_ERR_STABILITY;
+    if (!(d.exchange_rate < 1.0)) return LBM_ERR_STABILITY;
+    if (out) *out = d;
+    return LBM_OK;
+}
+
+struct Layout {
+    int pitch, nplanes;
+    long long plane;
+    size_t elem, buf_bytes, dT_bytes, off_buf1, off_dT, off_status, off_scratch, off_out, total;
+    int nblocks;
+};
+
+Layout layout_of(const lbm_params& p) {
+    Layout L;
+    L.elem = p.precision == LBM_F64 ? 8 : 4;
+    const int align_elems = (int)(128 / L.elem);
+    L.pitch = (p.nx + align_elems - 1) / align_elems * align_elems;
+    L.plane = (long long)L.pitch * p.ny;
+    L.nplanes = (p.flow ? 9 : 0) + 2 * p.thermal_q;
+    L.buf_bytes = align_up((size_t)L.nplanes * (size_t)L.plane * L.elem);
+    L.dT_bytes = align_up((size_t)L.plane * L.elem);
+    L.nblocks = lbmk::diag_blocks(p.nx, p.ny);
+    L.off_buf1 = L.buf_bytes;
+    L.off_dT = 2 * L.buf_bytes;
+    L.off_status = L.off_dT + L.dT_bytes;
+    L.off_scratch = L.off_status + kAlign;
+    L.off_out = L.off_scratch + align_up((size_t)L.nblocks * 4 * sizeof(double));
+    L.total = L.off_out + kAlign;
+    return L;
+}
+
+}  // namespace
+
+struct lbm_handle {
+    lbm_params p;
+    lbm_derived d;
+    Layout L;
+    cudaStream_t stream = nullptr;
+    cudaStream_t cap = nullptr;
+    lbm_alloc_fn alloc = nullptr;
+    lbm_free_fn release = nullptr;
+    void* ctx = nullptr;
+    char* base = nullptr;
+    void* buf[2] = {nullptr, nullptr};
+    void* dT = nullptr;
+    unsigned int* status = nullptr;
+    double* scratch = nullptr;
+    double* diag_out = nullptr;
+    int cur = 0;
+    int64_t steps = 0;
+    int sticky = LBM_OK;
+    cudaGraphExec_t graph = nullptr;
+};
+
+namespace {
+
+void* dev_alloc(lbm_handle* h, size_t bytes) {
+    if (h->alloc) return h->alloc(bytes, h->ctx);
+    void* p = nullptr;
+    if (cudaMallocAsync(&p, bytes, h->stream) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return p;
+}
+
+void dev_free(lbm_handle* h, void* p) {
+    if (!p) return;
+    if (h->release) h->release(p, h->ctx);
+    else cudaFreeAsync(p, h->stream);
+}
+
+template <typename R>
+lbmk::StepParams<R> make_params(const lbm_handle* h, int from) {
+    const lbm_params& p = h->p;
+    const lbm_derived& d = h->d;
+    lbmk::StepParams<R> P;
+    std::memset(&P, 0, sizeof P);
+    P.src = static_cast<const R*>(h->buf[from]);
+    P.dst = static_cast<R*>(h->buf[1 - from]);
+    P.dT = static_cast<R*>(h->dT);
+    P.status = h->status;
+    P.nx = p.nx;
+    P.ny = p.ny;
+    P.pitch = h->L.pitch;
+    P.plane = h->L.plane;
+    P.per_x = p.periodic_x;
+    P.per_y = p.periodic_y;
+    for (int s = 0; s < 4; ++s) {
+        P.wall_kind[s] = p.wall_kind[s];
+        P.wall_T[s] = (R)p.wall_T[s];
+        P.wall_H[s] = (R)d.H_wall[s];
+    }
+    const double phi = p.porosity;
+    P.phi = (R)phi;
+    P.inv_phi = (R)(1.0 / phi);
+    if (p.flow) {
+        P.drag_lin = (R)(phi * d.nu_f / d.K);
+        P.drag_forch = (R)(phi * p.F_phi / std::sqrt(d.K));
+        P.gbeta = (R)d.gbeta;
+        P.T0 = (R)p.T_ref0;
+        P.l0 = (R)d.l0;
+        P.l0sq = (R)(d.l0 * d.l0);
+        P.l1 = (R)d.l1;
+    }
+    for (int k = 0; k < 9; ++k) {
+        P.s[k] = (R)d.s[k];
+        P.zeta[k] = (R)d.zeta[k];
+        P.eta[k] = (R)d.eta[k];
+    }
+    P.H_fs = (R)d.H_fs;
+    P.H_fl = (R)d.H_fl;
+    P.inv_dH = (R)(1.0 / (d.H_fl - d.H_fs));
+    P.mush_slope = (R)((p.T_liquidus - p.T_solidus) / (d.H_fl - d.H_fs));
+    P.T_fs = (R)p.T_solidus;
+    P.T_fl = (R)p.T_liquidus;
+    P.inv_c_ps = (R)1.0;
+    P.inv_c_pl = (R)1.0;
+    P.c_pl = (R)1.0;
+    P.c_fref = (R)d.c_fref;
+    P.c_mref = (R)d.c_mref;
+    P.c_pm = (R)1.0;
+    P.inv_c_pm = (R)1.0;
+    P.varpi = (R)p.varpi;
+    P.a_f = (R)(d.h_v / (phi * 1.0));
+    P.a_m = (R)(d.h_v / ((1.0 - phi) * d.rho_m));
+    return P;
+}
+
+int cuda_fail(lbm_handle* h) {
+    cudaGetLastError();
+    if (h) h->sticky = LBM_ERR_CUDA;
+    return LBM_ERR_CUDA;
+}
+
+template <typename R>
+cudaError_t enqueue_step(lbm_handle* h, int from, cudaStream_t s) {
+    return lbmk::launch_step<R>(make_params<R>(h, from), h->p.thermal_q, h->p.flow, s);
+}
+
+cudaError_t enqueue_one(lbm_handle* h, int from, cudaStream_t s) {
+    return h->p.precision == LBM_F64 ? enqueue_step<double>(h, from, s) : enqueue_step<float>(h, from, s);
+}
+
+int build_graph(lbm_handle* h) {
+    if (h->graph) return LBM_OK;
+    if (!h->cap && cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking) != cudaSuccess) return cuda_fail(h);
+    if (cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return cuda_fail(h);
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < kGraphSteps && e == cudaSuccess; ++i) e = enqueue_one(h, i & 1, h->cap);
+    cudaGraph_t g = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(h->cap, &g);
+    if (e != cudaSuccess || e2 != cudaSuccess || !g) {
+        if (g) cudaGraphDestroy(g);
+        return cuda_fail(h);
+    }
+    cudaError_t e3 = cudaGraphInstantiate(&h->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e3 != cudaSuccess) {
+        h->graph = nullptr;
+        return cuda_fail(h);
+    }
+    return LBM_OK;
+}
+
+int sync_and_check(lbm_handle* h) {
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) return cuda_fail(h);
+    unsigned int st = 0;
+    if (cudaMemcpy(&st, h->status, sizeof st, cudaMemcpyDeviceToHost) != cudaSuccess) return cuda_fail(h);
+    if (st & lbmk::STATUS_UNSTABLE) h->sticky = LBM_ERR_UNSTABLE;
+    return h->sticky;
+}
+
+template <typename R>
+void init_values(const lbm_handle* h, lbmk::InitVals<R>& V) {
+    const lbm_params& p = h->p;
+    const lbm_derived& d = h->d;
+    const double w[9] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36};
+    const double T = p.T_init, H = enthalpy_of_T(p, d.L_a, T);
+    int k = 0;
+    if (p.flow)
+        for (int i = 0; i < 9; ++i) V.v[k++] = (R)w[i];     // f^eq(1, 0), Eq. 27
+    const int Q = p.thermal_q;
+    // g^eq(H, T, 0): Eq. 40 / B3; h^eq(T): Eq. 49 / B5 (c_pl = c_pm = 1)
+    const double gw0 = Q == 9 ? 5.0 / 9.0 : p.varpi;
+    V.v[k++] = (R)(H - gw0 * d.c_fref * T);
+    for (int i = 1; i < Q; ++i) V.v[k++] = (R)((Q == 9 ? w[i] : 0.25 * p.varpi) * d.c_fref * T);
+    V.v[k++] = (R)(T - gw0 * d.c_mref * T);
+    for (int i = 1; i < Q; ++i) V.v[k++] = (R)((Q == 9 ? w[i] : 0.25 * p.varpi) * d.c_mref * T);
+}
+
+template <typename R>
+cudaError_t enqueue_init(lbm_handle* h) {
+    lbmk::InitVals<R> V;
+    std::memset(&V, 0, sizeof V);
+    init_values<R>(h, V);
+    return lbmk::launch_init<R>(static_cast<R*>(h->buf[0]), static_cast<R*>(h->dT), h->L.nplanes, h->L.plane,
+                                h->p.nx, h->p.ny, h->L.pitch, V, h->stream);
+}
+
+void free_handle(lbm_handle* h) {
+    if (!h) return;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    if (h->graph) cudaGraphExecDestroy(h->graph);
+    if (h->cap) cudaStreamDestroy(h->cap);
+    dev_free(h, h->base);
+    if (h->stream && !h->release) cudaStreamSynchronize(h->stream);
+    cudaGetLastError();
+    delete h;
+}
+
+}  // namespace
+
+extern "C" {
+
+void lbm_params_default(lbm_params* p) {
+    if (!p) return;
+    std::memset(p, 0, sizeof *p);
+    p->nx = 150;
+    p->ny = 150;
+    p->thermal_q = 5;
+    p->precision = LBM_F32;
+    p->flow = 1;
+    p->periodic_x = 0;
+    p->periodic_y = 0;
+    p->wall_kind[0] = LBM_WALL_DIRICHLET;
+    p->wall_kind[1] = LBM_WALL_DIRICHLET;
+    p->wall_kind[2] = LBM_WALL_ADIABATIC;
+    p->wall_kind[3] = LBM_WALL_ADIABATIC;
+    p->wall_T[0] = 1.0;
+    p->wall_T[1] = 0.0;
+    p->porosity = 0.8;
+    p->Ra = 1e6;
+    p->Pr = 50.0;
+    p->Da = 1e-4;
+    p->Ste = 1.0;
+    p->cond_ratio = 1e3;
+    p->Nu_i = 5.9;
+    p->J = 1.0;
+    p->F_phi = 0.068;
+    p->sigma_hat = 1.0;
+    p->dp_over_L = 0.0135;
+    p->k_f = 5e-4;
+    p->cfref_over_cpl = 0.2;
+    p->cmref_over_cpm = 1.0;
+    p->T_hot = 1.0;
+    p->T_cold = 0.0;
+    p->T_init = 0.0;
+    p->T_ref0 = 0.0;
+    p->T_solidus = 0.299;
+    p->T_liquidus = 0.301;
+    p->L_char = 150.0;
+    p->varpi = 2.0 / 3.0;
+}
+
+int lbm_derive(const lbm_params* p, lbm_derived* d) { return derive_impl(p, d); }
+
+int64_t lbm_state_bytes(const lbm_params* p) {
+    if (derive_impl(p, nullptr) != LBM_OK) return -1;
+    return (int64_t)layout_of(*p).total;
+}
+
+int lbm_create_ex(const lbm_params* p, void* cuda_stream, lbm_alloc_fn alloc, lbm_free_fn release, void* ctx,
+                  lbm_handle** out) {
+    if (!out) return LBM_ERR_ARG;
+    *out = nullptr;
+    if ((alloc == nullptr) != (release == nullptr)) return LBM_ERR_ARG;
+    lbm_derived d;
+    int rc = derive_impl(p, &d);
+    if (rc != LBM_OK) return rc;
+    lbm_handle* h = new (std::nothrow) lbm_handle();
+    if (!h) return LBM_ERR_OOM;
+    h->p = *p;
+    h->d = d;
+    h->L = layout_of(*p);
+    h->stream = static_cast<cudaStream_t>(cuda_stream);
+    h->alloc = alloc;
+    h->release = release;
+    h->ctx = ctx;
+    h->base = static_cast<char*>(dev_alloc(h, h->L.total));
+    if (!h->base) {
+        delete h;
+        return LBM_ERR_OOM;
+    }
+    h->buf[0] = h->base;
+    h->buf[1] = h->base + h->L.off_buf1;
+    h->dT = h->base + h->L.off_dT;
+    h->status = reinterpret_cast<unsigned int*>(h->base + h->L.off_status);
+    h->scratch = reinterpret_cast<double*>(h->base + h->L.off_scratch);
+    h->diag_out = reinterpret_cast<double*>(h->base + h->L.off_out);
+    cudaError_t e = cudaMemsetAsync(h->status, 0, sizeof(unsigned int), h->stream);
+    if (e == cudaSuccess) e = p->precision == LBM_F64 ? enqueue_init<double>(h) : enqueue_init<float>(h);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        free_handle(h);
+        return LBM_ERR_CUDA;
+    }
+    *out = h;
+    return LBM_OK;
+}
+
+int lbm_create(const lbm_params* p, void* cuda_stream, lbm_handle** out) {
+    return lbm_create_ex(p, cuda_stream, nullptr, nullptr, nullptr, out);
+}
+
+int lbm_step(lbm_handle* h, int64_t nsteps) {
+    if (!h || nsteps < 0) return LBM_ERR_ARG;
+    if (h->sticky != LBM_OK) return h->sticky;
+    int64_t n = nsteps;
+    while (n > 0 && h->cur != 0) {
+        if (enqueue_one(h, h->cur, h->stream) != cudaSuccess) return cuda_fail(h);
+        h->cur ^= 1;
+        ++h->steps;
+        --n;
+    }
+    if (n >= kGraphSteps) {
+        int rc = build_graph(h);
+        if (rc != LBM_OK) return rc;
+        while (n >= kGraphSteps) {
+            if (cudaGraphLaunch(h->graph, h->stream) != cudaSuccess) return cuda_fail(h);
+            h->steps += kGraphSteps;
+            n -= kGraphSteps;
+        }
+    }
+    while (n > 0) {
+        if (enqueue_one(h, h->cur, h->stream) != cudaSuccess) return cuda_fail(h);
+        h->cur ^= 1;
+        ++h->steps;
+        --n;
+    }
+    return h->sticky;
+}
+
+int lbm_fields(lbm_handle* h, int32_t mask, void* const* dst, int32_t dst_on_device) {
+    if (!h || !dst || (mask & ~((1 << LBM_NUM_FIELDS) - 1))) return LBM_ERR_ARG;
+    if (h->sticky == LBM_ERR_CUDA) return LBM_ERR_STATE;
+    for (int i = 0; i < LBM_NUM_FIELDS; ++i)
+        if ((mask & (1 << i)) && !dst[i]) return LBM_ERR_ARG;
+    if (!mask) return h->sticky;
+    const size_t n = (size_t)h->p.nx * h->p.ny, bytes = n * h->L.elem;
+    char* staging = nullptr;
+    void* targets[LBM_NUM_FIELDS] = {nullptr};
+    if (dst_on_device) {
+        for (int i = 0; i < LBM_NUM_FIELDS; ++i) targets[i] = dst[i];
+    } else {
+        int cnt = 0;
+        for (int i = 0; i < LBM_NUM_FIELDS; ++i) cnt += (mask >> i) & 1;
+        staging = static_cast<char*>(dev_alloc(h, align_up(bytes) * cnt));
+        if (!staging) return LBM_ERR_OOM;
+        int k = 0;
+        for (int i = 0; i < LBM_NUM_FIELDS; ++i)
+            if (mask & (1 << i)) targets[i] = staging + align_up(bytes) * (k++);
+    }
+    cudaError_t e;
+    if (h->p.precision == LBM_F64) {
+        lbmk::FieldOut<double> o;
+        for (int i = 0; i < 7; ++i) o.dst[i] = static_cast<double*>(targets[i]);
+        o.mask = mask;
+        o.ld = h->p.nx;
+        e = lbmk::launch_fields<double>(make_params<double>(h, h->cur), o, h->p.thermal_q, h->p.flow, h->stream);
+    } else {
+        lbmk::FieldOut<float> o;
+        for (int i = 0; i < 7; ++i) o.dst[i] = static_cast<float*>(targets[i]);
+        o.mask = mask;
+        o.ld = h->p.nx;
+        e = lbmk::launch_fields<float>(make_params<float>(h, h->cur), o, h->p.thermal_q, h->p.flow, h->stream);
+    }
+    if (e == cudaSuccess && !dst_on_device)
+        for (int i = 0; i < LBM_NUM_FIELDS && e == cudaSuccess; ++i)
+            if (mask & (1 << i)) e = cudaMemcpyAsync(dst[i], targets[i], bytes, cudaMemcpyDeviceToHost, h->stream);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        cudaStreamSynchronize(h->stream);
+        dev_free(h, staging);
+        return cuda_fail(h);
+    }
+    int rc = sync_and_check(h);
+    dev_free(h, staging);
+    return rc;
+}
+
+int lbm_diag(lbm_handle* h, double* melt_frac, double* nu_hot, double* enthalpy, double* mass) {
+    if (!h) return LBM_ERR_ARG;
+    if (h->sticky == LBM_ERR_CUDA) return LBM_ERR_STATE;
+    const lbm_params& p = h->p;
+    lbmk::DiagConst C;
+    C.phi = p.porosity;
+    C.rho_l = 1.0;
+    C.rho_m = h->d.rho_m;
+    C.c_pm = 1.0;
+    C.k_f = p.k_f;
+    C.k_m = h->d.k_m;
+    C.left_wall = (!p.periodic_x && p.nx >= 3) ? 1 : 0;
+    cudaError_t e = p.precision == LBM_F64
+                        ? lbmk::launch_diag<double>(make_params<double>(h, h->cur), C, h->scratch, h->diag_out,
+                                                    p.thermal_q, p.flow, h->stream)
+                        : lbmk::launch_diag<float>(make_params<float>(h, h->cur), C, h->scratch, h->diag_out,
+                                                   p.thermal_q, p.flow, h->stream);
+    double s[4] = {0, 0, 0, 0};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(s, h->diag_out, sizeof s, cudaMemcpyDeviceToHost, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h);
+    int rc = sync_and_check(h);
+    if (rc == LBM_ERR_CUDA) return rc;
+    const double k_e = p.porosity * p.k_f + (1.0 - p.porosity) * h->d.k_m;
+    if (melt_frac) *melt_frac = s[0] / ((double)p.nx * p.ny);
+    if (nu_hot)
+        *nu_hot = C.left_wall ? p.L_char / (k_e * (p.T_hot - p.T_cold)) * (s[3] / p.ny) : std::nan("");
+    if (enthalpy) *enthalpy = s[1];
+    if (mass) *mass = s[2];
+    return rc;
+}
+
+static int copy_planes(lbm_handle* h, void* host_or_dev, int first_plane, int nplanes, bool to_state, int on_device,
+                       void* state_base) {
+    if (!host_or_dev || nplanes == 0) return LBM_OK;
+    const size_t el = h->L.elem;
+    char* s = static_cast<char*>(state_base) + (size_t)first_plane * h->L.plane * el;
+    const size_t dpitch = (size_t)h->p.nx * el, spitch = (size_t)h->L.pitch * el;
+    const size_t rows = (size_t)nplanes * h->p.ny;
+    cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : (to_state ? cudaMemcpyHostToDevice
+                                                                           : cudaMemcpyDeviceToHost);
+    cudaError_t e = to_state ? cudaMemcpy2DAsync(s, spitch, host_or_dev, dpitch, dpitch, rows, kind, h->stream)
+                             : cudaMemcpy2DAsync(host_or_dev, dpitch, s, spitch, dpitch, rows, kind, h->stream);
+    return e == cudaSuccess ? LBM_OK : cuda_fail(h);
+}
+
+int lbm_get_state(lbm_handle* h, void* f, void* g, void* hm, void* dT, int32_t on_device) {
+    if (!h) return LBM_ERR_ARG;
+    if (h->sticky == LBM_ERR_CUDA) return LBM_ERR_STATE;
+    const int Q = h->p.thermal_q, base = h->p.flow ? 9 : 0;
+    void* cur = h->buf[h->cur];
+    int rc = LBM_OK;
+    if (h->p.flow) rc = copy_planes(h, f, 0, 9, false, on_device, cur);
+    if (rc == LBM_OK) rc = copy_planes(h, g, base, Q, false, on_device, cur);
+    if (rc == LBM_OK) rc = copy_planes(h, hm, base + Q, Q, false, on_device, cur);
+    if (rc == LBM_OK) rc = copy_planes(h, dT, 0, 1, false, on_device, h->dT);
+    if (rc != LBM_OK) return rc;
+    return sync_and_check(h);
+}
+
+int lbm_set_state(lbm_handle* h, const void* f, const void* g, const void* hm, const void* dT, int32_t on_device) {
+    if (!h) return LBM_ERR_ARG;
+    if (h->sticky == LBM_ERR_CUDA) return LBM_ERR_STATE;
+    const int Q = h->p.thermal_q, base = h->p.flow ? 9 : 0;
+    void* cur = h->buf[h->cur];
+    int rc = LBM_OK;
+    if (h->p.flow) rc = copy_planes(h, const_cast<void*>(f), 0, 9, true, on_device, cur);
+    if (rc == LBM_OK) rc = copy_planes(h, const_cast<void*>(g), base, Q, true, on_device, cur);
+    if (rc == LBM_OK) rc = copy_planes(h, const_cast<void*>(hm), base + Q, Q, true, on_device, cur);
+    if (rc == LBM_OK) rc = copy_planes(h, const_cast<void*>(dT), 0, 1, true, on_device, h->dT);
+    if (rc != LBM_OK) return rc;
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) return cuda_fail(h);
+    return h->sticky;
+}
+
+int lbm_status(lbm_handle* h) {
+    if (!h) return LBM_ERR_ARG;
+    return sync_and_check(h);
+}
+
+int64_t lbm_steps_done(const lbm_handle* h) { return h ? h->steps : -1; }
+
+int lbm_describe(const lbm_handle* h, lbm_params* p, lbm_derived* d) {
+    if (!h) return LBM_ERR_ARG;
+    if (p) *p = h->p;
+    if (d) *d = h->d;
+    return LBM_OK;
+}
+
+int lbm_destroy(lbm_handle* h) {
+    if (!h) return LBM_OK;
+    free_handle(h);
+    return LBM_OK;
+}
+
+const char* lbm_strerror(int code) {
+    switch (code) {
+        case LBM_OK: return "ok";
+        case LBM_ERR_ARG: return "invalid argument";
+        case LBM_ERR_STABILITY: return "parameters outside the stable range of the scheme";
+        case LBM_ERR_OOM: return "device allocation failed";
+        case LBM_ERR_CUDA: return "CUDA runtime error";
+        case LBM_ERR_UNSTABLE: return "non-finite or runaway state detected on the device";
+        case LBM_ERR_TIMEOUT: return "bounded device wait expired";
+        case LBM_ERR_STATE: return "handle in a failed state or call out of order";
+        default: return "unknown status code";
+    }
+}
+
+}  // extern "C"

@@ -1,0 +1,122 @@
+"""Host-side checks of the C ABI (no GPU): the library builds, loads and exports
+every entry point that include/lbm.h declares; its parameter map agrees with
+the oracle's independent map; malformed and unstable inputs are rejected."""
+import ctypes
+import math
+import re
+from pathlib import Path
+
+import pytest
+
+from paper_1701_00702_gb300 import inputs
+
+ROOT = Path(__file__).resolve().parents[1]
+
+
+@pytest.fixture(scope="module")
+def lbm():
+    from paper_1701_00702_gb300 import build, lbm as mod
+    build.build()
+    return mod
+
+
+def declared_symbols():
+    text = "\n".join(p.read_text() for p in (ROOT / "include").glob("*.h"))
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(lbm_[a-z0-9_]+)\s*\(", text)) - {"lbm_alloc_fn", "lbm_free_fn"})
+
+
+def test_library_exports_every_declared_entry_point(lbm):
+    L = lbm.lib()
+    names = declared_symbols()
+    assert "lbm_step" in names and "lbm_create" in names
+    missing = [n for n in names if not hasattr(L, n)]
+    assert not missing, missing
+
+
+@pytest.mark.parametrize("make", [
+    lambda: inputs.conduction_1d(),
+    lambda: inputs.conduction_1d(thermal_q=9),
+    lambda: inputs.cavity(256),
+    lambda: inputs.cavity(1024, thermal_q=9),
+    lambda: inputs.paper_cavity_defaults(),
+    lambda: inputs.batch_draws(count=4)[3],
+])
+def test_parameter_map_matches_oracle(lbm, oracle_mod, make):
+    p = make()
+    d = lbm.derive(p)
+    lc = oracle_mod.lattice_config(p)
+    keys = ["k_m", "rho_m", "L_a", "h_v", "alpha_fref", "alpha_mref", "c_fref", "c_mref", "d_p"]
+    if p["flow"]:
+        keys += ["nu_f", "nu_e", "gbeta", "K"]
+    for k in keys:
+        assert math.isclose(d[k], lc[k], rel_tol=1e-15, abs_tol=0.0), k
+    q = lc["qt"]
+    assert d["zeta"][:q] == pytest.approx(lc["zeta"][:q], rel=1e-15)
+    assert d["eta"][:q] == pytest.approx(lc["eta"][:q], rel=1e-15)
+    if p["flow"]:
+        assert d["s"] == pytest.approx(lc["s"], rel=1e-15)
+    for side in range(4):
+        assert d["H_wall"][side] == pytest.approx(oracle_mod.H_of_T(p, p["wall_T"][side]), rel=1e-15, abs=1e-15)
+
+
+@pytest.mark.parametrize("change", [
+    dict(nx=0), dict(ny=-1), dict(nx=2), dict(thermal_q=7), dict(precision=5), dict(porosity=1.0),
+    dict(porosity=0.0), dict(Ste=0.0), dict(k_f=-1.0), dict(T_solidus=0.4, T_liquidus=0.3),
+    dict(T_hot=0.0, T_cold=0.0), dict(T_hot=0.0, T_cold=1.0), dict(varpi=1.0), dict(Da=0.0),
+    dict(Pr=float("nan")), dict(wall_kind=[0, 0, 2, 1]), dict(nx=65537), dict(nx=40000, ny=40000),
+])
+def test_malformed_parameters_are_rejected(lbm, change):
+    p = inputs.cavity(64)
+    p.update(change)
+    with pytest.raises(lbm.LbmError) as e:
+        lbm.derive(p)
+    assert e.value.code == -1
+    assert lbm.state_bytes(p) == -1
+
+
+@pytest.mark.parametrize("change", [
+    dict(k_f=0.2),                                # large diffusivity: exchange rate h_v grows past 1
+    dict(cfref_over_cpl=1.6, thermal_q=5),        # varpi c_f,ref >= c_pl (D2Q5 analogue of Remark I)
+    dict(cfref_over_cpl=1.85, thermal_q=9),       # Remark I
+    dict(Nu_i=500.0),                             # explicit exchange rate >= 1
+])
+def test_unstable_parameters_are_rejected(lbm, change):
+    p = inputs.cavity(64)
+    p.update(change)
+    with pytest.raises(lbm.LbmError) as e:
+        lbm.derive(p)
+    assert e.value.code == -2
+
+
+def test_size_limits(lbm):
+    p = inputs.periodic_box(32768, 32768)
+    assert lbm.state_bytes(p) > 0
+    p = inputs.periodic_box(32768, 32769)
+    assert lbm.state_bytes(p) == -1
+    p = inputs.periodic_box(1, 1, L_char=100.0)
+    assert lbm.state_bytes(p) > 0
+
+
+def test_state_bytes_account_for_both_copies(lbm):
+    p = inputs.cavity(2048)
+    b = lbm.state_bytes(p)
+    per_node = (2 * (9 + 5 + 5) + 1) * 4
+    assert per_node * 2048 * 2048 <= b < per_node * 2048 * 2048 * 1.01
+
+
+def test_strerror_names_every_code(lbm):
+    for code in range(0, -8, -1):
+        s = lbm.lib().lbm_strerror(code).decode()
+        assert s and s != "unknown status code"
+    assert lbm.lib().lbm_strerror(-99).decode() == "unknown status code"
+
+
+def test_create_without_gpu_fails_cleanly(lbm):
+    """On a host without a GPU lbm_create reports an error instead of crashing."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    h = ctypes.c_void_p()
+    rc = lbm.lib().lbm_create(ctypes.byref(lbm.to_struct(inputs.cavity(16))), None, ctypes.byref(h))
+    assert rc in (-3, -4) and not h.value

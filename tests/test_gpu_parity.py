@@ -1,0 +1,288 @@
+"""Parity of the CUDA path (called through the C ABI) with the FP64 oracle.
+
+Tolerances:
+  * FP64 storage: element-wise agreement to a few ulps of the largest value
+    (1e-12 relative) after one step; relative L2 <= 1e-10 after 20k steps.
+  * FP32 storage: one step from identical inputs agrees to 2e-6 of the
+    array's scale (FP32 rounding of a few dozen operations); after long runs
+    the fields T_f, T_s (= T_m), f_l and u agree in relative L2 to 1e-5, the
+    bound the method's stated target sets for the FP32 path.
+"""
+import numpy as np
+import pytest
+
+from paper_1701_00702_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lbm():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    from paper_1701_00702_gb300 import build, lbm as mod
+    build.build()
+    return mod
+
+
+def rel_l2(a, b):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    den = np.sqrt((b * b).sum())
+    return float(np.sqrt(((a - b) ** 2).sum()) / (den if den > 0 else 1.0))
+
+
+def _as_precision(arrs, prec):
+    dt = np.float64 if prec == 0 else np.float32
+    return [None if a is None else np.asarray(a).astype(dt) for a in arrs]
+
+
+def _random_pair(lbm, oracle_mod, p, seed):
+    """Solver and oracle holding the same (precision-rounded) random state."""
+    lc = oracle_mod.lattice_config(p)
+    H_lo, H_hi = lc["T_fs"] - 0.3, lc["T_fl"] + lc["L_a"] + 0.3
+    F, G, Hm, dT = inputs.random_state(p["nx"], p["ny"], p["thermal_q"], seed, H_range=(H_lo, H_hi),
+                                       Tm_range=(0.0, 1.0))
+    F, G, Hm, dT = _as_precision([F, G, Hm, dT], p["precision"])
+    s = lbm.Solver(p)
+    s.set_state(F if p["flow"] else None, G, Hm, dT)
+    o = oracle_mod.Oracle(p)
+    o.set_state(F.astype(np.float64), G.astype(np.float64), Hm.astype(np.float64), dT.astype(np.float64))
+    return s, o
+
+
+def _compare_states(s, o, prec, flow):
+    f, g, h, dT = s.get_state()
+    F, G, H, D = o.state()
+    tol = 1e-12 if prec == 0 else 2e-6
+    pairs = [(g, G, "g"), (h, H, "h"), (dT, D, "dT")] + ([(f, F, "f")] if flow else [])
+    for a, b, name in pairs:
+        scale = max(np.abs(b).max(), 1e-3)
+        err = np.abs(a.astype(np.float64) - b).max() / scale
+        assert err < tol, (name, err)
+
+
+SHAPES = [
+    # (nx, ny, periodic_x, periodic_y): several 128 x 2 blocks with ragged tails, tiny grids
+    (131, 7, 0, 0), (131, 7, 1, 1), (130, 9, 0, 1), (3, 3, 0, 0), (1, 1, 1, 1), (5, 1, 0, 1), (257, 4, 1, 0),
+]
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("qt", [5, 9])
+@pytest.mark.parametrize("flow", [1, 0])
+@pytest.mark.parametrize("shape", SHAPES)
+def test_steps_from_random_state(lbm, oracle_mod, prec, qt, flow, shape):
+    nx, ny, px, py = shape
+    p = inputs.cavity(max(nx, ny), ny=ny, precision=prec, thermal_q=qt, flow=flow, periodic_x=px,
+                      periodic_y=py, L_char=100.0, Ra=1e7)
+    p["nx"] = nx
+    s, o = _random_pair(lbm, oracle_mod, p, seed=nx * 31 + ny)
+    s.step(1)
+    o.run(1)
+    _compare_states(s, o, prec, flow)
+    s.step(2)
+    o.run(2)
+    _compare_states(s, o, prec, flow)
+    fs = s.fields(device=False)
+    fo = o.fields()
+    for name, key in (("T_f", "T_f"), ("T_s", "T_m"), ("f_l", "f_l"), ("u_x", "u_x"), ("u_y", "u_y"),
+                      ("rho", "rho"), ("H_f", "H_f")):
+        scale = max(np.abs(fo[key]).max(), 1e-3)
+        tol = 1e-12 if prec == 0 else 5e-6
+        assert np.abs(fs[name].astype(np.float64) - fo[key]).max() / scale < tol, name
+    s.close()
+
+
+@pytest.mark.parametrize("qt", [5, 9])
+@pytest.mark.parametrize("prec,tol", [(0, 1e-10), (1, 1e-5)])
+def test_conduction_melting_20k_steps(lbm, oracle_mod, qt, prec, tol):
+    """Conduction-only LTNE melting, 200 x 4, 20,000 steps (the Sec. IV A constants)."""
+    p = inputs.conduction_1d(thermal_q=qt, precision=prec)
+    s = lbm.Solver(p)
+    s.step(20000)
+    assert s.status() == 0
+    o = oracle_mod.Oracle(p).run(20000)
+    fs, fo = s.fields(device=False), o.fields()
+    for name, key in (("T_f", "T_f"), ("T_s", "T_m"), ("f_l", "f_l")):
+        assert rel_l2(fs[name], fo[key]) <= tol, name
+    assert np.all(fs["u_x"] == 0) and np.all(fs["u_y"] == 0)
+    d_s, d_o = s.diag(), o.diag()
+    assert abs(d_s["melt_frac"] - d_o["melt_frac"]) <= (1e-12 if prec == 0 else 1e-5)
+    s.close()
+
+
+def test_cavity_256_fp32_parity(lbm, oracle_mod):
+    """Square-cavity melting with natural convection, 256 x 256, FP32, 2,000 steps:
+    T_f, T_s, f_l, u_x, u_y against the oracle in relative L2."""
+    p = inputs.cavity(256, precision=1)
+    s = lbm.Solver(p)
+    s.step(2000)
+    assert s.status() == 0
+    o = oracle_mod.Oracle(p).run(2000)
+    fs, fo = s.fields(device=False), o.fields()
+    for name, key in (("T_f", "T_f"), ("T_s", "T_m"), ("f_l", "f_l"), ("u_x", "u_x"), ("u_y", "u_y")):
+        assert rel_l2(fs[name], fo[key]) <= 1e-5, name
+    assert np.abs(fo["u_y"]).max() > 1e-6      # the flow is really on
+    d_s, d_o = s.diag(), o.diag()
+    for k in ("melt_frac", "nu_hot", "enthalpy", "mass"):
+        assert abs(d_s[k] / d_o[k] - 1.0) < 1e-5, k
+    s.close()
+
+
+def test_diagnostics_match_oracle_fp64(lbm, oracle_mod):
+    p = inputs.cavity(96, ny=80, precision=0, thermal_q=9)
+    s = lbm.Solver(p)
+    s.step(300)
+    o = oracle_mod.Oracle(p).run(300)
+    d_s, d_o = s.diag(), o.diag()
+    for k in ("melt_frac", "nu_hot", "enthalpy", "mass"):
+        assert abs(d_s[k] / d_o[k] - 1.0) < 1e-12, k
+    # equal states give bit-equal diagnostics
+    assert s.diag() == d_s
+    s.close()
+
+
+def test_full_size_sampled_parity_2048(lbm, oracle_mod):
+    """2048 x 2048 cavity in FP32, the benchmark's launch configuration: one step
+    from a random state checked against the oracle at sampled nodes (all four
+    edges and corners plus random interior nodes)."""
+    n = 2048
+    p = inputs.cavity(n, precision=1)
+    lc = oracle_mod.lattice_config(p)
+    F, G, Hm, dT = inputs.random_state(n, n, 5, seed=2048, H_range=(lc["T_fs"] - 0.3, lc["T_fl"] + lc["L_a"] + 0.3))
+    F, G, Hm, dT = _as_precision([F, G, Hm, dT], 1)
+    s = lbm.Solver(p)
+    s.set_state(F, G, Hm, dT)
+    s.step(1)
+    f1, g1, h1, d1 = s.get_state()
+    o = oracle_mod.Oracle(p)
+    o.set_state(F.astype(np.float64), G.astype(np.float64), Hm.astype(np.float64), dT.astype(np.float64))
+    rng = np.random.default_rng(7)
+    edge = np.arange(n)
+    xs = np.concatenate([edge, edge, np.zeros(n, int), np.full(n, n - 1), rng.integers(0, n, 20000)])
+    ys = np.concatenate([np.zeros(n, int), np.full(n, n - 1), edge, edge, rng.integers(0, n, 20000)])
+    fo, go, ho, do = o.step_nodes(xs, ys)
+    for a, b in ((f1[:, ys, xs].T, fo), (g1[:, ys, xs].T, go), (h1[:, ys, xs].T, ho), (d1[ys, xs], do)):
+        assert np.abs(a.astype(np.float64) - b).max() / max(np.abs(b).max(), 1e-3) < 2e-6
+    s.close()
+
+
+def test_full_size_invariants_2048(lbm):
+    """Properties that hold at any size, on the benchmark's 2048 x 2048 FP32 cavity
+    after 2,000 steps from the uniform start: finite, 0 <= f_l <= 1, u = 0 exactly
+    in solid nodes and on walls, melting has started at the hot wall only."""
+    s = lbm.Solver(inputs.cavity(2048, precision=1))
+    s.step(2000)
+    assert s.status() == 0
+    f = s.fields(device=False)
+    fl, ux, uy = f["f_l"], f["u_x"], f["u_y"]
+    assert np.isfinite(f["T_f"]).all() and np.isfinite(ux).all()
+    assert fl.min() >= 0.0 and fl.max() <= 1.0
+    solid = fl == 0.0
+    assert solid.mean() > 0.9
+    assert np.all(ux[solid] == 0.0) and np.all(uy[solid] == 0.0)
+    assert np.all(ux[:, 0] == 0) and np.all(uy[0, :] == 0) and np.all(ux[:, -1] == 0)
+    assert fl[:, 1].mean() > 0.5 and fl[:, -2].max() == 0.0
+    s.close()
+
+
+@pytest.mark.parametrize("prec,tol", [(0, 1e-12), (1, 2e-5)])
+def test_periodic_box_conserves_mass_and_enthalpy(lbm, prec, tol):
+    p = inputs.periodic_box(512, 384, precision=prec, Ra=1e7)
+    F, G, Hm, dT = inputs.random_state(512, 384, 5, seed=5, H_range=(0.2, 1.4))
+    F, G, Hm, dT = _as_precision([F, G, Hm, dT], prec)
+    s = lbm.Solver(p)
+    s.set_state(F, G, Hm, dT)
+    d0 = s.diag()
+    s.step(500)
+    d1 = s.diag()
+    assert abs(d1["mass"] / d0["mass"] - 1) < tol
+    assert abs(d1["enthalpy"] / d0["enthalpy"] - 1) < tol
+    s.close()
+
+
+def test_graph_replay_equals_single_launches(lbm):
+    p = inputs.cavity(150, precision=1)
+    a, b = lbm.Solver(p), lbm.Solver(p)
+    a.step(3)
+    a.step(130)          # odd start: single launches, then two captured 64-step graphs
+    for _ in range(133):
+        b.step(1)
+    fa, fb = a.get_state(), b.get_state()
+    for x, y in zip(fa, fb):
+        assert np.array_equal(x, y)
+    assert a.steps == b.steps == 133
+    a.close(); b.close()
+
+
+def test_checkpoint_resume_is_bitwise(lbm):
+    p = inputs.cavity(128, precision=1)
+    ref = lbm.Solver(p)
+    ref.step(700)
+    a = lbm.Solver(p)
+    a.step(300)
+    snap = a.get_state()
+    a.close()
+    b = lbm.Solver(p)
+    b.set_state(*snap)
+    b.step(400)
+    for x, y in zip(ref.get_state(), b.get_state()):
+        assert np.array_equal(x, y)
+    ref.close(); b.close()
+
+
+def test_fields_on_device_equal_host_copies(lbm):
+    import torch
+    s = lbm.Solver(inputs.cavity(200, ny=130, precision=1))
+    s.step(100)
+    dev = s.fields(device=True)
+    host = s.fields(device=False)
+    for k in dev:
+        assert np.array_equal(dev[k].cpu().numpy(), host[k])
+    assert dev["T_f"].dtype == torch.float32
+    part = s.fields(names=("f_l",), device=False)
+    assert list(part) == ["f_l"] and np.array_equal(part["f_l"], host["f_l"])
+    s.close()
+
+
+def test_nonfinite_state_raises_sticky_unstable_flag(lbm):
+    """A NaN planted in the state is caught by the kernel's check, reported as
+    LBM_ERR_UNSTABLE, and later steps are refused; the context stays usable."""
+    p = inputs.cavity(64, precision=1)
+    s = lbm.Solver(p)
+    f, g, h, dT = s.get_state()
+    g[0, 10, 10] = np.nan
+    s.set_state(f, g, h, dT)
+    s.step(1)
+    assert s.status() == -5
+    with pytest.raises(lbm.LbmError) as e:
+        s.step(1)
+    assert e.value.code == -5
+    s.close()
+    ok = lbm.Solver(p)
+    ok.step(10)
+    assert ok.status() == 0
+    ok.close()
+
+
+def test_step_zero_and_negative(lbm):
+    s = lbm.Solver(inputs.cavity(32, precision=1))
+    s.step(0)
+    assert s.steps == 0
+    with pytest.raises(lbm.LbmError) as e:
+        s.step(-1)
+    assert e.value.code == -1
+    s.close()
+
+
+def test_lbm_create_with_cuda_allocator(lbm):
+    """The stream-ordered CUDA allocator path (no PyTorch allocation hooks)."""
+    p = inputs.cavity(64, precision=1)
+    a = lbm.Solver(p, use_torch_alloc=False)
+    b = lbm.Solver(p)
+    a.step(50); b.step(50)
+    for x, y in zip(a.get_state(), b.get_state()):
+        assert np.array_equal(x, y)
+    a.close(); b.close()
