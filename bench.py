@@ -12,8 +12,10 @@ benchmark step advances the run by ``--lb-steps`` time steps (a chunk of the
 (million node updates per second, every node counted).
 
 Besides the headline number the line carries:
-  * roofline: the same kernel on the 2048 x 2048 cavity (1.3 GB of state, far
-    beyond L2), algorithmic 160 B per node update against the measured HBM
+  * roofline: the same kernel on the 2048 x 2048 cavity (0.7 GB of state, far
+    beyond L2), algorithmic 168 B per node update (19 FP32 populations, the
+    low part of the PCM rest population and the exchange history, each read
+    and written once) against the measured HBM
     copy bandwidth;
   * e2e: the same workload through the C ABI with host buffers: each step
     uploads the full state from pinned memory, advances it and reads back
@@ -46,9 +48,11 @@ L2_FLUSH_BYTES = 512 << 20
 
 
 def bytes_per_update(qt: int, flow: int, elem: int) -> int:
-    """Algorithmic HBM bytes per node update: every population read and written
-    once, plus the exchange history read and written once."""
-    return ((9 if flow else 0) + 2 * qt) * elem * 2 + 2 * elem
+    """Algorithmic HBM bytes per node update of the storage format: every
+    population read and written once, the exchange history read and written
+    once, and with FP32 storage the low part of the PCM rest population."""
+    planes = (9 if flow else 0) + 2 * qt + (1 if elem == 4 else 0)
+    return planes * elem * 2 + 2 * elem
 
 
 def parse():

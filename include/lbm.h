@@ -172,11 +172,18 @@ int lbm_diag(lbm_handle* h, double* melt_frac, double* nu_hot, double* enthalpy,
 
 /* Copies the raw state out or in: f (9 planes; ignored when flow = 0), g and
  * hm (thermal_q planes each) hold the post-collision populations of the last
- * step, dT ([ny][nx]) the exchange history T_m - T_f of the last step.
- * on_device selects device or host pointers.  Synchronises. */
-int lbm_get_state(lbm_handle* h, void* f, void* g, void* hm, void* dT, int32_t on_device);
+ * step, dT ([ny][nx]) the exchange history T_m - T_f of the last step.  The
+ * flow populations are stored, and exchanged here, as deviations f_i - w_i
+ * from the rest equilibrium f^eq(rho_0 = 1, u = 0) = w_i of Eq. 27
+ * (w = 4/9, 1/9 x4, 1/36 x4); g and hm are the populations themselves.
+ * With LBM_F32 storage the PCM rest population is the float-float sum
+ * g[0] + g0_lo ([ny][nx]); g0_lo may be NULL (get: not copied; set: taken
+ * as zero when g is given) and is ignored for LBM_F64 runs.  Any other
+ * pointer may be NULL to skip that array.  on_device selects device or host
+ * pointers.  Synchronises. */
+int lbm_get_state(lbm_handle* h, void* f, void* g, void* hm, void* dT, void* g0_lo, int32_t on_device);
 int lbm_set_state(lbm_handle* h, const void* f, const void* g, const void* hm, const void* dT,
-                  int32_t on_device);
+                  const void* g0_lo, int32_t on_device);
 
 /* Synchronises the handle's stream and returns the sticky status. */
 int lbm_status(lbm_handle* h);

@@ -132,7 +132,8 @@ Layout layout_of(const lbm_params& p) {
     const int align_elems = (int)(128 / L.elem);
     L.pitch = (p.nx + align_elems - 1) / align_elems * align_elems;
     L.plane = (long long)L.pitch * p.ny;
-    L.nplanes = (p.flow ? 9 : 0) + 2 * p.thermal_q;
+    // flow (9, deviations), PCM (Q), metal (Q), and with FP32 storage the low part of g_0
+    L.nplanes = (p.flow ? 9 : 0) + 2 * p.thermal_q + (p.precision == LBM_F32 ? 1 : 0);
     L.buf_bytes = align_up((size_t)L.nplanes * (size_t)L.plane * L.elem);
     L.dT_bytes = align_up((size_t)L.plane * L.elem);
     L.nblocks = lbmk::diag_blocks(p.nx, p.ny);
@@ -206,6 +207,7 @@ lbmk::StepParams<R> make_params(const lbm_handle* h, int from) {
         P.wall_kind[s] = p.wall_kind[s];
         P.wall_T[s] = (R)p.wall_T[s];
         P.wall_H[s] = (R)d.H_wall[s];
+        P.wall_H_lo[s] = (R)(d.H_wall[s] - (double)(R)d.H_wall[s]);
     }
     const double phi = p.porosity;
     P.phi = (R)phi;
@@ -295,14 +297,16 @@ void init_values(const lbm_handle* h, lbmk::InitVals<R>& V) {
     const double T = p.T_init, H = enthalpy_of_T(p, d.L_a, T);
     int k = 0;
     if (p.flow)
-        for (int i = 0; i < 9; ++i) V.v[k++] = (R)w[i];     // f^eq(1, 0), Eq. 27
+        for (int i = 0; i < 9; ++i) V.v[k++] = (R)0;        // f^eq(1, 0) - w_i = 0 (Eq. 27, deviation storage)
     const int Q = p.thermal_q;
     // g^eq(H, T, 0): Eq. 40 / B3; h^eq(T): Eq. 49 / B5 (c_pl = c_pm = 1)
     const double gw0 = Q == 9 ? 5.0 / 9.0 : p.varpi;
-    V.v[k++] = (R)(H - gw0 * d.c_fref * T);
+    const double g0 = H - gw0 * d.c_fref * T;
+    V.v[k++] = (R)g0;
     for (int i = 1; i < Q; ++i) V.v[k++] = (R)((Q == 9 ? w[i] : 0.25 * p.varpi) * d.c_fref * T);
     V.v[k++] = (R)(T - gw0 * d.c_mref * T);
     for (int i = 1; i < Q; ++i) V.v[k++] = (R)((Q == 9 ? w[i] : 0.25 * p.varpi) * d.c_mref * T);
+    if (p.precision == LBM_F32) V.v[k++] = (R)(g0 - (double)(R)g0);   // low part of g_0
 }
 
 template <typename R>
@@ -540,7 +544,7 @@ static int copy_planes(lbm_handle* h, void* host_or_dev, int first_plane, int np
     return e == cudaSuccess ? LBM_OK : cuda_fail(h);
 }
 
-int lbm_get_state(lbm_handle* h, void* f, void* g, void* hm, void* dT, int32_t on_device) {
+int lbm_get_state(lbm_handle* h, void* f, void* g, void* hm, void* dT, void* g0_lo, int32_t on_device) {
     if (!h) return LBM_ERR_ARG;
     if (h->sticky == LBM_ERR_CUDA) return LBM_ERR_STATE;
     const int Q = h->p.thermal_q, base = h->p.flow ? 9 : 0;
@@ -550,11 +554,13 @@ int lbm_get_state(lbm_handle* h, void* f, void* g, void* hm, void* dT, int32_t o
     if (rc == LBM_OK) rc = copy_planes(h, g, base, Q, false, on_device, cur);
     if (rc == LBM_OK) rc = copy_planes(h, hm, base + Q, Q, false, on_device, cur);
     if (rc == LBM_OK) rc = copy_planes(h, dT, 0, 1, false, on_device, h->dT);
+    if (rc == LBM_OK && h->p.precision == LBM_F32) rc = copy_planes(h, g0_lo, base + 2 * Q, 1, false, on_device, cur);
     if (rc != LBM_OK) return rc;
     return sync_and_check(h);
 }
 
-int lbm_set_state(lbm_handle* h, const void* f, const void* g, const void* hm, const void* dT, int32_t on_device) {
+int lbm_set_state(lbm_handle* h, const void* f, const void* g, const void* hm, const void* dT, const void* g0_lo,
+                  int32_t on_device) {
     if (!h) return LBM_ERR_ARG;
     if (h->sticky == LBM_ERR_CUDA) return LBM_ERR_STATE;
     const int Q = h->p.thermal_q, base = h->p.flow ? 9 : 0;
@@ -564,6 +570,12 @@ int lbm_set_state(lbm_handle* h, const void* f, const void* g, const void* hm, c
     if (rc == LBM_OK) rc = copy_planes(h, const_cast<void*>(g), base, Q, true, on_device, cur);
     if (rc == LBM_OK) rc = copy_planes(h, const_cast<void*>(hm), base + Q, Q, true, on_device, cur);
     if (rc == LBM_OK) rc = copy_planes(h, const_cast<void*>(dT), 0, 1, true, on_device, h->dT);
+    if (rc == LBM_OK && h->p.precision == LBM_F32) {
+        char* lo = static_cast<char*>(cur) + (size_t)(base + 2 * Q) * h->L.plane * h->L.elem;
+        if (g0_lo) rc = copy_planes(h, const_cast<void*>(g0_lo), base + 2 * Q, 1, true, on_device, cur);
+        else if (g && cudaMemsetAsync(lo, 0, (size_t)h->L.plane * h->L.elem, h->stream) != cudaSuccess)
+            rc = cuda_fail(h);
+    }
     if (rc != LBM_OK) return rc;
     if (cudaStreamSynchronize(h->stream) != cudaSuccess) return cuda_fail(h);
     return h->sticky;

@@ -6,15 +6,28 @@
 // Everything after the pull works in moment space:
 //   * m+ = M f+, n_g = M g, n_h = M h with the integer matrices of Eq. 13
 //     (D2Q9) and Eq. B1 (D2Q5), hand-unrolled;
+//   * flow populations are stored as deviations f_i - w_i from the rest
+//     equilibrium f^eq(rho_0 = 1, 0) = w_i (Eq. 27), an exact change of
+//     variables that keeps storage resolution proportional to u instead of
+//     rho; all flow moments below are deviations from r = M w = (1, -2, 1,
+//     0, ..., 0) and delta_rho = rho - 1;
 //   * the volumetric blend f = f_l f+ + (1 - f_l) f^eq(rho, 0) (Eq. 20) is
-//     linear, and M f^eq(rho, 0) = rho (1, -2, 1, 0, ..., 0) (Eq. 18 at u = 0),
-//     so m = f_l m+ + (1 - f_l) rho (1, -2, 1, 0, ..., 0);
+//     linear, and M f^eq(rho, 0) = rho r (Eq. 18 at u = 0), so in deviation
+//     form m - r = f_l (m+ - r) + (1 - f_l) delta_rho r;
 //   * the wall rule of Eq. 52 is linear too: m+(x_b) = m+(x_f) +
 //     m^eq(rho_f, u_b = 0) - m^eq(rho_f, u_f), and likewise for the thermal
 //     moments with their own equilibria (Eqs. 34/B2, 45/B4);
 //   * the collisions are Eq. 14 (flow, with forcing Eq. 19), Eq. 32 (PCM,
 //     source Eqs. 35-36 or App. B) and Eq. 43 (metal, Eqs. 46-47 or App. B),
-//     followed by f* = M^-1 m*, with M^-1 = M^T diag(1/|row|^2) for D2Q9.
+//     followed by f* = M^-1 m*, with M^-1 = M^T diag(1/|row|^2) for D2Q9;
+//   * the PCM enthalpy is bookkept exactly: with FP32 storage the rest
+//     population g_0 is kept as an unevaluated float-float sum (hi in the
+//     g_0 plane, lo in one extra plane), H = g_0 + sum_{i>=1} g_i is formed
+//     with error-free additions (Knuth's TwoSum, Dekker's Fast2Sum), and the
+//     post-collision rest population is the remainder g_0* = n_0* - sum_{i>=1}
+//     g_i* of the rounded moving populations, so that streaming and collision
+//     conserve the enthalpy to ~2^-48 instead of accumulating FP32 rounding
+//     in the isothermal mushy zone, where nothing damps it.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -33,7 +46,7 @@ struct StepParams {
     long long plane;     // ny * pitch
     int per_x, per_y;
     int wall_kind[4];
-    R wall_T[4], wall_H[4];
+    R wall_T[4], wall_H[4], wall_H_lo[4];
     // flow (Eqs. 3, 7, 16, 25)
     R phi, inv_phi, drag_lin, drag_forch, gbeta, T0, l0, l0sq, l1;
     R s[9];
@@ -45,6 +58,48 @@ struct StepParams {
 };
 
 enum : unsigned int { STATUS_UNSTABLE = 1u };
+
+// FP32 storage keeps the PCM rest population as a float-float pair.
+template <typename R>
+constexpr bool kComp = sizeof(R) == 4;
+
+// Error-free transformations (IEEE round-to-nearest, no contraction).
+struct FF {
+    float hi, lo;
+};
+
+__device__ __forceinline__ FF two_sum(float a, float b) {        // Knuth
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return {s, e};
+}
+
+__device__ __forceinline__ FF fast_two_sum(float a, float b) {   // Dekker, |a| >= |b|
+    const float s = __fadd_rn(a, b);
+    return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+
+__device__ __forceinline__ FF ff_add(FF a, float b) {
+    const FF s = two_sum(a.hi, b);
+    return fast_two_sum(s.hi, __fadd_rn(s.lo, a.lo));
+}
+
+__device__ __forceinline__ FF ff_add(FF a, FF b) {
+    const FF s = two_sum(a.hi, b.hi);
+    return fast_two_sum(s.hi, __fadd_rn(__fadd_rn(s.lo, a.lo), b.lo));
+}
+
+__device__ __forceinline__ FF ff_neg(FF a) { return {-a.hi, -a.lo}; }
+
+// Exact-ish sum of the moving populations v[1..Q-1].
+template <int Q>
+__device__ __forceinline__ FF ff_sum_movers(const float* v) {
+    FF acc = {v[1], 0.0f};
+#pragma unroll
+    for (int i = 2; i < Q; ++i) acc = ff_add(acc, v[i]);
+    return acc;
+}
 
 // ---------------------------------------------------------------------------
 // Transforms
@@ -121,14 +176,15 @@ __device__ __forceinline__ void inv(const R* m, R* v) {
 // Equilibrium moments
 // ---------------------------------------------------------------------------
 
-// Eq. 18 (alpha_1 = 1, alpha_2 = -3)
+// Eq. 18 (alpha_1 = 1, alpha_2 = -3) minus the rest moments r = (1, -2, 1, 0, ..., 0);
+// rho = 1 + drho.
 template <typename R>
-__device__ __forceinline__ void meq_flow(const StepParams<R>& P, R rho, R ux, R uy, R* me) {
+__device__ __forceinline__ void meq_flow_dev(const StepParams<R>& P, R rho, R drho, R ux, R uy, R* me) {
     const R ip = P.inv_phi;
-    const R uu = (ux * ux + uy * uy) * ip;
-    me[0] = rho;
-    me[1] = rho * (R(-2) + R(3) * uu);
-    me[2] = rho * (R(1) - R(3) * uu);
+    const R q = R(3) * rho * (ux * ux + uy * uy) * ip;
+    me[0] = drho;
+    me[1] = R(-2) * drho + q;
+    me[2] = drho - q;
     me[3] = rho * ux;
     me[4] = -rho * ux;
     me[5] = rho * uy;
@@ -189,9 +245,10 @@ __device__ __forceinline__ void enthalpy_state(const StepParams<R>& P, R H, R& T
 
 template <typename R, int QT, bool FLOW>
 struct NodeState {
-    R mp[FLOW ? 9 : 1];  // moments of f+ (after the wall rule)
-    R ng[QT], nh[QT];    // moments of g and h (after the wall rule)
-    R H, Tf, fl, Tm, rho, ux, uy, Gy;
+    R mp[FLOW ? 9 : 1];  // moments of f+ minus r (after the wall rule)
+    R ng[QT], nh[QT];    // moments of g and h (after the wall rule); ng[0] = H (high part)
+    R Hlo;               // low part of H (float-float bookkeeping; 0 with FP64 storage)
+    R H, Tf, fl, Tm, rho, drho, ux, uy, Gy;
 };
 
 // Pull streaming around node (xs, ys): the population along e_i comes from
@@ -247,6 +304,15 @@ __device__ __forceinline__ void pull_moments(const StepParams<R>& P, int xs, int
     }
     fwd<R, QT>(g, n.ng);
     fwd<R, QT>(h, n.nh);
+    if constexpr (kComp<R>) {
+        // H = (g_0 hi + g_0 lo) + sum of movers, without rounding loss
+        const float lo = __ldg(s + (long long)(base + 2 * QT) * pl + r0 + xs);
+        const FF H = ff_add(FF{g[0], lo}, ff_sum_movers<QT>(g));
+        n.ng[0] = H.hi;
+        n.Hlo = H.lo;
+    } else {
+        n.Hlo = R(0);
+    }
 }
 
 // Macroscopic state from the moments (Eqs. 21, 23-25, 37-39, 48, 7).
@@ -256,7 +322,8 @@ __device__ __forceinline__ void macro(const StepParams<R>& P, NodeState<R, QT, F
     enthalpy_state(P, n.H, n.Tf, n.fl);
     n.Tm = n.nh[0] * P.inv_c_pm;
     if constexpr (FLOW) {
-        n.rho = n.mp[0];
+        n.drho = n.mp[0];
+        n.rho = R(1) + n.drho;
         n.Gy = P.gbeta * (n.Tf - P.T0) * n.fl;
         if (wall) {
             n.ux = R(0);
@@ -272,6 +339,7 @@ __device__ __forceinline__ void macro(const StepParams<R>& P, NodeState<R, QT, F
             n.uy = vy * den;
         }
     } else {
+        n.drho = R(0);
         n.rho = R(1);
         n.ux = R(0);
         n.uy = R(0);
@@ -306,16 +374,26 @@ __device__ __forceinline__ void node_state(const StepParams<R>& P, int x, int y,
     }
     R a[QT], b[QT];
     if constexpr (FLOW) {
-        R ea[9], eb[9];
-        meq_flow(P, n.rho, R(0), R(0), ea);
-        meq_flow(P, n.rho, n.ux, n.uy, eb);
-#pragma unroll
-        for (int k = 0; k < 9; ++k) n.mp[k] += ea[k] - eb[k];
+        // m^eq(rho_f, 0) - m^eq(rho_f, u_f), written out so that the rho r parts cancel exactly
+        const R rho = n.rho, ip = P.inv_phi;
+        const R q = R(3) * rho * (n.ux * n.ux + n.uy * n.uy) * ip;
+        n.mp[1] -= q;
+        n.mp[2] += q;
+        n.mp[3] -= rho * n.ux;
+        n.mp[4] += rho * n.ux;
+        n.mp[5] -= rho * n.uy;
+        n.mp[6] += rho * n.uy;
+        n.mp[7] -= rho * (n.ux * n.ux - n.uy * n.uy) * ip;
+        n.mp[8] -= rho * n.ux * n.uy * ip;
     }
     neq_pcm<R, QT>(P, Hb, Tb, R(0), R(0), a);
     neq_pcm<R, QT>(P, n.H, n.Tf, n.ux, n.uy, b);
 #pragma unroll
-    for (int k = 0; k < QT; ++k) n.ng[k] += a[k] - b[k];
+    for (int k = 1; k < QT; ++k) n.ng[k] += a[k] - b[k];
+    if (P.wall_kind[side] == 0) {   // n_0 = H_b exactly (adiabatic: n_0 = H(x_f), unchanged)
+        n.ng[0] = P.wall_H[side];
+        n.Hlo = P.wall_H_lo[side];
+    }
     neq_metal<R, QT>(P, Tmb, a);
     neq_metal<R, QT>(P, n.Tm, b);
 #pragma unroll
@@ -348,16 +426,16 @@ __global__ void __launch_bounds__(256) fused_step(const __grid_constant__ StepPa
         const R drag = P.drag_lin + P.drag_forch * um;
         const R Fx = -drag * n.ux;
         const R Fy = -drag * n.uy + P.phi * n.Gy;
-        // blended moments (Eq. 20 in moment space)
+        // blended moments (Eq. 20 in moment space, deviation form)
         R m[9];
-        const R sol = (R(1) - n.fl) * n.rho;
+        const R sol = (R(1) - n.fl) * n.drho;
 #pragma unroll
         for (int k = 0; k < 9; ++k) m[k] = n.fl * n.mp[k];
         m[0] += sol;
         m[1] -= R(2) * sol;
         m[2] += sol;
         R me[9];
-        meq_flow(P, n.rho, n.ux, n.uy, me);
+        meq_flow_dev(P, n.rho, n.drho, n.ux, n.uy, me);
         const R ip = P.inv_phi, rho = n.rho;
         const R uF = n.ux * Fx + n.uy * Fy;
         const R S[9] = {R(0), rho * R(6) * uF * ip, -rho * R(6) * uF * ip, rho * Fx, -rho * Fx,
@@ -383,16 +461,31 @@ __global__ void __launch_bounds__(256) fused_step(const __grid_constant__ StepPa
         R ne[QT];
         neq_pcm<R, QT>(P, n.H, n.Tf, n.ux, n.uy, ne);
 #pragma unroll
-        for (int k = 0; k < QT; ++k) n.ng[k] -= P.zeta[k] * (n.ng[k] - ne[k]);
+        for (int k = 1; k < QT; ++k) n.ng[k] -= P.zeta[k] * (n.ng[k] - ne[k]);
         if constexpr (QT == 9) {
-            n.ng[0] += S_pcm; n.ng[1] -= R(2) * S_pcm; n.ng[2] += S_pcm;
+            n.ng[1] -= R(2) * S_pcm; n.ng[2] += S_pcm;
         } else {
-            n.ng[0] += S_pcm; n.ng[3] += P.varpi * S_pcm;
+            n.ng[3] += P.varpi * S_pcm;
         }
+        // n_0* = H + S_PCM (n_0 is conserved up to the source, Eq. 32)
         R g[QT];
-        inv<R, QT>(n.ng, g);
+        if constexpr (kComp<R>) {
+            const FF n0 = ff_add(FF{n.ng[0], n.Hlo}, S_pcm);
+            n.ng[0] = n0.hi;
+            inv<R, QT>(n.ng, g);
+            const FF g0 = ff_add(n0, ff_neg(ff_sum_movers<QT>(g)));   // rest = exact remainder
+            d[(base + 0) * pl + o] = g0.hi;
+            d[(long long)(base + 2 * QT) * pl + o] = g0.lo;
+        } else {
+            n.ng[0] += S_pcm;
+            inv<R, QT>(n.ng, g);
+            R sm = g[1];
 #pragma unroll
-        for (int k = 0; k < QT; ++k) d[(base + k) * pl + o] = g[k];
+            for (int k = 2; k < QT; ++k) sm += g[k];
+            d[(base + 0) * pl + o] = n.ng[0] - sm;
+        }
+#pragma unroll
+        for (int k = 1; k < QT; ++k) d[(base + k) * pl + o] = g[k];
     }
     {
         R ne[QT];
@@ -460,8 +553,8 @@ __global__ void __launch_bounds__(256) diag_partial(const __grid_constant__ Step
         bool wall;
         node_state<R, QT, FLOW>(P, x, y, n, wall);
         v[0] = (double)n.fl;
-        v[1] = C.phi * C.rho_l * (double)n.H + (1.0 - C.phi) * C.rho_m * C.c_pm * (double)n.Tm;
-        v[2] = (double)n.rho;
+        v[1] = C.phi * C.rho_l * ((double)n.H + (double)n.Hlo) + (1.0 - C.phi) * C.rho_m * C.c_pm * (double)n.Tm;
+        v[2] = 1.0 + (double)n.drho;
         if (x == 0 && C.left_wall && P.nx >= 3) {
             NodeState<R, QT, FLOW> n1, n2;
             bool w1, w2;

@@ -15,7 +15,7 @@ inline dim3 grid_for(int nx, int ny) {
 
 template <typename R>
 struct InitVals {
-    R v[27];
+    R v[28];   // one value per plane: 9 flow + 9 PCM + 9 metal + low part of g_0
 };
 
 template <typename R>

@@ -90,9 +90,9 @@ def lib() -> ctypes.CDLL:
         L.lbm_fields.restype = ctypes.c_int
         L.lbm_diag.argtypes = [vp] + [ctypes.POINTER(ctypes.c_double)] * 4
         L.lbm_diag.restype = ctypes.c_int
-        L.lbm_get_state.argtypes = [vp, vp, vp, vp, vp, i32]
+        L.lbm_get_state.argtypes = [vp, vp, vp, vp, vp, vp, i32]
         L.lbm_get_state.restype = ctypes.c_int
-        L.lbm_set_state.argtypes = [vp, vp, vp, vp, vp, i32]
+        L.lbm_set_state.argtypes = [vp, vp, vp, vp, vp, vp, i32]
         L.lbm_set_state.restype = ctypes.c_int
         L.lbm_status.argtypes = [vp]
         L.lbm_status.restype = ctypes.c_int
@@ -270,18 +270,23 @@ class Solver:
         return _derived_dict(d)
 
     # -- raw state ----------------------------------------------------------
-    def get_state(self):
-        """(f, g, h, dT) as numpy arrays [q][ny][nx] / [ny][nx] (f is None when the flow lattice is off)."""
+    def get_state(self, with_lo: bool = False):
+        """(f, g, h, dT) as numpy arrays [q][ny][nx] / [ny][nx] (f is None when the
+        flow lattice is off).  f holds the deviations f_i - w_i from the rest
+        equilibrium, the library's storage form; g and h are the populations.
+        with_lo=True appends the low part of the FP32 PCM rest population
+        (None for FP64 runs), so that the tuple restores the state bit for bit."""
         f = np.empty((9, self.ny, self.nx), self.np_dtype) if self.flow else None
         g = np.empty((self.qt, self.ny, self.nx), self.np_dtype)
         h = np.empty((self.qt, self.ny, self.nx), self.np_dtype)
         dT = np.empty((self.ny, self.nx), self.np_dtype)
+        lo = np.empty((self.ny, self.nx), self.np_dtype) if self.np_dtype == np.float32 else None
         _check(lib().lbm_get_state(self._h, None if f is None else f.ctypes.data, g.ctypes.data, h.ctypes.data,
-                                   dT.ctypes.data, 0), "lbm_get_state")
-        return f, g, h, dT
+                                   dT.ctypes.data, None if lo is None else lo.ctypes.data, 0), "lbm_get_state")
+        return (f, g, h, dT, lo) if with_lo else (f, g, h, dT)
 
-    def set_state(self, f, g, h, dT):
-        conv = [None if a is None else np.ascontiguousarray(a, dtype=self.np_dtype) for a in (f, g, h, dT)]
+    def set_state(self, f, g, h, dT, g0_lo=None):
+        conv = [None if a is None else np.ascontiguousarray(a, dtype=self.np_dtype) for a in (f, g, h, dT, g0_lo)]
         if self.flow and conv[0] is None:
             raise ValueError("flow populations are required when the flow lattice is on")
         ptrs = [None if a is None else a.ctypes.data for a in conv]

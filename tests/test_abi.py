@@ -101,7 +101,7 @@ def test_size_limits(lbm):
 def test_state_bytes_account_for_both_copies(lbm):
     p = inputs.cavity(2048)
     b = lbm.state_bytes(p)
-    per_node = (2 * (9 + 5 + 5) + 1) * 4
+    per_node = (2 * (9 + 5 + 5 + 1) + 1) * 4     # two copies of 19 populations + the low part of g_0, history
     assert per_node * 2048 * 2048 <= b < per_node * 2048 * 2048 * 1.01
 
 
