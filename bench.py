@@ -30,8 +30,10 @@ scaling); no data crosses ranks, only the timing maximum.
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -53,6 +55,24 @@ def bytes_per_update(qt: int, flow: int, elem: int) -> int:
     once, and with FP32 storage the low part of the PCM rest population."""
     planes = (9 if flow else 0) + 2 * qt + (1 if elem == 4 else 0)
     return planes * elem * 2 + 2 * elem
+
+
+def measured_traffic(n: int):
+    """DRAM bytes per launch of the fused step from the committed ncu summary,
+    or None when the kernel sources changed since that capture (or for
+    another grid size)."""
+    prof = ROOT / "profiles" / "fused_step_cavity2048_fp32.md"
+    if n != 2048 or not prof.exists():
+        return None
+    text = prof.read_text()
+    want = re.search(r"kernel_sources_sha256_16: ([0-9a-f]+)", text)
+    val = re.search(r"traffic_bytes_per_launch: (\d+)", text)
+    if not want or not val:
+        return None
+    h = hashlib.sha256()
+    for name in ("lbm_kernels.cuh", "lbm_launch.cuh", "lbm_kernels_f32.cu"):
+        h.update((ROOT / "paper_1701_00702_gb300" / "csrc" / name).read_bytes())
+    return int(val.group(1)) if h.hexdigest()[:16] == want.group(1) else None
 
 
 def parse():
@@ -314,7 +334,7 @@ def main():
             nodes = pr["nx"] * pr["ny"]
             achieved = bpu * nodes / (ms / 1e3) / 1e9
             roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                    "frac": achieved / peak, "traffic": None,
+                    "frac": achieved / peak, "traffic": measured_traffic(pr["nx"]),
                     "kernel": "fused_step<float, Q_T=5, flow>",
                     "workload": f"square-cavity melting {pr['nx']}x{pr['ny']} FP32 (state {lbm.state_bytes(pr) / 2**30:.2f} GiB)",
                     "bytes_per_update": bpu, "units_per_launch": nodes,
