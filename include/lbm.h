@@ -47,6 +47,7 @@ extern "C" {
 #define LBM_ERR_UNSTABLE  (-5)  /* the kernel saw a non-finite state or |u| > 0.3 (sticky) */
 #define LBM_ERR_TIMEOUT   (-6)  /* a bounded device wait expired */
 #define LBM_ERR_STATE     (-7)  /* handle already failed, or call out of order */
+#define LBM_ERR_TOO_LARGE (-8)  /* grid exceeds the static scratch of lbm_diag_fields_noalloc */
 
 /* ---- storage precision (lbm_params.precision) ---- */
 #define LBM_F64 0
@@ -199,6 +200,46 @@ int lbm_destroy(lbm_handle* h);
 
 /* Static string naming a status code. */
 const char* lbm_strerror(int code);
+
+/*
+ * Allocation-free diagnostics (the paper has no counterpart; this entry
+ * point exists for callers that cannot allocate device memory).
+ *
+ * Who needs it: code whose device memory all belongs to another allocator (a
+ * framework's memory pool, or a serving loop that has already handed out its
+ * HBM budget) and latency-critical paths where cudaMalloc/cudaFree would
+ * synchronise the device.  The call computes the same four FP64 quantities as
+ * lbm_diag -- out[0] melt fraction, out[1] hot-wall Nusselt number, out[2]
+ * total enthalpy, out[3] mass -- from field arrays the caller already holds
+ * (for instance written by lbm_fields with dst_on_device = 1), without a handle.
+ *
+ * Arguments: p describes the run (as for lbm_create); T_f, T_s, f_l, rho and
+ * H_f are device arrays [ny][nx] of the run's element type (LBM_FIELD_* of
+ * the same names); out is a device array of 4 doubles; cuda_stream is a
+ * cudaStream_t (NULL = legacy default stream).  The work is enqueued on that
+ * stream and the call returns without synchronising; the caller keeps
+ * ownership of every buffer.
+ *
+ * Memory: no cudaMalloc, cudaFree or other allocating call is made.  The
+ * per-block FP64 partial sums live in one file-scope device array of
+ * 256 KiB (8192 blocks x 4 doubles) that every GPU loading this library
+ * holds until the process exits; grids above LBM_DIAG_NOALLOC_MAX_NODES nodes
+ * return LBM_ERR_TOO_LARGE.  Each call writes every partial it later reads,
+ * so nothing has to start at zero.  All calls share that one array: calls
+ * whose kernels overlap on the GPU (different streams, or different host
+ * threads on the same device) race and give wrong sums; serialise them.
+ *
+ * Set-up: the first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current) and caches it; make that
+ * first call before any stream capture.
+ *
+ * Errors: LBM_ERR_ARG for a null pointer or invalid p (LBM_ERR_STABILITY as
+ * in lbm_derive), LBM_ERR_TOO_LARGE as above, LBM_ERR_CUDA if the symbol
+ * lookup or a launch fails.
+ */
+#define LBM_DIAG_NOALLOC_MAX_NODES 67108864   /* 8192 x 8192 */
+int lbm_diag_fields_noalloc(const lbm_params* p, const void* T_f, const void* T_s, const void* f_l,
+                            const void* rho, const void* H_f, double* out, void* cuda_stream);
 
 #ifdef __cplusplus
 }

@@ -611,6 +611,7 @@ const char* lbm_strerror(int code) {
         case LBM_ERR_UNSTABLE: return "non-finite or runaway state detected on the device";
         case LBM_ERR_TIMEOUT: return "bounded device wait expired";
         case LBM_ERR_STATE: return "handle in a failed state or call out of order";
+        case LBM_ERR_TOO_LARGE: return "grid larger than the static scratch of the allocation-free diagnostics";
         default: return "unknown status code";
     }
 }

@@ -19,7 +19,7 @@ LIB_PATH = _PKG / "_build" / "liblbm_gb300.so"
 LBM_OK = 0
 ERRORS = {
     -1: "LBM_ERR_ARG", -2: "LBM_ERR_STABILITY", -3: "LBM_ERR_OOM", -4: "LBM_ERR_CUDA",
-    -5: "LBM_ERR_UNSTABLE", -6: "LBM_ERR_TIMEOUT", -7: "LBM_ERR_STATE",
+    -5: "LBM_ERR_UNSTABLE", -6: "LBM_ERR_TIMEOUT", -7: "LBM_ERR_STATE", -8: "LBM_ERR_TOO_LARGE",
 }
 F64, F32 = 0, 1
 FIELDS = ("T_f", "T_s", "f_l", "u_x", "u_y", "rho", "H_f")
@@ -104,6 +104,8 @@ def lib() -> ctypes.CDLL:
         L.lbm_destroy.restype = ctypes.c_int
         L.lbm_strerror.argtypes = [ctypes.c_int]
         L.lbm_strerror.restype = ctypes.c_char_p
+        L.lbm_diag_fields_noalloc.argtypes = [pp, vp, vp, vp, vp, vp, vp, vp]
+        L.lbm_diag_fields_noalloc.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -159,6 +161,19 @@ def derive(p: dict) -> dict:
 
 def state_bytes(p: dict) -> int:
     return int(lib().lbm_state_bytes(ctypes.byref(to_struct(p))))
+
+
+def diag_fields_noalloc(params: dict, fields: dict, out, stream=None) -> None:
+    """Enqueues the allocation-free diagnostics of caller-owned device fields
+    (torch tensors keyed T_f, T_s, f_l, rho, H_f) into ``out`` (a CUDA float64
+    tensor of 4 elements): melt fraction, hot-wall Nusselt number, enthalpy,
+    mass.  Only pointers are passed; the library allocates nothing."""
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    ptrs = [ctypes.c_void_p(fields[k].data_ptr()) for k in ("T_f", "T_s", "f_l", "rho", "H_f")]
+    rc = lib().lbm_diag_fields_noalloc(ctypes.byref(to_struct(params)), *ptrs, ctypes.c_void_p(out.data_ptr()),
+                                       ctypes.c_void_p(s.cuda_stream))
+    _check(rc, "lbm_diag_fields_noalloc")
 
 
 class TorchAllocator:
