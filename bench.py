@@ -49,12 +49,21 @@ UNIT = "MLUPS"
 L2_FLUSH_BYTES = 512 << 20
 
 
-def bytes_per_update(qt: int, flow: int, elem: int) -> int:
-    """Algorithmic HBM bytes per node update of the storage format: every
-    population read and written once, the exchange history read and written
-    once, and with FP32 storage the low part of the PCM rest population."""
-    planes = (9 if flow else 0) + 2 * qt + (1 if elem == 4 else 0)
-    return planes * elem * 2 + 2 * elem
+PREC_NAMES = {0: "f64", 1: "f32", 2: "f16", 3: "bf16"}
+
+
+def bytes_per_update(qt: int, flow: int, precision: int) -> int:
+    """Algorithmic HBM bytes per node update of a storage form: every stored
+    value read and written once.  FP64/FP32: all populations plus the exchange
+    history (FP32 adds the low part of the PCM rest population); FP16/BF16:
+    16-bit flow deviations and moving thermal populations, FP32 thermal rest
+    populations and history."""
+    fl = 9 if flow else 0
+    if precision == 0:
+        return (fl + 2 * qt + 1) * 8 * 2
+    if precision == 1:
+        return (fl + 2 * qt + 1 + 1) * 4 * 2
+    return ((fl + 2 * (qt - 1)) * 2 + 2 * 4 + 4) * 2
 
 
 def measured_traffic(n: int):
@@ -82,6 +91,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=256, help="cavity side")
+    ap.add_argument("--precision", default="f32", choices=["f64", "f32", "f16", "bf16"],
+                    help="storage form of the headline run")
     ap.add_argument("--lb-steps", type=int, default=2000, help="LB time steps per benchmark step")
     ap.add_argument("--roofline-n", type=int, default=2048)
     ap.add_argument("--no-e2e", action="store_true")
@@ -98,7 +109,7 @@ def dist_env():
 
 def workload_config(args, p, chunk):
     return {
-        "workload": f"square-cavity melting with natural convection {p['nx']}x{p['ny']} FP32",
+        "workload": f"square-cavity melting with natural convection {p['nx']}x{p['ny']} {PREC_NAMES[p['precision']].upper()}",
         "grid": [p["nx"], p["ny"]],
         "lattices": "D2Q9 flow + D2Q5 PCM + D2Q5 metal",
         "Ra": p["Ra"], "Pr": p["Pr"], "Da": p["Da"], "porosity": p["porosity"], "Ste": p["Ste"],
@@ -236,9 +247,10 @@ def main():
     dev = torch.device("cuda", local)
     stream = torch.cuda.Stream(dev)
     chunk = args.lb_steps
-    p = inputs.cavity(args.n, precision=1)
+    prec = {"f64": 0, "f32": 1, "f16": 2, "bf16": 3}[args.precision]
+    p = inputs.cavity(args.n, precision=prec)
     cells = p["nx"] * p["ny"]
-    bpu = bytes_per_update(p["thermal_q"], p["flow"], 4)
+    bpu = bytes_per_update(p["thermal_q"], p["flow"], p["precision"])
     props = torch.cuda.get_device_properties(dev)
     bus = getattr(props, "pci_bus_id", None)
     bus_id = None
@@ -281,11 +293,12 @@ def main():
         e2e = None
         if not args.no_e2e:
             f0, g0, h0, d0 = s.get_state()
-            pin = {k: torch.empty(a.shape, dtype=torch.float32, pin_memory=True).numpy()
+            tdt = torch.float64 if prec == 0 else torch.float32
+            pin = {k: torch.empty(a.shape, dtype=tdt, pin_memory=True).numpy()
                    for k, a in (("f", f0), ("g", g0), ("h", h0), ("dT", d0))}
             for k, a in (("f", f0), ("g", g0), ("h", h0), ("dT", d0)):
                 pin[k][...] = a
-            outs = {name: torch.empty((p["ny"], p["nx"]), dtype=torch.float32, pin_memory=True).numpy()
+            outs = {name: torch.empty((p["ny"], p["nx"]), dtype=tdt, pin_memory=True).numpy()
                     for name in ("T_f", "T_s", "f_l", "u_x", "u_y")}
             h2d = sum(a.nbytes for a in pin.values())
             d2h = sum(a.nbytes for a in outs.values())
@@ -309,6 +322,24 @@ def main():
                    "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
         s.close()
         del flush
+
+        def time_form(prec: int, n: int, per: int, reps: int = 3):
+            pf = inputs.cavity(n, precision=prec)
+            sf = lbm.Solver(pf, stream=stream)
+            sf.step(64)
+            stream.synchronize()
+            e = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+            for a, b in e:
+                a.record(stream)
+                sf.step(per)
+                b.record(stream)
+            stream.synchronize()
+            ms = sum(a.elapsed_time(b) for a, b in e) / (reps * per)
+            rc = sf.status()
+            sf.close()
+            if rc != 0:
+                raise SystemExit(f"form {PREC_NAMES[prec]} {n}^2 reported an unstable state")
+            return ms
 
         # roofline: the same kernel on a state far larger than L2
         roof = None
@@ -341,6 +372,19 @@ def main():
                     "mlups": nodes / (ms / 1e3) / 1e6, "avg_launch_us": ms * 1e3,
                     "peak_source": "measured" if peaks else "fallback"}
 
+        # every storage form of the same step, on the L2-resident and the HBM-bound cavity
+        forms = []
+        if args.roofline_n > 0:
+            peak = roof["peak"]
+            for prec in (1, 2, 3):
+                for n, per in ((args.roofline_n, 128), (args.n, 2048)):
+                    ms = time_form(prec, n, per)
+                    b = bytes_per_update(5, 1, prec)
+                    gbs = b * n * n / (ms / 1e3) / 1e9
+                    forms.append({"precision": PREC_NAMES[prec], "grid": n, "us_per_step": ms * 1e3,
+                                  "mlups": n * n / (ms / 1e3) / 1e6, "bytes_per_update": b,
+                                  "gbs_algorithmic": gbs, "frac_of_measured_hbm": gbs / peak})
+
     if rank != 0:
         return
     cpu = None
@@ -349,12 +393,13 @@ def main():
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None, "dtype": PREC_NAMES[prec], "data": "synthetic",
         "config": workload_config(args, p, chunk),
         "roofline": roof,
         "l2_resident": {"avg_launch_us": launch_ms_small * 1e3,
                         "gbs_algorithmic": bpu * cells / (launch_ms_small / 1e3) / 1e9,
                         "note": "256x256 state (10 MB) is L2-resident; launch-to-launch time inside CUDA graphs"},
+        "forms": forms if args.roofline_n > 0 else None,
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": args.steps * chunk,

@@ -20,7 +20,7 @@
  *  - Array layout at the boundary: every field is row-major [ny][nx] (x fastest);
  *    distribution arrays are [q][ny][nx] with the velocity order of Eq. 11
  *    (D2Q9: rest, +x, +y, -x, -y, (+,+), (-,+), (-,-), (+,-); D2Q5: the first
- *    five).  Element type is double for LBM_F64 runs and float for LBM_F32 runs.
+ *    five).  Element type is double for LBM_F64 runs and float for the others.
  *  - Status: every int-returning call returns LBM_OK (0) or a negative
  *    LBM_ERR_* code.  lbm_strerror() names it.  No call aborts the process.
  *  - Streams: work is enqueued on the cudaStream_t given at creation; calls
@@ -49,9 +49,20 @@ extern "C" {
 #define LBM_ERR_STATE     (-7)  /* handle already failed, or call out of order */
 #define LBM_ERR_TOO_LARGE (-8)  /* grid exceeds the static scratch of lbm_diag_fields_noalloc */
 
-/* ---- storage precision (lbm_params.precision) ---- */
-#define LBM_F64 0
-#define LBM_F32 1
+/* ---- storage precision (lbm_params.precision) ----
+ * LBM_F64   all populations FP64, FP64 arithmetic.
+ * LBM_F32   all populations FP32, FP32 arithmetic; the PCM rest population is
+ *           kept as a float-float pair (one extra FP32 plane) so that the
+ *           enthalpy is conserved exactly.
+ * LBM_F16, LBM_BF16  flow deviations f_i - w_i and the moving thermal
+ *           populations in FP16 / BF16, the two thermal rest populations and
+ *           the exchange history in FP32, FP32 arithmetic.
+ * Fields and state arrays at the boundary are double for LBM_F64 and float
+ * for the other three. */
+#define LBM_F64  0
+#define LBM_F32  1
+#define LBM_F16  2
+#define LBM_BF16 3
 
 /* ---- wall kinds (lbm_params.wall_kind[side]) ---- */
 #define LBM_WALL_DIRICHLET 0    /* T_f = T_m = wall_T[side] on the wall nodes */
@@ -83,7 +94,7 @@ extern "C" {
 typedef struct lbm_params {
     int32_t nx, ny;            /* grid nodes; >= 3 in a direction that has walls */
     int32_t thermal_q;         /* 5 (App. B) or 9 (Sec. III B) */
-    int32_t precision;         /* LBM_F64 or LBM_F32 */
+    int32_t precision;         /* LBM_F64, LBM_F32, LBM_F16 or LBM_BF16 */
     int32_t flow;              /* 1: flow lattice on; 0: u = 0 everywhere (Sec. IV A) */
     int32_t periodic_x;        /* 1: periodic in x; 0: wall nodes at x = 0 and x = nx-1 */
     int32_t periodic_y;        /* 1: periodic in y; 0: wall nodes at y = 0 and y = ny-1 */
@@ -179,12 +190,26 @@ int lbm_diag(lbm_handle* h, double* melt_frac, double* nu_hot, double* enthalpy,
  * (w = 4/9, 1/9 x4, 1/36 x4); g and hm are the populations themselves.
  * With LBM_F32 storage the PCM rest population is the float-float sum
  * g[0] + g0_lo ([ny][nx]); g0_lo may be NULL (get: not copied; set: taken
- * as zero when g is given) and is ignored for LBM_F64 runs.  Any other
+ * as zero when g is given) and is ignored for the other modes.  LBM_F16 and
+ * LBM_BF16 runs exchange the populations as float arrays: reading decodes the
+ * stored form exactly, writing re-encodes with one 16-bit rounding per moving
+ * population (use lbm_save / lbm_load for a bit-exact round trip).  Any other
  * pointer may be NULL to skip that array.  on_device selects device or host
  * pointers.  Synchronises. */
 int lbm_get_state(lbm_handle* h, void* f, void* g, void* hm, void* dT, void* g0_lo, int32_t on_device);
 int lbm_set_state(lbm_handle* h, const void* f, const void* g, const void* hm, const void* dT,
                   const void* g0_lo, int32_t on_device);
+
+/* Raw checkpoints: the current state copy, the exchange history and the step
+ * count, byte for byte, behind a 64-byte header that records the run's
+ * layout.  lbm_load accepts only a checkpoint of a run with the same grid,
+ * lattices, precision and flow flag (LBM_ERR_ARG otherwise) and restores it
+ * bit for bit in every storage mode; the sticky status is left unchanged.
+ * dst/src hold lbm_checkpoint_bytes(h) bytes on the device (on_device = 1)
+ * or the host.  Both synchronise. */
+int64_t lbm_checkpoint_bytes(const lbm_handle* h);
+int lbm_save(lbm_handle* h, void* dst, int32_t on_device);
+int lbm_load(lbm_handle* h, const void* src, int32_t on_device);
 
 /* Synchronises the handle's stream and returns the sticky status. */
 int lbm_status(lbm_handle* h);

@@ -17,7 +17,7 @@ ROOT = PKG.parent
 CSRC = PKG / "csrc"
 OUT = PKG / "_build"
 LIB = OUT / "liblbm_gb300.so"
-SOURCES = ["lbm_api.cu", "lbm_kernels_f32.cu", "lbm_kernels_f64.cu", "lbm_noalloc.cu"]
+SOURCES = ["lbm_api.cu", "lbm_kernels_f32.cu", "lbm_kernels_f64.cu", "lbm_kernels_f16.cu", "lbm_noalloc.cu"]
 GENCODE = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -41,7 +41,7 @@ def build(force: bool = False, verbose_ptxas: bool = False) -> Path:
         return LIB
     OUT.mkdir(exist_ok=True)
     cc = nvcc()
-    common = GENCODE + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
+    common = GENCODE + ["-O3", "-lineinfo", "-std=c++20", "-Xcompiler", "-fPIC",
                         "-I", str(ROOT / "include"), "-I", str(CSRC)]
     if verbose_ptxas or os.environ.get("LBM_PTXAS_VERBOSE"):
         common += ["-Xptxas", "-v"]

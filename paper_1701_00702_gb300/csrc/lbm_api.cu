@@ -35,7 +35,8 @@ int derive_impl(const lbm_params* pp, lbm_derived* out) {
     if (!p.periodic_x && p.nx < 3) return LBM_ERR_ARG;
     if (!p.periodic_y && p.ny < 3) return LBM_ERR_ARG;
     if (p.thermal_q != 5 && p.thermal_q != 9) return LBM_ERR_ARG;
-    if (p.precision != LBM_F64 && p.precision != LBM_F32) return LBM_ERR_ARG;
+    if (p.precision != LBM_F64 && p.precision != LBM_F32 && p.precision != LBM_F16 && p.precision != LBM_BF16)
+        return LBM_ERR_ARG;
     if (p.flow != 0 && p.flow != 1) return LBM_ERR_ARG;
     for (int s = 0; s < 4; ++s) {
         if (p.wall_kind[s] != LBM_WALL_DIRICHLET && p.wall_kind[s] != LBM_WALL_ADIABATIC) return LBM_ERR_ARG;
@@ -120,25 +121,36 @@ int derive_impl(const lbm_params* pp, lbm_derived* out) {
 }
 
 struct Layout {
-    int pitch, nplanes;
+    int pitch, nplanes, nwide;
     long long plane;
-    size_t elem, buf_bytes, dT_bytes, off_buf1, off_dT, off_status, off_scratch, off_out, total;
+    size_t elem;      // bytes of one bulk element (8, 4 or 2)
+    size_t relem;     // bytes of one arithmetic element (8 or 4): history, fields, state I/O
+    size_t copy_bytes, wide_off, dT_bytes, off_buf1, off_dT, off_status, off_scratch, off_out, total;
     int nblocks;
 };
 
+bool split_mode(int precision) { return precision == LBM_F16 || precision == LBM_BF16; }
+
 Layout layout_of(const lbm_params& p) {
     Layout L;
-    L.elem = p.precision == LBM_F64 ? 8 : 4;
+    const bool split = split_mode(p.precision);
+    L.elem = p.precision == LBM_F64 ? 8 : (split ? 2 : 4);
+    L.relem = p.precision == LBM_F64 ? 8 : 4;
     const int align_elems = (int)(128 / L.elem);
     L.pitch = (p.nx + align_elems - 1) / align_elems * align_elems;
     L.plane = (long long)L.pitch * p.ny;
-    // flow (9, deviations), PCM (Q), metal (Q), and with FP32 storage the low part of g_0
-    L.nplanes = (p.flow ? 9 : 0) + 2 * p.thermal_q + (p.precision == LBM_F32 ? 1 : 0);
-    L.buf_bytes = align_up((size_t)L.nplanes * (size_t)L.plane * L.elem);
-    L.dT_bytes = align_up((size_t)L.plane * L.elem);
+    // bulk planes: flow (9, deviations), PCM and metal populations; FP32 adds the low
+    // part of the PCM rest population; 16-bit modes keep both rest populations in
+    // two FP32 "wide" planes after the bulk planes of each copy
+    const int fb = p.flow ? 9 : 0;
+    L.nplanes = split ? fb + 2 * (p.thermal_q - 1) : fb + 2 * p.thermal_q + (p.precision == LBM_F32 ? 1 : 0);
+    L.nwide = split ? 2 : 0;
+    L.wide_off = align_up((size_t)L.nplanes * (size_t)L.plane * L.elem);
+    L.copy_bytes = L.wide_off + align_up((size_t)L.nwide * (size_t)L.plane * 4);
+    L.dT_bytes = align_up((size_t)L.plane * L.relem);
     L.nblocks = lbmk::diag_blocks(p.nx, p.ny);
-    L.off_buf1 = L.buf_bytes;
-    L.off_dT = 2 * L.buf_bytes;
+    L.off_buf1 = L.copy_bytes;
+    L.off_dT = 2 * L.copy_bytes;
     L.off_status = L.off_dT + L.dT_bytes;
     L.off_scratch = L.off_status + kAlign;
     L.off_out = L.off_scratch + align_up((size_t)L.nblocks * 4 * sizeof(double));
@@ -193,8 +205,17 @@ lbmk::StepParams<R> make_params(const lbm_handle* h, int from) {
     const lbm_derived& d = h->d;
     lbmk::StepParams<R> P;
     std::memset(&P, 0, sizeof P);
-    P.src = static_cast<const R*>(h->buf[from]);
-    P.dst = static_cast<R*>(h->buf[1 - from]);
+    char* cur = static_cast<char*>(h->buf[from]);
+    char* nxt = static_cast<char*>(h->buf[1 - from]);
+    const size_t pb = (size_t)h->L.plane * h->L.elem;
+    for (int q = 0; q < h->L.nplanes; ++q) {
+        P.src[q] = cur + q * pb;
+        P.dst[q] = nxt + q * pb;
+    }
+    for (int w = 0; w < h->L.nwide; ++w) {
+        P.src[h->L.nplanes + w] = cur + h->L.wide_off + (size_t)w * h->L.plane * 4;
+        P.dst[h->L.nplanes + w] = nxt + h->L.wide_off + (size_t)w * h->L.plane * 4;
+    }
     P.dT = static_cast<R*>(h->dT);
     P.status = h->status;
     P.nx = p.nx;
@@ -206,8 +227,25 @@ lbmk::StepParams<R> make_params(const lbm_handle* h, int from) {
     for (int s = 0; s < 4; ++s) {
         P.wall_kind[s] = p.wall_kind[s];
         P.wall_T[s] = (R)p.wall_T[s];
+        P.wall_T_lo[s] = (R)(p.wall_T[s] - (double)(R)p.wall_T[s]);
         P.wall_H[s] = (R)d.H_wall[s];
         P.wall_H_lo[s] = (R)(d.H_wall[s] - (double)(R)d.H_wall[s]);
+    }
+    // FP16 keeps flow deviations (|f_i - w_i| < 1 while |u| < 0.3) in its normal range
+    P.fscale = p.precision == LBM_F16 ? (R)1024.0 : (R)1.0;
+    P.finv = (R)1.0 / P.fscale;
+    {   // references of the 16-bit moving thermal populations (equilibria of Eqs. 40, 49, B3, B5 at u = 0)
+        const int Q = p.thermal_q;
+        const double om = Q == 9 ? 5.0 / 9.0 : p.varpi;
+        const double w9[9] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36};
+        for (int k = 0; k < 9; ++k) P.w_move[k] = (R)(Q == 9 ? w9[k] : 0.25 * p.varpi);
+        const double g0fs = d.H_fs - om * d.c_fref * p.T_solidus, g0fl = d.H_fl - om * d.c_fref * p.T_liquidus;
+        P.g0_fs = (R)g0fs;
+        P.g0_fl = (R)g0fl;
+        P.tg_solid = (R)(1.0 / (1.0 - om * d.c_fref));
+        P.tg_liquid = (R)(1.0 / (1.0 - om * d.c_fref));
+        P.tg_mushy = (R)((p.T_liquidus - p.T_solidus) / (g0fl - g0fs));
+        P.kappa_m = (R)(d.c_mref / (1.0 - om * d.c_mref));
     }
     const double phi = p.porosity;
     P.phi = (R)phi;
@@ -251,13 +289,14 @@ int cuda_fail(lbm_handle* h) {
     return LBM_ERR_CUDA;
 }
 
-template <typename R>
-cudaError_t enqueue_step(lbm_handle* h, int from, cudaStream_t s) {
-    return lbmk::launch_step<R>(make_params<R>(h, from), h->p.thermal_q, h->p.flow, s);
-}
-
 cudaError_t enqueue_one(lbm_handle* h, int from, cudaStream_t s) {
-    return h->p.precision == LBM_F64 ? enqueue_step<double>(h, from, s) : enqueue_step<float>(h, from, s);
+    const int q = h->p.thermal_q, fl = h->p.flow;
+    switch (h->p.precision) {
+        case LBM_F64: return lbmk::launch_step<lbmk::MODE_F64>(make_params<double>(h, from), q, fl, s);
+        case LBM_F32: return lbmk::launch_step<lbmk::MODE_F32>(make_params<float>(h, from), q, fl, s);
+        case LBM_F16: return lbmk::launch_step<lbmk::MODE_F16>(make_params<float>(h, from), q, fl, s);
+        default: return lbmk::launch_step<lbmk::MODE_BF16>(make_params<float>(h, from), q, fl, s);
+    }
 }
 
 int build_graph(lbm_handle* h) {
@@ -289,33 +328,37 @@ int sync_and_check(lbm_handle* h) {
     return h->sticky;
 }
 
-template <typename R>
-void init_values(const lbm_handle* h, lbmk::InitVals<R>& V) {
+void init_values(const lbm_handle* h, lbmk::InitVals& V) {
     const lbm_params& p = h->p;
     const lbm_derived& d = h->d;
     const double w[9] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36};
     const double T = p.T_init, H = enthalpy_of_T(p, d.L_a, T);
-    int k = 0;
-    if (p.flow)
-        for (int i = 0; i < 9; ++i) V.v[k++] = (R)0;        // f^eq(1, 0) - w_i = 0 (Eq. 27, deviation storage)
+    for (int i = 0; i < 9; ++i) V.f[i] = 0.0;            // f^eq(1, 0) - w_i = 0 (Eq. 27, deviation storage)
     const int Q = p.thermal_q;
     // g^eq(H, T, 0): Eq. 40 / B3; h^eq(T): Eq. 49 / B5 (c_pl = c_pm = 1)
     const double gw0 = Q == 9 ? 5.0 / 9.0 : p.varpi;
-    const double g0 = H - gw0 * d.c_fref * T;
-    V.v[k++] = (R)g0;
-    for (int i = 1; i < Q; ++i) V.v[k++] = (R)((Q == 9 ? w[i] : 0.25 * p.varpi) * d.c_fref * T);
-    V.v[k++] = (R)(T - gw0 * d.c_mref * T);
-    for (int i = 1; i < Q; ++i) V.v[k++] = (R)((Q == 9 ? w[i] : 0.25 * p.varpi) * d.c_mref * T);
-    if (p.precision == LBM_F32) V.v[k++] = (R)(g0 - (double)(R)g0);   // low part of g_0
+    V.g[0] = H - gw0 * d.c_fref * T;
+    V.h[0] = T - gw0 * d.c_mref * T;
+    for (int i = 1; i < Q; ++i) {
+        const double wi = Q == 9 ? w[i] : 0.25 * p.varpi;
+        V.g[i] = wi * d.c_fref * T;
+        V.h[i] = wi * d.c_mref * T;
+    }
+    V.g0_lo = V.g[0] - (double)(float)V.g[0];            // low part of g_0 (FP32 storage)
 }
 
-template <typename R>
 cudaError_t enqueue_init(lbm_handle* h) {
-    lbmk::InitVals<R> V;
+    lbmk::InitVals V;
     std::memset(&V, 0, sizeof V);
-    init_values<R>(h, V);
-    return lbmk::launch_init<R>(static_cast<R*>(h->buf[0]), static_cast<R*>(h->dT), h->L.nplanes, h->L.plane,
-                                h->p.nx, h->p.ny, h->L.pitch, V, h->stream);
+    init_values(h, V);
+    const int q = h->p.thermal_q, fl = h->p.flow;
+    cudaStream_t s = h->stream;
+    switch (h->p.precision) {
+        case LBM_F64: return lbmk::launch_init<lbmk::MODE_F64>(make_params<double>(h, 0), V, q, fl, s);
+        case LBM_F32: return lbmk::launch_init<lbmk::MODE_F32>(make_params<float>(h, 0), V, q, fl, s);
+        case LBM_F16: return lbmk::launch_init<lbmk::MODE_F16>(make_params<float>(h, 0), V, q, fl, s);
+        default: return lbmk::launch_init<lbmk::MODE_BF16>(make_params<float>(h, 0), V, q, fl, s);
+    }
 }
 
 void free_handle(lbm_handle* h) {
@@ -408,8 +451,10 @@ int lbm_create_ex(const lbm_params* p, void* cuda_stream, lbm_alloc_fn alloc, lb
     h->status = reinterpret_cast<unsigned int*>(h->base + h->L.off_status);
     h->scratch = reinterpret_cast<double*>(h->base + h->L.off_scratch);
     h->diag_out = reinterpret_cast<double*>(h->base + h->L.off_out);
-    cudaError_t e = cudaMemsetAsync(h->status, 0, sizeof(unsigned int), h->stream);
-    if (e == cudaSuccess) e = p->precision == LBM_F64 ? enqueue_init<double>(h) : enqueue_init<float>(h);
+    // zero everything once: row padding is never written by the kernels, so
+    // checkpoints of equal states are equal byte for byte
+    cudaError_t e = cudaMemsetAsync(h->base, 0, h->L.total, h->stream);
+    if (e == cudaSuccess) e = enqueue_init(h);
     if (e != cudaSuccess) {
         cudaGetLastError();
         free_handle(h);
@@ -457,7 +502,7 @@ int lbm_fields(lbm_handle* h, int32_t mask, void* const* dst, int32_t dst_on_dev
     for (int i = 0; i < LBM_NUM_FIELDS; ++i)
         if ((mask & (1 << i)) && !dst[i]) return LBM_ERR_ARG;
     if (!mask) return h->sticky;
-    const size_t n = (size_t)h->p.nx * h->p.ny, bytes = n * h->L.elem;
+    const size_t n = (size_t)h->p.nx * h->p.ny, bytes = n * h->L.relem;
     char* staging = nullptr;
     void* targets[LBM_NUM_FIELDS] = {nullptr};
     if (dst_on_device) {
@@ -472,18 +517,22 @@ int lbm_fields(lbm_handle* h, int32_t mask, void* const* dst, int32_t dst_on_dev
             if (mask & (1 << i)) targets[i] = staging + align_up(bytes) * (k++);
     }
     cudaError_t e;
+    const int q = h->p.thermal_q, fl = h->p.flow;
     if (h->p.precision == LBM_F64) {
         lbmk::FieldOut<double> o;
         for (int i = 0; i < 7; ++i) o.dst[i] = static_cast<double*>(targets[i]);
         o.mask = mask;
         o.ld = h->p.nx;
-        e = lbmk::launch_fields<double>(make_params<double>(h, h->cur), o, h->p.thermal_q, h->p.flow, h->stream);
+        e = lbmk::launch_fields<lbmk::MODE_F64>(make_params<double>(h, h->cur), o, q, fl, h->stream);
     } else {
         lbmk::FieldOut<float> o;
         for (int i = 0; i < 7; ++i) o.dst[i] = static_cast<float*>(targets[i]);
         o.mask = mask;
         o.ld = h->p.nx;
-        e = lbmk::launch_fields<float>(make_params<float>(h, h->cur), o, h->p.thermal_q, h->p.flow, h->stream);
+        const lbmk::StepParams<float> P = make_params<float>(h, h->cur);
+        if (h->p.precision == LBM_F32) e = lbmk::launch_fields<lbmk::MODE_F32>(P, o, q, fl, h->stream);
+        else if (h->p.precision == LBM_F16) e = lbmk::launch_fields<lbmk::MODE_F16>(P, o, q, fl, h->stream);
+        else e = lbmk::launch_fields<lbmk::MODE_BF16>(P, o, q, fl, h->stream);
     }
     if (e == cudaSuccess && !dst_on_device)
         for (int i = 0; i < LBM_NUM_FIELDS && e == cudaSuccess; ++i)
@@ -511,11 +560,20 @@ int lbm_diag(lbm_handle* h, double* melt_frac, double* nu_hot, double* enthalpy,
     C.k_f = p.k_f;
     C.k_m = h->d.k_m;
     C.left_wall = (!p.periodic_x && p.nx >= 3) ? 1 : 0;
-    cudaError_t e = p.precision == LBM_F64
-                        ? lbmk::launch_diag<double>(make_params<double>(h, h->cur), C, h->scratch, h->diag_out,
-                                                    p.thermal_q, p.flow, h->stream)
-                        : lbmk::launch_diag<float>(make_params<float>(h, h->cur), C, h->scratch, h->diag_out,
-                                                   p.thermal_q, p.flow, h->stream);
+    cudaError_t e;
+    const int q = p.thermal_q, fl = p.flow;
+    if (p.precision == LBM_F64) {
+        e = lbmk::launch_diag<lbmk::MODE_F64>(make_params<double>(h, h->cur), C, h->scratch, h->diag_out, q, fl,
+                                              h->stream);
+    } else {
+        const lbmk::StepParams<float> P = make_params<float>(h, h->cur);
+        if (p.precision == LBM_F32)
+            e = lbmk::launch_diag<lbmk::MODE_F32>(P, C, h->scratch, h->diag_out, q, fl, h->stream);
+        else if (p.precision == LBM_F16)
+            e = lbmk::launch_diag<lbmk::MODE_F16>(P, C, h->scratch, h->diag_out, q, fl, h->stream);
+        else
+            e = lbmk::launch_diag<lbmk::MODE_BF16>(P, C, h->scratch, h->diag_out, q, fl, h->stream);
+    }
     double s[4] = {0, 0, 0, 0};
     if (e == cudaSuccess) e = cudaMemcpyAsync(s, h->diag_out, sizeof s, cudaMemcpyDeviceToHost, h->stream);
     if (e != cudaSuccess) return cuda_fail(h);
@@ -531,9 +589,8 @@ int lbm_diag(lbm_handle* h, double* melt_frac, double* nu_hot, double* enthalpy,
 }
 
 static int copy_planes(lbm_handle* h, void* host_or_dev, int first_plane, int nplanes, bool to_state, int on_device,
-                       void* state_base) {
+                       void* state_base, size_t el) {
     if (!host_or_dev || nplanes == 0) return LBM_OK;
-    const size_t el = h->L.elem;
     char* s = static_cast<char*>(state_base) + (size_t)first_plane * h->L.plane * el;
     const size_t dpitch = (size_t)h->p.nx * el, spitch = (size_t)h->L.pitch * el;
     const size_t rows = (size_t)nplanes * h->p.ny;
@@ -544,17 +601,58 @@ static int copy_planes(lbm_handle* h, void* host_or_dev, int first_plane, int np
     return e == cudaSuccess ? LBM_OK : cuda_fail(h);
 }
 
+// 16-bit runs: the state goes through dense FP32 arrays [q][ny][nx] on the device.
+static int convert_state_io(lbm_handle* h, void* f, void* g, void* hm, int to_state, int on_device) {
+    const int Q = h->p.thermal_q;
+    const size_t n = (size_t)h->p.nx * h->p.ny;
+    const size_t nf = h->p.flow ? 9 : 0;
+    float* stage = static_cast<float*>(dev_alloc(h, align_up((nf + 2 * Q) * n * sizeof(float))));
+    if (!stage) return LBM_ERR_OOM;
+    lbmk::DenseState D;
+    D.f = (h->p.flow && f) ? stage : nullptr;
+    D.g = g ? stage + nf * n : nullptr;
+    D.h = hm ? stage + (nf + Q) * n : nullptr;
+    const cudaMemcpyKind in = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    const cudaMemcpyKind out = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    cudaError_t e = cudaSuccess;
+    if (to_state) {
+        if (D.f) e = cudaMemcpyAsync(D.f, f, 9 * n * sizeof(float), in, h->stream);
+        if (e == cudaSuccess && D.g) e = cudaMemcpyAsync(D.g, g, Q * n * sizeof(float), in, h->stream);
+        if (e == cudaSuccess && D.h) e = cudaMemcpyAsync(D.h, hm, Q * n * sizeof(float), in, h->stream);
+    }
+    if (e == cudaSuccess) {
+        const lbmk::StepParams<float> P = make_params<float>(h, h->cur);
+        e = h->p.precision == LBM_F16
+                ? lbmk::launch_convert<lbmk::MODE_F16>(P, D, to_state ? 0 : 1, Q, h->p.flow, h->stream)
+                : lbmk::launch_convert<lbmk::MODE_BF16>(P, D, to_state ? 0 : 1, Q, h->p.flow, h->stream);
+    }
+    if (!to_state && e == cudaSuccess) {
+        if (D.f) e = cudaMemcpyAsync(f, D.f, 9 * n * sizeof(float), out, h->stream);
+        if (e == cudaSuccess && D.g) e = cudaMemcpyAsync(g, D.g, Q * n * sizeof(float), out, h->stream);
+        if (e == cudaSuccess && D.h) e = cudaMemcpyAsync(hm, D.h, Q * n * sizeof(float), out, h->stream);
+    }
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) e = cudaErrorUnknown;
+    dev_free(h, stage);
+    return e == cudaSuccess ? LBM_OK : cuda_fail(h);
+}
+
 int lbm_get_state(lbm_handle* h, void* f, void* g, void* hm, void* dT, void* g0_lo, int32_t on_device) {
     if (!h) return LBM_ERR_ARG;
     if (h->sticky == LBM_ERR_CUDA) return LBM_ERR_STATE;
     const int Q = h->p.thermal_q, base = h->p.flow ? 9 : 0;
     void* cur = h->buf[h->cur];
+    const size_t el = h->L.elem, rel = h->L.relem;
     int rc = LBM_OK;
-    if (h->p.flow) rc = copy_planes(h, f, 0, 9, false, on_device, cur);
-    if (rc == LBM_OK) rc = copy_planes(h, g, base, Q, false, on_device, cur);
-    if (rc == LBM_OK) rc = copy_planes(h, hm, base + Q, Q, false, on_device, cur);
-    if (rc == LBM_OK) rc = copy_planes(h, dT, 0, 1, false, on_device, h->dT);
-    if (rc == LBM_OK && h->p.precision == LBM_F32) rc = copy_planes(h, g0_lo, base + 2 * Q, 1, false, on_device, cur);
+    if (split_mode(h->p.precision)) {
+        rc = convert_state_io(h, f, g, hm, 0, on_device);
+    } else {
+        if (h->p.flow) rc = copy_planes(h, f, 0, 9, false, on_device, cur, el);
+        if (rc == LBM_OK) rc = copy_planes(h, g, base, Q, false, on_device, cur, el);
+        if (rc == LBM_OK) rc = copy_planes(h, hm, base + Q, Q, false, on_device, cur, el);
+        if (rc == LBM_OK && h->p.precision == LBM_F32)
+            rc = copy_planes(h, g0_lo, base + 2 * Q, 1, false, on_device, cur, el);
+    }
+    if (rc == LBM_OK) rc = copy_planes(h, dT, 0, 1, false, on_device, h->dT, rel);
     if (rc != LBM_OK) return rc;
     return sync_and_check(h);
 }
@@ -565,19 +663,97 @@ int lbm_set_state(lbm_handle* h, const void* f, const void* g, const void* hm, c
     if (h->sticky == LBM_ERR_CUDA) return LBM_ERR_STATE;
     const int Q = h->p.thermal_q, base = h->p.flow ? 9 : 0;
     void* cur = h->buf[h->cur];
+    const size_t el = h->L.elem, rel = h->L.relem;
     int rc = LBM_OK;
-    if (h->p.flow) rc = copy_planes(h, const_cast<void*>(f), 0, 9, true, on_device, cur);
-    if (rc == LBM_OK) rc = copy_planes(h, const_cast<void*>(g), base, Q, true, on_device, cur);
-    if (rc == LBM_OK) rc = copy_planes(h, const_cast<void*>(hm), base + Q, Q, true, on_device, cur);
-    if (rc == LBM_OK) rc = copy_planes(h, const_cast<void*>(dT), 0, 1, true, on_device, h->dT);
-    if (rc == LBM_OK && h->p.precision == LBM_F32) {
-        char* lo = static_cast<char*>(cur) + (size_t)(base + 2 * Q) * h->L.plane * h->L.elem;
-        if (g0_lo) rc = copy_planes(h, const_cast<void*>(g0_lo), base + 2 * Q, 1, true, on_device, cur);
-        else if (g && cudaMemsetAsync(lo, 0, (size_t)h->L.plane * h->L.elem, h->stream) != cudaSuccess)
-            rc = cuda_fail(h);
+    if (split_mode(h->p.precision)) {
+        rc = convert_state_io(h, const_cast<void*>(f), const_cast<void*>(g), const_cast<void*>(hm), 1, on_device);
+    } else {
+        if (h->p.flow) rc = copy_planes(h, const_cast<void*>(f), 0, 9, true, on_device, cur, el);
+        if (rc == LBM_OK) rc = copy_planes(h, const_cast<void*>(g), base, Q, true, on_device, cur, el);
+        if (rc == LBM_OK) rc = copy_planes(h, const_cast<void*>(hm), base + Q, Q, true, on_device, cur, el);
+        if (rc == LBM_OK && h->p.precision == LBM_F32) {
+            char* lo = static_cast<char*>(cur) + (size_t)(base + 2 * Q) * h->L.plane * el;
+            if (g0_lo) rc = copy_planes(h, const_cast<void*>(g0_lo), base + 2 * Q, 1, true, on_device, cur, el);
+            else if (g && cudaMemsetAsync(lo, 0, (size_t)h->L.plane * el, h->stream) != cudaSuccess)
+                rc = cuda_fail(h);
+        }
     }
+    if (rc == LBM_OK) rc = copy_planes(h, const_cast<void*>(dT), 0, 1, true, on_device, h->dT, rel);
     if (rc != LBM_OK) return rc;
     if (cudaStreamSynchronize(h->stream) != cudaSuccess) return cuda_fail(h);
+    return h->sticky;
+}
+
+namespace {
+struct CkptHeader {
+    char magic[8];
+    int32_t version, precision, thermal_q, flow, nx, ny, pitch, nplanes;
+    int64_t steps, copy_bytes, dT_bytes;
+};
+static_assert(sizeof(CkptHeader) == 64, "checkpoint header is 64 bytes");
+const char kMagic[8] = {'L', 'B', 'M', 'C', 'K', 'P', 'T', '1'};
+
+CkptHeader header_of(const lbm_handle* h) {
+    CkptHeader c;
+    std::memset(&c, 0, sizeof c);
+    std::memcpy(c.magic, kMagic, 8);
+    c.version = 1;
+    c.precision = h->p.precision;
+    c.thermal_q = h->p.thermal_q;
+    c.flow = h->p.flow;
+    c.nx = h->p.nx;
+    c.ny = h->p.ny;
+    c.pitch = h->L.pitch;
+    c.nplanes = h->L.nplanes;
+    c.steps = h->steps;
+    c.copy_bytes = (int64_t)h->L.copy_bytes;
+    c.dT_bytes = (int64_t)h->L.dT_bytes;
+    return c;
+}
+}  // namespace
+
+int64_t lbm_checkpoint_bytes(const lbm_handle* h) {
+    if (!h) return -1;
+    return (int64_t)(sizeof(CkptHeader) + h->L.copy_bytes + h->L.dT_bytes);
+}
+
+int lbm_save(lbm_handle* h, void* dst, int32_t on_device) {
+    if (!h || !dst) return LBM_ERR_ARG;
+    if (h->sticky == LBM_ERR_CUDA) return LBM_ERR_STATE;
+    const CkptHeader c = header_of(h);
+    char* out = static_cast<char*>(dst);
+    const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    cudaError_t e = on_device ? cudaMemcpyAsync(out, &c, sizeof c, cudaMemcpyHostToDevice, h->stream)
+                              : cudaSuccess;
+    if (!on_device) std::memcpy(out, &c, sizeof c);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out + sizeof c, h->buf[h->cur], h->L.copy_bytes, k, h->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(out + sizeof c + h->L.copy_bytes, h->dT, h->L.dT_bytes, k, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h);
+    return sync_and_check(h);
+}
+
+int lbm_load(lbm_handle* h, const void* src, int32_t on_device) {
+    if (!h || !src) return LBM_ERR_ARG;
+    if (h->sticky == LBM_ERR_CUDA) return LBM_ERR_STATE;
+    CkptHeader c;
+    if (on_device) {
+        if (cudaMemcpy(&c, src, sizeof c, cudaMemcpyDeviceToHost) != cudaSuccess) return cuda_fail(h);
+    } else {
+        std::memcpy(&c, src, sizeof c);
+    }
+    const CkptHeader want = header_of(h);
+    if (std::memcmp(c.magic, kMagic, 8) != 0 || c.version != 1 || c.precision != want.precision ||
+        c.thermal_q != want.thermal_q || c.flow != want.flow || c.nx != want.nx || c.ny != want.ny ||
+        c.pitch != want.pitch || c.nplanes != want.nplanes || c.copy_bytes != want.copy_bytes ||
+        c.dT_bytes != want.dT_bytes || c.steps < 0)
+        return LBM_ERR_ARG;
+    const char* in = static_cast<const char*>(src);
+    const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    cudaError_t e = cudaMemcpyAsync(h->buf[h->cur], in + sizeof c, h->L.copy_bytes, k, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->dT, in + sizeof c + h->L.copy_bytes, h->L.dT_bytes, k, h->stream);
+    if (e != cudaSuccess || cudaStreamSynchronize(h->stream) != cudaSuccess) return cuda_fail(h);
+    h->steps = c.steps;
     return h->sticky;
 }
 

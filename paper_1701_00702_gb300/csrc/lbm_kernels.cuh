@@ -30,23 +30,82 @@
 //     in the isothermal mushy zone, where nothing damps it.
 #pragma once
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 namespace lbmk {
 
-// Per-run constants, passed by value (__grid_constant__).
+// Storage modes.  Arithmetic is FP64 for MODE_F64 and FP32 otherwise.
+//   MODE_F64  every population in FP64;
+//   MODE_F32  every population in FP32, the PCM rest population as a
+//             float-float pair (one extra FP32 plane for the low part);
+//   MODE_F16, MODE_BF16  flow deviations (scaled by 2^10 for FP16) and the
+//             moving thermal populations in 16 bits, the two thermal rest
+//             populations and the exchange history in FP32.  A moving thermal
+//             population is stored as its deviation from a reference that any
+//             reader rebuilds from the FP32 rest population of the node that
+//             sent it: at equilibrium with u = 0 every moving population is
+//             w'_i c_ref T and the rest population is g_0 = H - omega c_ref T
+//             (Eqs. 40, 49, B3, B5), a monotone map of the node's state, so
+//             T (hence the reference) follows from g_0 alone.  The 16-bit
+//             values then carry only the flux and non-equilibrium parts.
+enum : int { MODE_F64 = 0, MODE_F32 = 1, MODE_F16 = 2, MODE_BF16 = 3 };
+
+template <int M> struct ModeTraits;
+template <> struct ModeTraits<MODE_F64> { using R = double; using B = double; };
+template <> struct ModeTraits<MODE_F32> { using R = float; using B = float; };
+template <> struct ModeTraits<MODE_F16> { using R = float; using B = __half; };
+template <> struct ModeTraits<MODE_BF16> { using R = float; using B = __nv_bfloat16; };
+
+template <int M> constexpr bool kSplit = (M == MODE_F16 || M == MODE_BF16);
+template <int M> constexpr bool kComp = (M == MODE_F32);
+
+__device__ __forceinline__ float to_f(__half v) { return __half2float(v); }
+__device__ __forceinline__ float to_f(__nv_bfloat16 v) { return __bfloat162float(v); }
+__device__ __forceinline__ float to_f(float v) { return v; }
+__device__ __forceinline__ double to_f(double v) { return v; }
+
+template <typename B> __device__ __forceinline__ B from_f(float v);
+template <> __device__ __forceinline__ __half from_f<__half>(float v) { return __float2half_rn(v); }
+template <> __device__ __forceinline__ __nv_bfloat16 from_f<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
+template <> __device__ __forceinline__ float from_f<float>(float v) { return v; }
+template <typename B> __device__ __forceinline__ B from_f(double v) { return v; }
+
+// Plane numbering inside one state copy.  Bulk planes hold type B; the wide
+// planes (16-bit modes only) hold the PCM (0) and metal (1) rest populations.
+template <int M, int QT, bool FLOW>
+struct Planes {
+    static constexpr int fb = FLOW ? 9 : 0;
+    __host__ __device__ static constexpr int pcm(int q) { return kSplit<M> ? fb + q - 1 : fb + q; }   // q >= 1 when split
+    __host__ __device__ static constexpr int met(int q) { return kSplit<M> ? fb + (QT - 1) + q - 1 : fb + QT + q; }
+    static constexpr int lo = fb + 2 * QT;                                                  // MODE_F32 only
+    static constexpr int bulk = kSplit<M> ? fb + 2 * (QT - 1) : fb + 2 * QT + (kComp<M> ? 1 : 0);
+};
+
+// Planes per state copy at most: 9 flow + 2 x 9 thermal + 1 low part, + 2 wide.
+constexpr int kMaxPlanes = 30;
+
+// Per-run constants, passed by value (__grid_constant__).  A node's element
+// in every plane is at the same 32-bit offset y * pitch + x.
 template <typename R>
 struct StepParams {
-    const R* src;        // [planes][ny][pitch]: 9 flow planes (if flow), Q_T PCM, Q_T metal
-    R* dst;
+    const void* src[kMaxPlanes];   // plane base pointers of the current copy (bulk, then wide)
+    void* dst[kMaxPlanes];         // plane base pointers of the next copy
     R* dT;               // [ny][pitch] exchange history T_m - T_f of the previous step
     unsigned int* status;
     int nx, ny, pitch;
     long long plane;     // ny * pitch
     int per_x, per_y;
     int wall_kind[4];
-    R wall_T[4], wall_H[4], wall_H_lo[4];
+    R wall_T[4], wall_T_lo[4], wall_H[4], wall_H_lo[4];
+    R fscale, finv;      // flow deviations are stored times fscale (a power of two)
+    // 16-bit modes: references of the moving thermal populations
+    R w_move[9];         // w'_i: the equilibrium weight of mover i (D2Q9 w_i, D2Q5 varpi/4)
+    R g0_fs, g0_fl;      // PCM rest population at solidus / liquidus equilibrium
+    R tg_solid, tg_mushy, tg_liquid;   // dT/dg_0 on the three branches
+    R kappa_m;           // c_m,ref / (c_pm - omega c_m,ref): mover reference per unit of h_0 / w'_i
     // flow (Eqs. 3, 7, 16, 25)
     R phi, inv_phi, drag_lin, drag_forch, gbeta, T0, l0, l0sq, l1;
     R s[9];
@@ -58,10 +117,6 @@ struct StepParams {
 };
 
 enum : unsigned int { STATUS_UNSTABLE = 1u };
-
-// FP32 storage keeps the PCM rest population as a float-float pair.
-template <typename R>
-constexpr bool kComp = sizeof(R) == 4;
 
 // Error-free transformations (IEEE round-to-nearest, no contraction).
 struct FF {
@@ -92,7 +147,7 @@ __device__ __forceinline__ FF ff_add(FF a, FF b) {
 
 __device__ __forceinline__ FF ff_neg(FF a) { return {-a.hi, -a.lo}; }
 
-// Exact-ish sum of the moving populations v[1..Q-1].
+// Sum of the moving populations v[1..Q-1] as a float-float pair.
 template <int Q>
 __device__ __forceinline__ FF ff_sum_movers(const float* v) {
     FF acc = {v[1], 0.0f};
@@ -239,85 +294,115 @@ __device__ __forceinline__ void enthalpy_state(const StepParams<R>& P, R H, R& T
     }
 }
 
+// c_f,ref T at equilibrium as a function of the PCM rest population g_0: the
+// inverse of g_0 = H - omega c_f,ref T(H) with T(H) from Eq. 38 (16-bit modes).
+template <typename R>
+__device__ __forceinline__ R pcm_ref(const StepParams<R>& P, R g0) {
+    const R Ts = g0 * P.tg_solid;
+    const R Tm = P.T_fs + (g0 - P.g0_fs) * P.tg_mushy;
+    const R Tl = P.T_fl + (g0 - P.g0_fl) * P.tg_liquid;
+    return P.c_fref * (g0 <= P.g0_fs ? Ts : (g0 < P.g0_fl ? Tm : Tl));
+}
+
+template <typename R>
+__device__ __forceinline__ R fast_rcp(R x) {
+    if constexpr (sizeof(R) == 4) return __fdividef(1.0f, x);
+    else return R(1) / x;
+}
+
+template <typename R>
+__device__ __forceinline__ R fast_sqrt(R x) {   // x >= 0
+    if constexpr (sizeof(R) == 4) return x > 0.0f ? x * rsqrtf(x) : 0.0f;
+    else return sqrt(x);
+}
+
 // ---------------------------------------------------------------------------
 // Node state
 // ---------------------------------------------------------------------------
 
-template <typename R, int QT, bool FLOW>
+template <int M, int QT, bool FLOW>
 struct NodeState {
+    using R = typename ModeTraits<M>::R;
     R mp[FLOW ? 9 : 1];  // moments of f+ minus r (after the wall rule)
-    R ng[QT], nh[QT];    // moments of g and h (after the wall rule); ng[0] = H (high part)
-    R Hlo;               // low part of H (float-float bookkeeping; 0 with FP64 storage)
+    R ng[QT], nh[QT];    // moments of g and h (after the wall rule); ng[0] = H, nh[0] = c_pm T_m (high parts)
+    R Hlo, Elo;          // low parts of H and c_pm T_m (error-free bookkeeping; 0 where unused)
     R H, Tf, fl, Tm, rho, drho, ux, uy, Gy;
 };
+
+template <int M>
+__device__ __forceinline__ typename ModeTraits<M>::R ldb(const void* plane, int i) {
+    using B = typename ModeTraits<M>::B;
+    return to_f(__ldg(static_cast<const B*>(plane) + i));
+}
+
+template <int M, typename R>
+__device__ __forceinline__ void stb(void* plane, int i, R v) {
+    using B = typename ModeTraits<M>::B;
+    static_cast<B*>(plane)[i] = from_f<B>(v);
+}
 
 // Pull streaming around node (xs, ys): the population along e_i comes from
 // xs - e_i.  The index wrap is also correct for interior nodes of a walled
 // direction, which never reach the edge.
-template <typename R, int QT, bool FLOW>
-__device__ __forceinline__ void pull_moments(const StepParams<R>& P, int xs, int ys,
-                                             NodeState<R, QT, FLOW>& n) {
+template <int M, int QT, bool FLOW>
+__device__ __forceinline__ void pull_moments(const StepParams<typename ModeTraits<M>::R>& P, int xs, int ys,
+                                             NodeState<M, QT, FLOW>& n) {
+    using R = typename ModeTraits<M>::R;
+    using PL = Planes<M, QT, FLOW>;
     const int xm = xs == 0 ? P.nx - 1 : xs - 1;
     const int xp = xs == P.nx - 1 ? 0 : xs + 1;
     const int ym = ys == 0 ? P.ny - 1 : ys - 1;
     const int yp = ys == P.ny - 1 ? 0 : ys + 1;
-    const long long r0 = (long long)ys * P.pitch, rm = (long long)ym * P.pitch, rp = (long long)yp * P.pitch;
-    const R* __restrict__ s = P.src;
-    const long long pl = P.plane;
-    int base = 0;
+    const int r0 = ys * P.pitch, rm = ym * P.pitch, rp = yp * P.pitch;
+    // source offset of the population along e_q (D2Q9 order of Eq. 11)
+    const int off[9] = {r0 + xs, r0 + xm, rm + xs, r0 + xp, rp + xs, rm + xm, rm + xp, rp + xp, rp + xm};
     if constexpr (FLOW) {
         R f[9];
-        f[0] = __ldg(s + 0 * pl + r0 + xs);
-        f[1] = __ldg(s + 1 * pl + r0 + xm);
-        f[2] = __ldg(s + 2 * pl + rm + xs);
-        f[3] = __ldg(s + 3 * pl + r0 + xp);
-        f[4] = __ldg(s + 4 * pl + rp + xs);
-        f[5] = __ldg(s + 5 * pl + rm + xm);
-        f[6] = __ldg(s + 6 * pl + rm + xp);
-        f[7] = __ldg(s + 7 * pl + rp + xp);
-        f[8] = __ldg(s + 8 * pl + rp + xm);
+#pragma unroll
+        for (int q = 0; q < 9; ++q) {
+            f[q] = ldb<M>(P.src[q], off[q]);
+            if constexpr (M == MODE_F16) f[q] *= R(1.0 / 1024.0);
+        }
         m_from_f9(f, n.mp);
-        base = 9;
     }
     R g[QT], h[QT];
-    const R* sg = s + (long long)base * pl;
-    const R* sh = s + (long long)(base + QT) * pl;
-    g[0] = __ldg(sg + 0 * pl + r0 + xs);
-    g[1] = __ldg(sg + 1 * pl + r0 + xm);
-    g[2] = __ldg(sg + 2 * pl + rm + xs);
-    g[3] = __ldg(sg + 3 * pl + r0 + xp);
-    g[4] = __ldg(sg + 4 * pl + rp + xs);
-    h[0] = __ldg(sh + 0 * pl + r0 + xs);
-    h[1] = __ldg(sh + 1 * pl + r0 + xm);
-    h[2] = __ldg(sh + 2 * pl + rm + xs);
-    h[3] = __ldg(sh + 3 * pl + r0 + xp);
-    h[4] = __ldg(sh + 4 * pl + rp + xs);
-    if constexpr (QT == 9) {
-        g[5] = __ldg(sg + 5 * pl + rm + xm);
-        g[6] = __ldg(sg + 6 * pl + rm + xp);
-        g[7] = __ldg(sg + 7 * pl + rp + xp);
-        g[8] = __ldg(sg + 8 * pl + rp + xm);
-        h[5] = __ldg(sh + 5 * pl + rm + xm);
-        h[6] = __ldg(sh + 6 * pl + rm + xp);
-        h[7] = __ldg(sh + 7 * pl + rp + xp);
-        h[8] = __ldg(sh + 8 * pl + rp + xm);
+    if constexpr (kSplit<M>) {
+        const float* G0 = static_cast<const float*>(P.src[PL::bulk]);
+        const float* M0 = static_cast<const float*>(P.src[PL::bulk + 1]);
+        g[0] = __ldg(G0 + off[0]);
+        h[0] = __ldg(M0 + off[0]);
+#pragma unroll
+        for (int q = 1; q < QT; ++q) {   // deviation + reference of the sending node
+            g[q] = ldb<M>(P.src[PL::pcm(q)], off[q]) + P.w_move[q] * pcm_ref(P, __ldg(G0 + off[q]));
+            h[q] = ldb<M>(P.src[PL::met(q)], off[q]) + P.w_move[q] * P.kappa_m * __ldg(M0 + off[q]);
+        }
+    } else {
+        g[0] = ldb<M>(P.src[PL::pcm(0)], off[0]);
+        h[0] = ldb<M>(P.src[PL::met(0)], off[0]);
+#pragma unroll
+        for (int q = 1; q < QT; ++q) {
+            g[q] = ldb<M>(P.src[PL::pcm(q)], off[q]);
+            h[q] = ldb<M>(P.src[PL::met(q)], off[q]);
+        }
     }
     fwd<R, QT>(g, n.ng);
     fwd<R, QT>(h, n.nh);
-    if constexpr (kComp<R>) {
+    n.Hlo = R(0);
+    n.Elo = R(0);
+    if constexpr (kComp<M>) {
         // H = (g_0 hi + g_0 lo) + sum of movers, without rounding loss
-        const float lo = __ldg(s + (long long)(base + 2 * QT) * pl + r0 + xs);
+        const float lo = ldb<M>(P.src[PL::lo], off[0]);
         const FF H = ff_add(FF{g[0], lo}, ff_sum_movers<QT>(g));
         n.ng[0] = H.hi;
         n.Hlo = H.lo;
-    } else {
-        n.Hlo = R(0);
     }
 }
 
 // Macroscopic state from the moments (Eqs. 21, 23-25, 37-39, 48, 7).
-template <typename R, int QT, bool FLOW>
-__device__ __forceinline__ void macro(const StepParams<R>& P, NodeState<R, QT, FLOW>& n, bool wall) {
+template <int M, int QT, bool FLOW>
+__device__ __forceinline__ void macro(const StepParams<typename ModeTraits<M>::R>& P, NodeState<M, QT, FLOW>& n,
+                                      bool wall) {
+    using R = typename ModeTraits<M>::R;
     n.H = n.ng[0];
     enthalpy_state(P, n.H, n.Tf, n.fl);
     n.Tm = n.nh[0] * P.inv_c_pm;
@@ -330,11 +415,11 @@ __device__ __forceinline__ void macro(const StepParams<R>& P, NodeState<R, QT, F
             n.uy = R(0);
         } else {
             // Eq. 24 with sum_i e_i f_i = f_l sum_i e_i f+_i (the equilibrium at rest carries no momentum)
-            const R ir = R(1) / n.rho;
+            const R ir = fast_rcp(n.rho);
             const R vx = n.fl * n.mp[3] * ir;
             const R vy = n.fl * n.mp[5] * ir + R(0.5) * P.phi * n.Gy;
-            const R vm = sqrt(vx * vx + vy * vy);
-            const R den = R(1) / (P.l0 + sqrt(P.l0sq + P.l1 * vm));   // Eq. 23
+            const R vm = fast_sqrt(vx * vx + vy * vy);
+            const R den = fast_rcp(P.l0 + fast_sqrt(P.l0sq + P.l1 * vm));   // Eq. 23
             n.ux = vx * den;
             n.uy = vy * den;
         }
@@ -349,21 +434,23 @@ __device__ __forceinline__ void macro(const StepParams<R>& P, NodeState<R, QT, F
 
 // Full state of node (x, y): interior nodes pull at themselves; wall nodes pull
 // at x_f = x_b + inward normal and apply Eq. 52 in moment space.
-template <typename R, int QT, bool FLOW>
-__device__ __forceinline__ void node_state(const StepParams<R>& P, int x, int y,
-                                           NodeState<R, QT, FLOW>& n, bool& wall) {
+template <int M, int QT, bool FLOW>
+__device__ __forceinline__ void node_state(const StepParams<typename ModeTraits<M>::R>& P, int x, int y,
+                                           NodeState<M, QT, FLOW>& n, bool& wall) {
+    using R = typename ModeTraits<M>::R;
     const bool wx = !P.per_x && (x == 0 || x == P.nx - 1);
     const bool wy = !P.per_y && (y == 0 || y == P.ny - 1);
     wall = wx || wy;
     const int xs = wx ? (x == 0 ? 1 : P.nx - 2) : x;
     const int ys = wy ? (y == 0 ? 1 : P.ny - 2) : y;
-    pull_moments<R, QT, FLOW>(P, xs, ys, n);
-    macro<R, QT, FLOW>(P, n, false);
+    pull_moments<M, QT, FLOW>(P, xs, ys, n);
+    macro<M, QT, FLOW>(P, n, false);
     if (!wall) return;
 
     const int side = wx ? (x == 0 ? 0 : 1) : (y == 0 ? 2 : 3);
+    const bool dirichlet = P.wall_kind[side] == 0;
     R Tb, Hb, Tmb;
-    if (P.wall_kind[side] == 0) {
+    if (dirichlet) {
         Tb = P.wall_T[side];
         Tmb = Tb;
         Hb = P.wall_H[side];
@@ -390,39 +477,99 @@ __device__ __forceinline__ void node_state(const StepParams<R>& P, int x, int y,
     neq_pcm<R, QT>(P, n.H, n.Tf, n.ux, n.uy, b);
 #pragma unroll
     for (int k = 1; k < QT; ++k) n.ng[k] += a[k] - b[k];
-    if (P.wall_kind[side] == 0) {   // n_0 = H_b exactly (adiabatic: n_0 = H(x_f), unchanged)
+    if (dirichlet) {   // n_0 = H_b exactly (adiabatic: n_0 = H(x_f), unchanged)
         n.ng[0] = P.wall_H[side];
         n.Hlo = P.wall_H_lo[side];
     }
     neq_metal<R, QT>(P, Tmb, a);
     neq_metal<R, QT>(P, n.Tm, b);
+    if constexpr (kSplit<M>) {
 #pragma unroll
-    for (int k = 0; k < QT; ++k) n.nh[k] += a[k] - b[k];
-    macro<R, QT, FLOW>(P, n, true);
+        for (int k = 1; k < QT; ++k) n.nh[k] += a[k] - b[k];
+        if (dirichlet) {   // c_pm T_m = c_pm T_b exactly (c_pm = 1)
+            n.nh[0] = P.wall_T[side];
+            n.Elo = P.wall_T_lo[side];
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < QT; ++k) n.nh[k] += a[k] - b[k];
+    }
+    macro<M, QT, FLOW>(P, n, true);
+}
+
+// Post-collision thermal populations from their moments.  n0 is the
+// conserved moment after the source (hi, lo).  The rest population is the
+// remainder n0 - sum of the moving populations as they are stored, so the
+// stored populations carry exactly the enthalpy (internal energy) that the
+// collision produced: to float-float accuracy with FP32 storage, to one FP32
+// rounding with 16-bit movers, to FP64 rounding with FP64 storage.
+template <int M, int QT>
+__device__ __forceinline__ void store_thermal(const StepParams<typename ModeTraits<M>::R>& P,
+                                              typename ModeTraits<M>::R* nm, typename ModeTraits<M>::R n0hi,
+                                              typename ModeTraits<M>::R n0lo, int o, int rest_plane,
+                                              int mover_plane1, int lo_plane, bool remainder, bool is_pcm) {
+    using R = typename ModeTraits<M>::R;
+    R v[QT];
+    nm[0] = n0hi;
+    inv<R, QT>(nm, v);
+    if constexpr (kSplit<M>) {
+        // reference from the provisional rest population, 16-bit deviations,
+        // then the rest population that closes the balance with the movers as
+        // readers will rebuild them
+        using B = typename ModeTraits<M>::B;
+        float sm = v[1];
+#pragma unroll
+        for (int k = 2; k < QT; ++k) sm += v[k];
+        const float g0a = n0hi - sm;
+        const float ref = is_pcm ? pcm_ref(P, g0a) : P.kappa_m * g0a;
+        float st = 0.0f;
+#pragma unroll
+        for (int k = 1; k < QT; ++k) {
+            const float r = P.w_move[k] * ref;
+            const B b = from_f<B>(v[k] - r);
+            static_cast<B*>(P.dst[mover_plane1 + k - 1])[o] = b;
+            st += to_f(b) + r;
+        }
+        static_cast<float*>(P.dst[rest_plane])[o] = n0hi - st;
+    } else {
+#pragma unroll
+        for (int k = 1; k < QT; ++k) stb<M>(P.dst[mover_plane1 + k - 1], o, v[k]);
+        if (!remainder) {
+            stb<M>(P.dst[rest_plane], o, v[0]);
+        } else if constexpr (kComp<M>) {
+            const FF r = ff_add(FF{n0hi, n0lo}, ff_neg(ff_sum_movers<QT>(v)));
+            stb<M>(P.dst[rest_plane], o, r.hi);
+            stb<M>(P.dst[lo_plane], o, r.lo);
+        } else {
+            R sm = v[1];
+#pragma unroll
+            for (int k = 2; k < QT; ++k) sm += v[k];
+            stb<M>(P.dst[rest_plane], o, n0hi - sm);
+        }
+    }
 }
 
 // ---------------------------------------------------------------------------
 // The fused step
 // ---------------------------------------------------------------------------
 
-template <typename R, int QT, bool FLOW>
-__global__ void __launch_bounds__(256) fused_step(const __grid_constant__ StepParams<R> P) {
+template <int M, int QT, bool FLOW>
+__global__ void __launch_bounds__(256) fused_step(const __grid_constant__ StepParams<typename ModeTraits<M>::R> P) {
+    using R = typename ModeTraits<M>::R;
+    using PL = Planes<M, QT, FLOW>;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     if (x >= P.nx || y >= P.ny) return;
 
-    NodeState<R, QT, FLOW> n;
+    NodeState<M, QT, FLOW> n;
     bool wall;
-    node_state<R, QT, FLOW>(P, x, y, n, wall);
+    node_state<M, QT, FLOW>(P, x, y, n, wall);
 
-    const long long o = (long long)y * P.pitch + x;
-    R* __restrict__ d = P.dst;
-    const long long pl = P.plane;
-    int base = 0;
+    const int o = y * P.pitch + x;
 
     if constexpr (FLOW) {
         // Eq. 3 at the node's velocity (u = u_b = 0 on walls)
-        const R um = sqrt(n.ux * n.ux + n.uy * n.uy);
+        const R um = fast_sqrt(n.ux * n.ux + n.uy * n.uy);
         const R drag = P.drag_lin + P.drag_forch * um;
         const R Fx = -drag * n.ux;
         const R Fy = -drag * n.uy + P.phi * n.Gy;
@@ -446,8 +593,10 @@ __global__ void __launch_bounds__(256) fused_step(const __grid_constant__ StepPa
         R f[9];
         f_from_m9(m, f);
 #pragma unroll
-        for (int k = 0; k < 9; ++k) d[k * pl + o] = f[k];
-        base = 9;
+        for (int k = 0; k < 9; ++k) {
+            if constexpr (M == MODE_F16) f[k] *= R(1024.0);
+            stb<M>(P.dst[k], o, f[k]);
+        }
     }
 
     // exchange sources, Eqs. 36 and 47 with the backward difference of Remark III
@@ -468,39 +617,32 @@ __global__ void __launch_bounds__(256) fused_step(const __grid_constant__ StepPa
             n.ng[3] += P.varpi * S_pcm;
         }
         // n_0* = H + S_PCM (n_0 is conserved up to the source, Eq. 32)
-        R g[QT];
-        if constexpr (kComp<R>) {
+        R hi, lo;
+        if constexpr (kComp<M>) {
             const FF n0 = ff_add(FF{n.ng[0], n.Hlo}, S_pcm);
-            n.ng[0] = n0.hi;
-            inv<R, QT>(n.ng, g);
-            const FF g0 = ff_add(n0, ff_neg(ff_sum_movers<QT>(g)));   // rest = exact remainder
-            d[(base + 0) * pl + o] = g0.hi;
-            d[(long long)(base + 2 * QT) * pl + o] = g0.lo;
+            hi = n0.hi;
+            lo = n0.lo;
         } else {
-            n.ng[0] += S_pcm;
-            inv<R, QT>(n.ng, g);
-            R sm = g[1];
-#pragma unroll
-            for (int k = 2; k < QT; ++k) sm += g[k];
-            d[(base + 0) * pl + o] = n.ng[0] - sm;
+            hi = n.ng[0] + S_pcm;
+            lo = R(0);
         }
-#pragma unroll
-        for (int k = 1; k < QT; ++k) d[(base + k) * pl + o] = g[k];
+        store_thermal<M, QT>(P, n.ng, hi, lo, o, kSplit<M> ? PL::bulk : PL::pcm(0), PL::pcm(1), PL::lo, true, true);
     }
     {
         R ne[QT];
         neq_metal<R, QT>(P, n.Tm, ne);
 #pragma unroll
-        for (int k = 0; k < QT; ++k) n.nh[k] -= P.eta[k] * (n.nh[k] - ne[k]);
+        for (int k = 1; k < QT; ++k) n.nh[k] -= P.eta[k] * (n.nh[k] - ne[k]);
         if constexpr (QT == 9) {
-            n.nh[0] += S_met; n.nh[1] -= R(2) * S_met; n.nh[2] += S_met;
+            n.nh[1] -= R(2) * S_met; n.nh[2] += S_met;
         } else {
-            n.nh[0] += S_met; n.nh[3] += P.varpi * S_met;
+            n.nh[3] += P.varpi * S_met;
         }
-        R h[QT];
-        inv<R, QT>(n.nh, h);
-#pragma unroll
-        for (int k = 0; k < QT; ++k) d[(base + QT + k) * pl + o] = h[k];
+        R hi;
+        if constexpr (kSplit<M>) hi = n.nh[0] + S_met;
+        else hi = n.nh[0] - P.eta[0] * (n.nh[0] - ne[0]) + S_met;
+        store_thermal<M, QT>(P, n.nh, hi, R(0), o, kSplit<M> ? PL::bulk + 1 : PL::met(0), PL::met(1), PL::lo,
+                             kSplit<M>, false);
     }
     P.dT[o] = dTn;
 
@@ -518,17 +660,18 @@ struct FieldOut {
     int ld;   // row stride of the outputs (elements)
 };
 
-template <typename R, int QT, bool FLOW>
-__global__ void __launch_bounds__(256) fields_kernel(const __grid_constant__ StepParams<R> P,
-                                                     const __grid_constant__ FieldOut<R> out) {
+template <int M, int QT, bool FLOW>
+__global__ void __launch_bounds__(256) fields_kernel(const __grid_constant__ StepParams<typename ModeTraits<M>::R> P,
+                                                     const __grid_constant__ FieldOut<typename ModeTraits<M>::R> out) {
+    using R = typename ModeTraits<M>::R;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     if (x >= P.nx || y >= P.ny) return;
-    NodeState<R, QT, FLOW> n;
+    NodeState<M, QT, FLOW> n;
     bool wall;
-    node_state<R, QT, FLOW>(P, x, y, n, wall);
+    node_state<M, QT, FLOW>(P, x, y, n, wall);
     const long long o = (long long)y * out.ld + x;
-    const R v[7] = {n.Tf, n.Tm, n.fl, n.ux, n.uy, n.rho, n.H};
+    const R v[7] = {n.Tf, n.Tm, n.fl, n.ux, n.uy, n.rho, n.H};   // H: high part
 #pragma unroll
     for (int i = 0; i < 7; ++i)
         if (out.mask & (1 << i)) out.dst[i][o] = v[i];
@@ -541,25 +684,26 @@ struct DiagConst {
     int left_wall;  // 1 when x = 0 is a wall (Nusselt number defined)
 };
 
-template <typename R, int QT, bool FLOW>
-__global__ void __launch_bounds__(256) diag_partial(const __grid_constant__ StepParams<R> P,
+template <int M, int QT, bool FLOW>
+__global__ void __launch_bounds__(256) diag_partial(const __grid_constant__ StepParams<typename ModeTraits<M>::R> P,
                                                     const __grid_constant__ DiagConst C,
                                                     double* __restrict__ scratch) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     double v[4] = {0.0, 0.0, 0.0, 0.0};
     if (x < P.nx && y < P.ny) {
-        NodeState<R, QT, FLOW> n;
+        NodeState<M, QT, FLOW> n;
         bool wall;
-        node_state<R, QT, FLOW>(P, x, y, n, wall);
+        node_state<M, QT, FLOW>(P, x, y, n, wall);
         v[0] = (double)n.fl;
-        v[1] = C.phi * C.rho_l * ((double)n.H + (double)n.Hlo) + (1.0 - C.phi) * C.rho_m * C.c_pm * (double)n.Tm;
+        v[1] = C.phi * C.rho_l * ((double)n.H + (double)n.Hlo) +
+               (1.0 - C.phi) * C.rho_m * C.c_pm * ((double)n.Tm + (double)n.Elo);
         v[2] = 1.0 + (double)n.drho;
         if (x == 0 && C.left_wall && P.nx >= 3) {
-            NodeState<R, QT, FLOW> n1, n2;
+            NodeState<M, QT, FLOW> n1, n2;
             bool w1, w2;
-            node_state<R, QT, FLOW>(P, 1, y, n1, w1);
-            node_state<R, QT, FLOW>(P, 2, y, n2, w2);
+            node_state<M, QT, FLOW>(P, 1, y, n1, w1);
+            node_state<M, QT, FLOW>(P, 2, y, n2, w2);
             const double gf = 0.5 * (3.0 * (double)n.Tf - 4.0 * (double)n1.Tf + (double)n2.Tf);
             const double gm = 0.5 * (3.0 * (double)n.Tm - 4.0 * (double)n1.Tm + (double)n2.Tm);
             v[3] = C.phi * C.k_f * gf + (1.0 - C.phi) * C.k_m * gm;

@@ -1,6 +1,7 @@
-// FP32 storage: instantiation of the fused step, fields, diagnostics and init kernels.
+// FP32 storage (float-float PCM rest population): fused step, fields,
+// diagnostics and init kernels.
 #include "lbm_launch.cuh"
 
 namespace lbmk {
-LBMK_INSTANTIATE(float)
+LBMK_INSTANTIATE(MODE_F32)
 }  // namespace lbmk

@@ -3,7 +3,7 @@
 #include "lbm_launch.cuh"
 
 namespace lbmk {
-LBMK_INSTANTIATE(double)
+LBMK_INSTANTIATE(MODE_F64)
 
 // Fixed-order sum of the per-block partials: thread t adds blocks t, t+256, ...
 // then a shared-memory tree combines the 256 thread sums; out[0..3] =

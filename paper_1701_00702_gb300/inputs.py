@@ -15,6 +15,8 @@ import numpy as np
 
 PREC_F64 = 0
 PREC_F32 = 1
+PREC_F16 = 2
+PREC_BF16 = 3
 
 WALL_DIRICHLET = 0
 WALL_ADIABATIC = 1

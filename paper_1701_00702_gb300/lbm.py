@@ -21,7 +21,7 @@ ERRORS = {
     -1: "LBM_ERR_ARG", -2: "LBM_ERR_STABILITY", -3: "LBM_ERR_OOM", -4: "LBM_ERR_CUDA",
     -5: "LBM_ERR_UNSTABLE", -6: "LBM_ERR_TIMEOUT", -7: "LBM_ERR_STATE", -8: "LBM_ERR_TOO_LARGE",
 }
-F64, F32 = 0, 1
+F64, F32, F16, BF16 = 0, 1, 2, 3
 FIELDS = ("T_f", "T_s", "f_l", "u_x", "u_y", "rho", "H_f")
 
 
@@ -94,6 +94,12 @@ def lib() -> ctypes.CDLL:
         L.lbm_get_state.restype = ctypes.c_int
         L.lbm_set_state.argtypes = [vp, vp, vp, vp, vp, vp, i32]
         L.lbm_set_state.restype = ctypes.c_int
+        L.lbm_checkpoint_bytes.argtypes = [vp]
+        L.lbm_checkpoint_bytes.restype = i64
+        L.lbm_save.argtypes = [vp, vp, i32]
+        L.lbm_save.restype = ctypes.c_int
+        L.lbm_load.argtypes = [vp, vp, i32]
+        L.lbm_load.restype = ctypes.c_int
         L.lbm_status.argtypes = [vp]
         L.lbm_status.restype = ctypes.c_int
         L.lbm_steps_done.argtypes = [vp]
@@ -295,7 +301,7 @@ class Solver:
         g = np.empty((self.qt, self.ny, self.nx), self.np_dtype)
         h = np.empty((self.qt, self.ny, self.nx), self.np_dtype)
         dT = np.empty((self.ny, self.nx), self.np_dtype)
-        lo = np.empty((self.ny, self.nx), self.np_dtype) if self.np_dtype == np.float32 else None
+        lo = np.empty((self.ny, self.nx), self.np_dtype) if self._struct.precision == F32 else None
         _check(lib().lbm_get_state(self._h, None if f is None else f.ctypes.data, g.ctypes.data, h.ctypes.data,
                                    dT.ctypes.data, None if lo is None else lo.ctypes.data, 0), "lbm_get_state")
         return (f, g, h, dT, lo) if with_lo else (f, g, h, dT)
@@ -306,6 +312,17 @@ class Solver:
             raise ValueError("flow populations are required when the flow lattice is on")
         ptrs = [None if a is None else a.ctypes.data for a in conv]
         _check(lib().lbm_set_state(self._h, *ptrs, 0), "lbm_set_state")
+
+    def save(self) -> np.ndarray:
+        """Raw checkpoint (header + current state copy + history) as host bytes."""
+        buf = np.empty(int(lib().lbm_checkpoint_bytes(self._h)), np.uint8)
+        _check(lib().lbm_save(self._h, buf.ctypes.data, 0), "lbm_save")
+        return buf
+
+    def load(self, buf: np.ndarray):
+        """Restores a checkpoint written by save() of a run with the same layout."""
+        buf = np.ascontiguousarray(buf, np.uint8)
+        _check(lib().lbm_load(self._h, buf.ctypes.data, 0), "lbm_load")
 
     def close(self):
         if self._h:
