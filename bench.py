@@ -96,6 +96,8 @@ def parse():
     ap.add_argument("--lb-steps", type=int, default=2000, help="LB time steps per benchmark step")
     ap.add_argument("--roofline-n", type=int, default=2048)
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--batch-runs", type=int, default=64)
     ap.add_argument("--no-cpu", action="store_true")
     return ap.parse_args()
 
@@ -229,6 +231,51 @@ def run_reference(args):
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
+
+def bench_batched(args, lbm, inputs, torch, stream, steps_per_solve: int = 10_000, chunk: int = 64, reps: int = 3):
+    """64 cavities, sides uniform in [64, 512], porosity, Da, Ra, Ste drawn as in
+    the batched workload; every form advances all runs by the same steps."""
+    draws = inputs.batch_draws(count=args.batch_runs)
+    nodes = sum(p["nx"] * p["ny"] for p in draws)
+
+    def make(prec):
+        return [lbm.Solver(dict(p, precision=prec), stream=stream) for p in draws]
+
+    def timed(fn):
+        fn()
+        stream.synchronize()
+        e = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+        for a, b in e:
+            a.record(stream)
+            fn()
+            b.record(stream)
+        stream.synchronize()
+        return sum(a.elapsed_time(b) for a, b in e) / (reps * chunk)   # ms per step of all runs
+
+    out = {"runs": len(draws), "nodes": nodes, "steps_per_solve": steps_per_solve, "forms": []}
+    runs = make(1)
+    ms = timed(lambda: [r.step(chunk) for r in runs])
+    ok = all(r.status() == 0 for r in runs)
+    for r in runs:
+        r.close()
+    out["forms"].append({"form": "plain per-run FP32", "ms_per_step": ms, "mlups": nodes / (ms / 1e3) / 1e6,
+                         "solves_per_s": len(draws) / (ms / 1e3 * steps_per_solve), "ok": ok})
+    for prec, name in ((1, "batched FP32"), (2, "batched FP16")):
+        runs = make(prec)
+        b = lbm.Batch(runs, autotune=True, stream=stream)
+        ms = timed(lambda: b.step(chunk))
+        info = b.info()
+        ok = all(r.status() == 0 for r in runs)
+        b.close()
+        for r in runs:
+            r.close()
+        out["forms"].append({"form": name, "ms_per_step": ms, "mlups": nodes / (ms / 1e3) / 1e6,
+                             "solves_per_s": len(draws) / (ms / 1e3 * steps_per_solve), "ok": ok,
+                             "tuned": info})
+    base = out["forms"][0]["solves_per_s"]
+    for f in out["forms"]:
+        f["speedup_vs_plain_fp32"] = f["solves_per_s"] / base
+    return out
 
 def main():
     args = parse()
@@ -372,16 +419,21 @@ def main():
                     "mlups": nodes / (ms / 1e3) / 1e6, "avg_launch_us": ms * 1e3,
                     "peak_source": "measured" if peaks else "fallback"}
 
+        # many unequal cavities: plain per-run FP32 vs one launch per step for all runs
+        batched = None
+        if not args.no_batched:
+            batched = bench_batched(args, lbm, inputs, torch, stream)
+
         # every storage form of the same step, on the L2-resident and the HBM-bound cavity
         forms = []
         if args.roofline_n > 0:
             peak = roof["peak"]
-            for prec in (1, 2, 3):
+            for fprec in (1, 2, 3):
                 for n, per in ((args.roofline_n, 128), (args.n, 2048)):
-                    ms = time_form(prec, n, per)
-                    b = bytes_per_update(5, 1, prec)
+                    ms = time_form(fprec, n, per)
+                    b = bytes_per_update(5, 1, fprec)
                     gbs = b * n * n / (ms / 1e3) / 1e9
-                    forms.append({"precision": PREC_NAMES[prec], "grid": n, "us_per_step": ms * 1e3,
+                    forms.append({"precision": PREC_NAMES[fprec], "grid": n, "us_per_step": ms * 1e3,
                                   "mlups": n * n / (ms / 1e3) / 1e6, "bytes_per_update": b,
                                   "gbs_algorithmic": gbs, "frac_of_measured_hbm": gbs / peak})
 
@@ -400,6 +452,7 @@ def main():
                         "gbs_algorithmic": bpu * cells / (launch_ms_small / 1e3) / 1e9,
                         "note": "256x256 state (10 MB) is L2-resident; launch-to-launch time inside CUDA graphs"},
         "forms": forms if args.roofline_n > 0 else None,
+        "batched": batched,
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": args.steps * chunk,

@@ -227,6 +227,45 @@ int lbm_destroy(lbm_handle* h);
 const char* lbm_strerror(int code);
 
 /*
+ * Batches: many runs (cavities of unequal size and parameters) advanced
+ * together by one kernel launch per time step, replayed from captured CUDA
+ * graphs (the persistent, graph-captured form of Sec. III's step for many
+ * independent problems; the paper itself runs one problem at a time).
+ *
+ * lbm_batch_create takes n_runs distinct handles that share precision,
+ * thermal_q and flow and have taken steps of the same parity; it
+ * synchronises their streams.  The work is a list of tiles (one run, w x
+ * 256/w nodes, w a power of two from 32 to 256); with autotune = 1 the call
+ * times every combination of tile-width cap (64, 128, 256) and cell-to-block
+ * map (one block per tile, persistent blocks over contiguous chunks,
+ * persistent blocks striding over the list) on freshly created copies of the
+ * runs -- the runs themselves do not move, but the copies hold as much
+ * device memory again while tuning -- and keeps the fastest; otherwise it
+ * takes width cap 128, one block per tile.  Every node's arithmetic is the
+ * same under every map, so the choice cannot change results: a batched step
+ * equals lbm_step on each run.
+ *
+ * lbm_batch_step enqueues nsteps steps of every run on the batch's stream
+ * and advances each run's step count.  Use the runs' own calls (fields,
+ * diagnostics, checkpoints, lbm_step) only on the same stream or after
+ * synchronising it.  A run whose sticky status is set stops the batch
+ * (LBM_ERR_STATE).  lbm_batch_info reports the tile count, the chosen width
+ * cap and map (0, 1, 2), the grid size and the tuned microseconds per step.
+ * lbm_batch_destroy synchronises and frees the batch (not its runs).
+ * The batch allocates its work list and parameter blocks through the first
+ * run's allocation hooks (or the CUDA stream-ordered allocator).
+ */
+typedef struct lbm_batch lbm_batch;
+int lbm_batch_create(lbm_handle* const* runs, int32_t n_runs, int32_t autotune, void* cuda_stream,
+                     lbm_batch** out);
+int lbm_batch_step(lbm_batch* b, int64_t nsteps);
+/* Forces a tile-width cap (32, 64, 128 or 256) and a map (0, 1, 2); synchronises. */
+int lbm_batch_configure(lbm_batch* b, int32_t width_cap, int32_t mapping);
+int lbm_batch_info(const lbm_batch* b, int32_t* n_tiles, int32_t* width_cap, int32_t* mapping, int32_t* grid,
+                   double* tuned_us_per_step);
+int lbm_batch_destroy(lbm_batch* b);
+
+/*
  * Allocation-free diagnostics (the paper has no counterpart; this entry
  * point exists for callers that cannot allocate device memory).
  *

@@ -1,9 +1,11 @@
 // Host runtime behind the C ABI of include/lbm.h: parameter map and checks,
 // device state, graph-replayed stepping, fields, diagnostics, state I/O.
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
 #include <new>
+#include <vector>
 
 #include "lbm.h"
 #include "lbm_launch.cuh"
@@ -790,6 +792,374 @@ const char* lbm_strerror(int code) {
         case LBM_ERR_TOO_LARGE: return "grid larger than the static scratch of the allocation-free diagnostics";
         default: return "unknown status code";
     }
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Batches: many runs advanced by one launch per time step
+// ---------------------------------------------------------------------------
+
+struct lbm_batch {
+    std::vector<lbm_handle*> runs;
+    int precision = 0, qt = 0, flow = 0;
+    cudaStream_t stream = nullptr;
+    cudaStream_t cap = nullptr;
+    lbm_alloc_fn alloc = nullptr;
+    lbm_free_fn release = nullptr;
+    void* ctx = nullptr;
+    char* dev = nullptr;          // params[2][n] then tiles
+    size_t params_stride = 0;     // bytes of one StepParams
+    void* params[2] = {nullptr, nullptr};
+    lbmk::Tile* tiles = nullptr;
+    size_t tile_capacity = 0;     // tiles that fit in the allocation
+    int ntiles = 0, width_cap = 128, chunk = 1, grid = 0, parity = 0, mapping = 0;
+    double tuned_us = 0.0;
+    cudaGraphExec_t graph = nullptr;
+};
+
+namespace {
+
+int pow2_at_least(int v) {
+    int p = 32;
+    while (p < v && p < 256) p <<= 1;
+    return p;
+}
+
+std::vector<lbmk::Tile> make_tiles(const std::vector<lbm_handle*>& runs, int width_cap) {
+    std::vector<lbmk::Tile> t;
+    for (int r = 0; r < (int)runs.size(); ++r) {
+        const int nx = runs[r]->p.nx, ny = runs[r]->p.ny;
+        const int w = std::min(width_cap, pow2_at_least(nx));
+        int lg = 0;
+        while ((1 << lg) < w) ++lg;
+        const int h = 256 / w;
+        for (int y0 = 0; y0 < ny; y0 += h)
+            for (int x0 = 0; x0 < nx; x0 += w) t.push_back({r, x0, y0, lg});
+    }
+    return t;
+}
+
+void* batch_alloc(lbm_batch* b, size_t bytes, cudaStream_t s) {
+    if (b->alloc) return b->alloc(bytes, b->ctx);
+    void* p = nullptr;
+    if (cudaMallocAsync(&p, bytes, s) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return p;
+}
+
+void batch_free(lbm_batch* b, void* p) {
+    if (!p) return;
+    if (b->release) b->release(p, b->ctx);
+    else cudaFreeAsync(p, b->stream);
+}
+
+template <typename R>
+void fill_params(lbm_batch* b, std::vector<char>& host, int parity) {
+    for (size_t r = 0; r < b->runs.size(); ++r) {
+        const lbmk::StepParams<R> P = make_params<R>(b->runs[r], parity);
+        std::memcpy(host.data() + r * sizeof P, &P, sizeof P);
+    }
+}
+
+// Writes params for both parities and the tiles of width_cap into b->dev.
+int upload_batch(lbm_batch* b, const std::vector<lbmk::Tile>& tiles) {
+    const size_t n = b->runs.size();
+    if (tiles.size() > b->tile_capacity) return LBM_ERR_ARG;
+    std::vector<char> host(2 * n * b->params_stride + tiles.size() * sizeof(lbmk::Tile));
+    std::vector<char> one(n * b->params_stride);
+    for (int par = 0; par < 2; ++par) {
+        if (b->precision == LBM_F64) fill_params<double>(b, one, par);
+        else fill_params<float>(b, one, par);
+        std::memcpy(host.data() + par * n * b->params_stride, one.data(), one.size());
+    }
+    std::memcpy(host.data() + 2 * n * b->params_stride, tiles.data(), tiles.size() * sizeof(lbmk::Tile));
+    if (cudaMemcpyAsync(b->dev, host.data(), host.size(), cudaMemcpyHostToDevice, b->stream) != cudaSuccess ||
+        cudaStreamSynchronize(b->stream) != cudaSuccess) {
+        cudaGetLastError();
+        return LBM_ERR_CUDA;
+    }
+    b->params[0] = b->dev;
+    b->params[1] = b->dev + n * b->params_stride;
+    b->tiles = reinterpret_cast<lbmk::Tile*>(b->dev + 2 * n * b->params_stride);
+    b->ntiles = (int)tiles.size();
+    return LBM_OK;
+}
+
+cudaError_t batch_launch(lbm_batch* b, int parity, cudaStream_t s) {
+    const int q = b->qt, fl = b->flow;
+    switch (b->precision) {
+        case LBM_F64:
+            return lbmk::launch_batch<lbmk::MODE_F64>(static_cast<const lbmk::StepParams<double>*>(b->params[parity]),
+                                                      b->tiles, b->ntiles, b->chunk, b->grid, q, fl, s);
+        case LBM_F32:
+            return lbmk::launch_batch<lbmk::MODE_F32>(static_cast<const lbmk::StepParams<float>*>(b->params[parity]),
+                                                      b->tiles, b->ntiles, b->chunk, b->grid, q, fl, s);
+        case LBM_F16:
+            return lbmk::launch_batch<lbmk::MODE_F16>(static_cast<const lbmk::StepParams<float>*>(b->params[parity]),
+                                                      b->tiles, b->ntiles, b->chunk, b->grid, q, fl, s);
+        default:
+            return lbmk::launch_batch<lbmk::MODE_BF16>(static_cast<const lbmk::StepParams<float>*>(b->params[parity]),
+                                                       b->tiles, b->ntiles, b->chunk, b->grid, q, fl, s);
+    }
+}
+
+int batch_blocks_per_sm(const lbm_batch* b) {
+    switch (b->precision) {
+        case LBM_F64: return lbmk::batch_blocks_per_sm<lbmk::MODE_F64>(b->qt, b->flow);
+        case LBM_F32: return lbmk::batch_blocks_per_sm<lbmk::MODE_F32>(b->qt, b->flow);
+        case LBM_F16: return lbmk::batch_blocks_per_sm<lbmk::MODE_F16>(b->qt, b->flow);
+        default: return lbmk::batch_blocks_per_sm<lbmk::MODE_BF16>(b->qt, b->flow);
+    }
+}
+
+// Cell-to-block maps: 0 one block per tile, 1 persistent blocks over
+// contiguous chunks of tiles, 2 persistent blocks striding over the tiles.
+void set_mapping(lbm_batch* b, int mapping, int resident_blocks) {
+    b->mapping = mapping;
+    if (mapping == 0) {
+        b->grid = b->ntiles;
+        b->chunk = 1;
+    } else {
+        b->grid = std::max(1, std::min(b->ntiles, resident_blocks));
+        b->chunk = mapping == 1 ? (b->ntiles + b->grid - 1) / b->grid : 0;
+    }
+}
+
+void batch_destroy_graph(lbm_batch* b) {
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+}
+
+void free_batch(lbm_batch* b) {
+    if (!b) return;
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    batch_destroy_graph(b);
+    if (b->cap) cudaStreamDestroy(b->cap);
+    batch_free(b, b->dev);
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    cudaGetLastError();
+    delete b;
+}
+
+int build_batch_graph(lbm_batch* b) {
+    if (b->graph) return LBM_OK;
+    if (!b->cap && cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess) return LBM_ERR_CUDA;
+    if (cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return LBM_ERR_CUDA;
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < kGraphSteps && e == cudaSuccess; ++i) e = batch_launch(b, i & 1, b->cap);
+    cudaGraph_t g = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(b->cap, &g);
+    if (e != cudaSuccess || e2 != cudaSuccess || !g) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        return LBM_ERR_CUDA;
+    }
+    cudaError_t e3 = cudaGraphInstantiate(&b->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e3 != cudaSuccess) {
+        b->graph = nullptr;
+        cudaGetLastError();
+        return LBM_ERR_CUDA;
+    }
+    return LBM_OK;
+}
+
+int batch_advance(lbm_batch* b, int64_t n) {
+    auto single = [&]() -> int {
+        if (batch_launch(b, b->parity, b->stream) != cudaSuccess) {
+            cudaGetLastError();
+            return LBM_ERR_CUDA;
+        }
+        b->parity ^= 1;
+        return LBM_OK;
+    };
+    int64_t left = n;
+    while (left > 0 && b->parity != 0) {
+        if (single() != LBM_OK) return LBM_ERR_CUDA;
+        --left;
+    }
+    if (left >= kGraphSteps) {
+        if (build_batch_graph(b) != LBM_OK) return LBM_ERR_CUDA;
+        while (left >= kGraphSteps) {
+            if (cudaGraphLaunch(b->graph, b->stream) != cudaSuccess) {
+                cudaGetLastError();
+                return LBM_ERR_CUDA;
+            }
+            left -= kGraphSteps;
+        }
+    }
+    while (left > 0) {
+        if (single() != LBM_OK) return LBM_ERR_CUDA;
+        --left;
+    }
+    return LBM_OK;
+}
+
+// Times `steps` batched steps of the current configuration (microseconds per step).
+double time_batch(lbm_batch* b, int steps) {
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        cudaGetLastError();
+        return 1e30;
+    }
+    for (int i = 0; i < 4; ++i) batch_launch(b, i & 1, b->stream);
+    cudaEventRecord(e0, b->stream);
+    for (int i = 0; i < steps; ++i) batch_launch(b, i & 1, b->stream);
+    cudaEventRecord(e1, b->stream);
+    float ms = 0.0f;
+    const bool ok = cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaGetLastError();
+    return ok ? 1e3 * ms / steps : 1e30;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lbm_batch_create(lbm_handle* const* runs, int32_t n_runs, int32_t autotune, void* cuda_stream, lbm_batch** out) {
+    if (!out || !runs || n_runs < 1) return LBM_ERR_ARG;
+    *out = nullptr;
+    for (int r = 0; r < n_runs; ++r) {
+        if (!runs[r]) return LBM_ERR_ARG;
+        if (runs[r]->sticky != LBM_OK) return LBM_ERR_STATE;
+        if (runs[r]->p.precision != runs[0]->p.precision || runs[r]->p.thermal_q != runs[0]->p.thermal_q ||
+            runs[r]->p.flow != runs[0]->p.flow)
+            return LBM_ERR_ARG;
+        if (runs[r]->cur != runs[0]->cur) return LBM_ERR_STATE;
+        for (int q = 0; q < r; ++q)
+            if (runs[q] == runs[r]) return LBM_ERR_ARG;
+    }
+    lbm_batch* b = new (std::nothrow) lbm_batch();
+    if (!b) return LBM_ERR_OOM;
+    b->runs.assign(runs, runs + n_runs);
+    b->precision = runs[0]->p.precision;
+    b->qt = runs[0]->p.thermal_q;
+    b->flow = runs[0]->p.flow;
+    b->stream = static_cast<cudaStream_t>(cuda_stream);
+    b->alloc = runs[0]->alloc;
+    b->release = runs[0]->release;
+    b->ctx = runs[0]->ctx;
+    b->parity = runs[0]->cur;
+    b->params_stride = b->precision == LBM_F64 ? sizeof(lbmk::StepParams<double>) : sizeof(lbmk::StepParams<float>);
+    for (lbm_handle* h : b->runs)
+        if (cudaStreamSynchronize(h->stream) != cudaSuccess) {
+            cudaGetLastError();
+            delete b;
+            return LBM_ERR_CUDA;
+        }
+    // room for the longest tile list any width cap gives (ragged widths make wide
+    // tiles the longest list, narrow grids make narrow tiles the longest)
+    size_t max_tiles = 0;
+    for (int cap : {32, 64, 128, 256}) max_tiles = std::max(max_tiles, make_tiles(b->runs, cap).size());
+    b->tile_capacity = max_tiles;
+    const size_t bytes = 2 * (size_t)n_runs * b->params_stride + max_tiles * sizeof(lbmk::Tile);
+    b->dev = static_cast<char*>(batch_alloc(b, bytes, b->stream));
+    if (!b->dev) {
+        delete b;
+        return LBM_ERR_OOM;
+    }
+    int dev_id = 0, sms = 0;
+    cudaGetDevice(&dev_id);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev_id);
+    const int resident = std::max(1, batch_blocks_per_sm(b)) * std::max(1, sms);
+
+    int best_cap = 128, best_map = 0;
+    if (autotune) {
+        // tune on fresh clones of the runs so the runs themselves do not move
+        std::vector<lbm_handle*> clones;
+        bool ok = true;
+        for (lbm_handle* h : b->runs) {
+            lbm_handle* c = nullptr;
+            if (lbm_create_ex(&h->p, b->stream, h->alloc, h->release, h->ctx, &c) != LBM_OK) {
+                ok = false;
+                break;
+            }
+            clones.push_back(c);
+        }
+        if (ok) {
+            std::vector<lbm_handle*> keep = b->runs;
+            b->runs = clones;
+            b->parity = 0;
+            double best = 1e30;
+            for (int cap : {64, 128, 256}) {
+                if (upload_batch(b, make_tiles(b->runs, cap)) != LBM_OK) continue;
+                for (int map = 0; map < 3; ++map) {
+                    set_mapping(b, map, resident);
+                    const double us = time_batch(b, 16);
+                    if (us < best) {
+                        best = us;
+                        best_cap = cap;
+                        best_map = map;
+                    }
+                }
+            }
+            b->tuned_us = best;
+            b->runs = keep;
+        }
+        for (lbm_handle* c : clones) lbm_destroy(c);
+        b->parity = runs[0]->cur;
+    }
+    b->width_cap = best_cap;
+    if (upload_batch(b, make_tiles(b->runs, best_cap)) != LBM_OK) {
+        free_batch(b);
+        return LBM_ERR_CUDA;
+    }
+    set_mapping(b, best_map, resident);
+    *out = b;
+    return LBM_OK;
+}
+
+int lbm_batch_step(lbm_batch* b, int64_t nsteps) {
+    if (!b || nsteps < 0) return LBM_ERR_ARG;
+    for (lbm_handle* h : b->runs)
+        if (h->sticky != LBM_OK) return LBM_ERR_STATE;
+    const int rc = batch_advance(b, nsteps);
+    for (lbm_handle* h : b->runs) {
+        h->cur = b->parity;
+        if (rc == LBM_OK) h->steps += nsteps;
+        else h->sticky = LBM_ERR_CUDA;
+    }
+    return rc;
+}
+
+int lbm_batch_configure(lbm_batch* b, int32_t width_cap, int32_t mapping) {
+    if (!b || (width_cap != 32 && width_cap != 64 && width_cap != 128 && width_cap != 256) || mapping < 0 ||
+        mapping > 2)
+        return LBM_ERR_ARG;
+    if (cudaStreamSynchronize(b->stream) != cudaSuccess) {
+        cudaGetLastError();
+        return LBM_ERR_CUDA;
+    }
+    batch_destroy_graph(b);
+    const int rc = upload_batch(b, make_tiles(b->runs, width_cap));
+    if (rc != LBM_OK) return rc;
+    b->width_cap = width_cap;
+    int dev_id = 0, sms = 0;
+    cudaGetDevice(&dev_id);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev_id);
+    set_mapping(b, mapping, std::max(1, batch_blocks_per_sm(b)) * std::max(1, sms));
+    return LBM_OK;
+}
+
+int lbm_batch_info(const lbm_batch* b, int32_t* n_tiles, int32_t* width_cap, int32_t* mapping, int32_t* grid,
+                   double* tuned_us_per_step) {
+    if (!b) return LBM_ERR_ARG;
+    if (n_tiles) *n_tiles = b->ntiles;
+    if (width_cap) *width_cap = b->width_cap;
+    if (mapping) *mapping = b->mapping;
+    if (grid) *grid = b->grid;
+    if (tuned_us_per_step) *tuned_us_per_step = b->tuned_us;
+    return LBM_OK;
+}
+
+int lbm_batch_destroy(lbm_batch* b) {
+    free_batch(b);
+    return LBM_OK;
 }
 
 }  // extern "C"

@@ -553,14 +553,12 @@ __device__ __forceinline__ void store_thermal(const StepParams<typename ModeTrai
 // The fused step
 // ---------------------------------------------------------------------------
 
+// One time step of node (x, y): steps a1-a9 (pull, walls, state, blend,
+// velocity, three collisions, store).
 template <int M, int QT, bool FLOW>
-__global__ void __launch_bounds__(256) fused_step(const __grid_constant__ StepParams<typename ModeTraits<M>::R> P) {
+__device__ __forceinline__ void step_node(const StepParams<typename ModeTraits<M>::R>& P, int x, int y) {
     using R = typename ModeTraits<M>::R;
     using PL = Planes<M, QT, FLOW>;
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y * blockDim.y + threadIdx.y;
-    if (x >= P.nx || y >= P.ny) return;
-
     NodeState<M, QT, FLOW> n;
     bool wall;
     node_state<M, QT, FLOW>(P, x, y, n, wall);
@@ -650,6 +648,51 @@ __global__ void __launch_bounds__(256) fused_step(const __grid_constant__ StepPa
     const bool bad = !(fabs(n.H) < R(1e30)) || !(n.rho > R(0) && n.rho < R(1e30)) ||
                      !(n.ux * n.ux + n.uy * n.uy <= R(0.09)) || !(fabs(n.Tm) < R(1e30));
     if (bad) atomicOr(P.status, STATUS_UNSTABLE);
+}
+
+// One run: one thread per node, 128 x 2 threads per block.
+template <int M, int QT, bool FLOW>
+__global__ void __launch_bounds__(256) fused_step(const __grid_constant__ StepParams<typename ModeTraits<M>::R> P) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= P.nx || y >= P.ny) return;
+    step_node<M, QT, FLOW>(P, x, y);
+}
+
+// Many runs in one launch.  A tile is w x (256 / w) nodes of one run (w a
+// power of two, 32..256); thread t of a block takes node (x0 + t mod w,
+// y0 + t div w).  The runs' parameter blocks sit in global memory; a block
+// copies the block of its current run into shared memory when the run
+// changes.  Map: chunk > 0 gives block b the tiles [b chunk, (b+1) chunk),
+// chunk = 0 strides over the tiles by the grid size.
+struct Tile {
+    int run, x0, y0, log2w;
+};
+
+template <int M, int QT, bool FLOW>
+__global__ void __launch_bounds__(256) batch_step(const StepParams<typename ModeTraits<M>::R>* __restrict__ runs,
+                                                  const Tile* __restrict__ tiles, int ntiles, int chunk) {
+    using R = typename ModeTraits<M>::R;
+    __shared__ StepParams<R> P;
+    static_assert(sizeof(StepParams<R>) % 4 == 0, "parameter block copied as words");
+    int cached = -1;
+    const int t0 = chunk > 0 ? blockIdx.x * chunk : blockIdx.x;
+    const int t1 = chunk > 0 ? min(ntiles, t0 + chunk) : ntiles;
+    const int dt = chunk > 0 ? 1 : gridDim.x;
+    for (int t = t0; t < t1; t += dt) {
+        const Tile tl = tiles[t];
+        if (tl.run != cached) {   // uniform across the block
+            __syncthreads();
+            const int* src = reinterpret_cast<const int*>(runs + tl.run);
+            int* dst = reinterpret_cast<int*>(&P);
+            for (int i = threadIdx.x; i < (int)(sizeof(StepParams<R>) / 4); i += blockDim.x) dst[i] = __ldg(src + i);
+            __syncthreads();
+            cached = tl.run;
+        }
+        const int x = tl.x0 + (threadIdx.x & ((1 << tl.log2w) - 1));
+        const int y = tl.y0 + (threadIdx.x >> tl.log2w);
+        if (x < P.nx && y < P.ny) step_node<M, QT, FLOW>(P, x, y);
+    }
 }
 
 // Fields at the current time level (LBM_FIELD_* order).

@@ -165,13 +165,34 @@ cudaError_t launch_convert(const StepParams<float>& P, const DenseState& D, int 
     });
 }
 
+template <int M>
+cudaError_t launch_batch(const StepParams<typename ModeTraits<M>::R>* runs, const Tile* tiles, int ntiles,
+                         int chunk, int grid, int qt, int flow, cudaStream_t s) {
+    return dispatch<M>(qt, flow, [&]<int MM, int Q, bool F>() {
+        batch_step<MM, Q, F><<<grid, 256, 0, s>>>(runs, tiles, ntiles, chunk);
+        return cudaGetLastError();
+    });
+}
+
+template <int M>
+int batch_blocks_per_sm(int qt, int flow) {
+    int n = 0;
+    dispatch<M>(qt, flow, [&]<int MM, int Q, bool F>() {
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_step<MM, Q, F>, 256, 0);
+    });
+    return n;
+}
+
 #define LBMK_INSTANTIATE(M)                                                                                   \
     template cudaError_t launch_step<M>(const StepParams<ModeTraits<M>::R>&, int, int, cudaStream_t);        \
     template cudaError_t launch_fields<M>(const StepParams<ModeTraits<M>::R>&, const FieldOut<ModeTraits<M>::R>&, \
                                           int, int, cudaStream_t);                                            \
     template cudaError_t launch_diag<M>(const StepParams<ModeTraits<M>::R>&, const DiagConst&, double*, double*, \
                                         int, int, cudaStream_t);                                              \
-    template cudaError_t launch_init<M>(const StepParams<ModeTraits<M>::R>&, const InitVals&, int, int, cudaStream_t);
+    template cudaError_t launch_init<M>(const StepParams<ModeTraits<M>::R>&, const InitVals&, int, int, cudaStream_t); \
+    template cudaError_t launch_batch<M>(const StepParams<ModeTraits<M>::R>*, const Tile*, int, int, int, int, int, \
+                                         cudaStream_t);                                                         \
+    template int batch_blocks_per_sm<M>(int, int);
 
 #define LBMK_INSTANTIATE_CONVERT(M) \
     template cudaError_t launch_convert<M>(const StepParams<float>&, const DenseState&, int, int, int, cudaStream_t);

@@ -110,6 +110,16 @@ def lib() -> ctypes.CDLL:
         L.lbm_destroy.restype = ctypes.c_int
         L.lbm_strerror.argtypes = [ctypes.c_int]
         L.lbm_strerror.restype = ctypes.c_char_p
+        L.lbm_batch_create.argtypes = [ctypes.POINTER(vp), i32, i32, vp, ctypes.POINTER(vp)]
+        L.lbm_batch_create.restype = ctypes.c_int
+        L.lbm_batch_step.argtypes = [vp, i64]
+        L.lbm_batch_step.restype = ctypes.c_int
+        L.lbm_batch_configure.argtypes = [vp, i32, i32]
+        L.lbm_batch_configure.restype = ctypes.c_int
+        L.lbm_batch_info.argtypes = [vp] + [ctypes.POINTER(i32)] * 4 + [ctypes.POINTER(ctypes.c_double)]
+        L.lbm_batch_info.restype = ctypes.c_int
+        L.lbm_batch_destroy.argtypes = [vp]
+        L.lbm_batch_destroy.restype = ctypes.c_int
         L.lbm_diag_fields_noalloc.argtypes = [pp, vp, vp, vp, vp, vp, vp, vp]
         L.lbm_diag_fields_noalloc.restype = ctypes.c_int
         _lib = L
@@ -340,3 +350,46 @@ class Solver:
 
     def __exit__(self, *exc):
         self.close()
+
+
+class Batch:
+    """Runs advanced together by one launch per time step (lbm_batch_*)."""
+
+    MAPS = ("one block per tile", "persistent contiguous chunks", "persistent grid stride")
+
+    def __init__(self, runs, autotune: bool = True, stream=None):
+        import torch
+        self.runs = list(runs)
+        self.stream = stream if stream is not None else self.runs[0].stream
+        arr = (ctypes.c_void_p * len(self.runs))(*[r._h.value for r in self.runs])
+        self._b = ctypes.c_void_p()
+        with torch.cuda.device(self.runs[0].device):
+            rc = lib().lbm_batch_create(arr, len(self.runs), 1 if autotune else 0,
+                                        ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(self._b))
+        _check(rc, "lbm_batch_create")
+
+    def step(self, n: int) -> "Batch":
+        _check(lib().lbm_batch_step(self._b, int(n)), "lbm_batch_step")
+        return self
+
+    def configure(self, width_cap: int, mapping: int) -> "Batch":
+        _check(lib().lbm_batch_configure(self._b, int(width_cap), int(mapping)), "lbm_batch_configure")
+        return self
+
+    def info(self) -> dict:
+        v = [ctypes.c_int32() for _ in range(4)]
+        us = ctypes.c_double()
+        _check(lib().lbm_batch_info(self._b, *[ctypes.byref(x) for x in v], ctypes.byref(us)), "lbm_batch_info")
+        return dict(n_tiles=v[0].value, width_cap=v[1].value, mapping=self.MAPS[v[2].value], grid=v[3].value,
+                    tuned_us_per_step=us.value)
+
+    def close(self):
+        if self._b:
+            lib().lbm_batch_destroy(self._b)
+            self._b = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
