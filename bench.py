@@ -98,6 +98,10 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--batch-runs", type=int, default=64)
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=16)
+    ap.add_argument("--serve-step-scale", type=float, default=0.1,
+                    help="scale of the serving trace's step counts (log-uniform 1e4..5e5 before scaling)")
     ap.add_argument("--no-cpu", action="store_true")
     return ap.parse_args()
 
@@ -231,6 +235,39 @@ def run_reference(args):
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
+
+def bench_serving(args, lbm, inputs, stream, plain_mlups: float, seed: int = 1701):
+    """Poisson arrivals of melting runs (grids 128^2, 256^2, 512^2, 1024^2,
+    2048x1024; mixed porosity, Da, Ra, Ste), served by the plain form (FP32,
+    one request at a time in arrival order) and by continuous batching (FP16,
+    150 GB HBM budget), both replaying the same trace on the host clock."""
+    import numpy as np
+    scale = args.serve_step_scale
+    lo, hi = int(1e4 * scale), int(5e5 * scale)
+    grids = ((128, 128), (256, 256), (512, 512), (1024, 1024), (2048, 1024))
+    mean_nodes = float(np.mean([a * b for a, b in grids]))
+    mean_steps = (hi - lo) / np.log(hi / lo)
+    rate = 0.8 * plain_mlups * 1e6 / (mean_nodes * mean_steps)   # ~80 % of the plain form's capacity
+    base = inputs.serving_arrivals(count=args.serve_requests, rate_per_s=rate, seed=seed, grids=grids,
+                                   steps_lo=lo, steps_hi=hi)
+    out = {"requests": len(base), "arrival_rate_per_s": rate, "step_range": [lo, hi],
+           "note": f"step counts of the 1e4..5e5 serving trace scaled by {scale}", "forms": []}
+    for name, batched, prec in (("plain FP32 (one at a time)", False, 1), ("continuous batching FP16", True, 2)):
+        trace = [dict(r, params=dict(r["params"], precision=prec)) for r in base]
+        srv = lbm.Server(hbm_budget_bytes=150 * 10 ** 9, max_active=64, batched=batched, quantum=256,
+                         precision=prec, stream=stream)
+        res = srv.replay(trace)
+        st = srv.stats()
+        srv.close()
+        lat = np.array([r["finish_s"] - r["submit_s"] for r in res])
+        span = max(r["finish_s"] for r in res) - min(r["submit_s"] for r in res)
+        out["forms"].append({
+            "form": name, "ok": all(r["status"] == 0 for r in res),
+            "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
+            "runs_per_s": len(res) / span, "aggregate_mlups": st["node_steps"] / span / 1e6,
+            "busy_mlups": st["node_steps"] / max(st["busy_s"], 1e-9) / 1e6,
+            "peak_admitted_gb": st["peak_used_bytes"] / 1e9})
+    return out
 
 def bench_batched(args, lbm, inputs, torch, stream, steps_per_solve: int = 10_000, chunk: int = 64, reps: int = 3):
     """64 cavities, sides uniform in [64, 512], porosity, Da, Ra, Ste drawn as in
@@ -424,6 +461,10 @@ def main():
         if not args.no_batched:
             batched = bench_batched(args, lbm, inputs, torch, stream)
 
+        serving = None
+        if not args.no_serving:
+            serving = bench_serving(args, lbm, inputs, stream, roof["mlups"] if roof else 30000.0)
+
         # every storage form of the same step, on the L2-resident and the HBM-bound cavity
         forms = []
         if args.roofline_n > 0:
@@ -453,6 +494,7 @@ def main():
                         "note": "256x256 state (10 MB) is L2-resident; launch-to-launch time inside CUDA graphs"},
         "forms": forms if args.roofline_n > 0 else None,
         "batched": batched,
+        "serving": serving,
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": args.steps * chunk,

@@ -118,6 +118,10 @@ typedef struct lbm_params {
     double  T_solidus, T_liquidus;  /* T_fs <= T_fl (Eqs. 38-39) */
     double  L_char;            /* characteristic length L in lattice units */
     double  varpi;             /* ϖ of App. B, in (0, 1); used when thermal_q = 5 */
+    /* comparison variants of Sec. V (0 = the present method) */
+    int32_t thermal_collision; /* 0: MRT (Sec. III B); 1: BGK, every thermal rate = ζ_α (η_α) (Sec. V A) */
+    int32_t solid_scheme;      /* 0: volumetric blend (Eq. 20); 1: bounce-back where f_l <= 0.5, no blend (Sec. V B) */
+    double  zeta_e;            /* 0: ζ_e = 2 - ζ_α (Eq. 53); > 0: this ζ_e (and ζ_ε for D2Q9) instead (Sec. V D) */
 } lbm_params;
 
 /* Lattice-unit constants derived from lbm_params (output of lbm_derive). */
@@ -228,20 +232,22 @@ const char* lbm_strerror(int code);
 
 /*
  * Batches: many runs (cavities of unequal size and parameters) advanced
- * together by one kernel launch per time step, replayed from captured CUDA
- * graphs (the persistent, graph-captured form of Sec. III's step for many
- * independent problems; the paper itself runs one problem at a time).
+ * together, replayed from CUDA graphs (the graph-launched form of Sec. III's
+ * step for many independent problems; the paper itself runs one problem at
+ * a time).
  *
  * lbm_batch_create takes n_runs distinct handles that share precision,
- * thermal_q and flow and have taken steps of the same parity; it
- * synchronises their streams.  The work is a list of tiles (one run, w x
- * 256/w nodes, w a power of two from 32 to 256); with autotune = 1 the call
- * times every combination of tile-width cap (64, 128, 256) and cell-to-block
- * map (one block per tile, persistent blocks over contiguous chunks,
- * persistent blocks striding over the list) on freshly created copies of the
- * runs -- the runs themselves do not move, but the copies hold as much
- * device memory again while tuning -- and keeps the fastest; otherwise it
- * takes width cap 128, one block per tile.  Every node's arithmetic is the
+ * thermal_q and flow (their step counts may differ); it synchronises their
+ * streams.  Maps 0-2 launch one kernel per time step over a list of tiles
+ * (one run, w x 256/w nodes, w a power of two from 32 to 256): 0 one block
+ * per tile, 1 persistent blocks over contiguous chunks of the list, 2
+ * persistent blocks striding over the list.  Map 3 launches lbm_step's own
+ * kernel once per run and step, each run a chain of kernel nodes in one
+ * graph and the chains independent, so small runs overlap large ones.  With
+ * autotune = 1 the call times every combination of tile-width cap (64, 128,
+ * 256) and map on freshly created copies of the runs -- the runs themselves
+ * do not move, but the copies hold as much device memory again while tuning
+ * -- and keeps the fastest; otherwise it takes width cap 128, map 0.  Every node's arithmetic is the
  * same under every map, so the choice cannot change results: a batched step
  * equals lbm_step on each run.
  *
@@ -250,7 +256,8 @@ const char* lbm_strerror(int code);
  * diagnostics, checkpoints, lbm_step) only on the same stream or after
  * synchronising it.  A run whose sticky status is set stops the batch
  * (LBM_ERR_STATE).  lbm_batch_info reports the tile count, the chosen width
- * cap and map (0, 1, 2), the grid size and the tuned microseconds per step.
+ * cap and map (0-3), the grid size (0 for map 3) and the tuned microseconds
+ * per step.
  * lbm_batch_destroy synchronises and frees the batch (not its runs).
  * The batch allocates its work list and parameter blocks through the first
  * run's allocation hooks (or the CUDA stream-ordered allocator).
@@ -259,11 +266,62 @@ typedef struct lbm_batch lbm_batch;
 int lbm_batch_create(lbm_handle* const* runs, int32_t n_runs, int32_t autotune, void* cuda_stream,
                      lbm_batch** out);
 int lbm_batch_step(lbm_batch* b, int64_t nsteps);
-/* Forces a tile-width cap (32, 64, 128 or 256) and a map (0, 1, 2); synchronises. */
+/* Forces a tile-width cap (32, 64, 128 or 256) and a map (0-3); synchronises. */
 int lbm_batch_configure(lbm_batch* b, int32_t width_cap, int32_t mapping);
 int lbm_batch_info(const lbm_batch* b, int32_t* n_tiles, int32_t* width_cap, int32_t* mapping, int32_t* grid,
                    double* tuned_us_per_step);
 int lbm_batch_destroy(lbm_batch* b);
+
+/*
+ * Serving: continuous batching of melting runs.
+ *
+ * Requests (one lbm_params and a step count each) are queued by
+ * lbm_server_submit.  Every lbm_server_tick
+ *   1. admits queued requests in arrival order while fewer than max_active
+ *      runs are active and the device bytes of the active runs
+ *      (lbm_state_bytes) plus the next request's stay within hbm_budget_bytes;
+ *   2. advances all active runs together by min(quantum, the smallest number
+ *      of steps any active run still needs) through one lbm_batch (batched =
+ *      1; the batch is rebuilt when membership changes, with the tile width
+ *      cap and map of lbm_server_configure, default 128 and map 3, the runs'
+ *      own kernels in concurrent chains), then synchronises the stream;
+ *   3. retires every run that has taken its steps: its FP64 diagnostics
+ *      (lbm_diag) go into a result record and its device memory is freed.
+ * A request that arrives while others run joins them at the next tick.
+ * With batched = 0 the engine is the plain form: one request at a time, in
+ * arrival order, each advanced by lbm_step.  A run is the same alone and in
+ * a batch (batched steps equal single steps bit for bit).
+ *
+ * All requests of a server share precision, thermal_q and flow (LBM_ERR_ARG
+ * otherwise); a request whose state alone exceeds the budget is refused at
+ * submission.  Times in the results are seconds since lbm_server_create on
+ * the host clock: submission, admission, completion.  lbm_server_results
+ * moves up to max_results finished records into out.  lbm_server_stats
+ * reports node updates performed, seconds the device was busy with ticks,
+ * seconds since creation, and current and peak admitted bytes.  Device
+ * memory comes through the allocation hooks (or the stream-ordered
+ * allocator).  Not thread-safe.
+ */
+typedef struct lbm_request_result {
+    int64_t id;
+    int32_t status;            /* LBM_OK or the failure of this request */
+    int32_t reserved;
+    int64_t steps, nodes;      /* steps taken, grid nodes */
+    double submit_s, admit_s, finish_s;
+    double melt_frac, nu_hot, enthalpy, mass;   /* as lbm_diag, at the last step */
+} lbm_request_result;
+
+typedef struct lbm_server lbm_server;
+int lbm_server_create(int64_t hbm_budget_bytes, int32_t max_active, int32_t batched, int32_t quantum,
+                      int32_t precision, int32_t thermal_q, int32_t flow, void* cuda_stream, lbm_alloc_fn alloc,
+                      lbm_free_fn release, void* ctx, lbm_server** out);
+int lbm_server_configure(lbm_server* s, int32_t width_cap, int32_t mapping);
+int lbm_server_submit(lbm_server* s, const lbm_params* p, int64_t nsteps, int64_t* id);
+int lbm_server_tick(lbm_server* s, int32_t* n_active, int32_t* n_queued, int32_t* n_done);
+int lbm_server_results(lbm_server* s, lbm_request_result* out, int32_t max_results, int32_t* n);
+int lbm_server_stats(const lbm_server* s, int64_t* node_steps, double* busy_s, double* elapsed_s,
+                     int64_t* used_bytes, int64_t* peak_used_bytes);
+int lbm_server_destroy(lbm_server* s);
 
 /*
  * Allocation-free diagnostics (the paper has no counterpart; this entry

@@ -64,6 +64,7 @@ class OrcCfg(ctypes.Structure):
         ("c_mref", ctypes.c_double), ("L_a", ctypes.c_double), ("h_v", ctypes.c_double),
         ("T_fs", ctypes.c_double), ("T_fl", ctypes.c_double), ("varpi", ctypes.c_double),
         ("s", ctypes.c_double * 9), ("zeta", ctypes.c_double * 9), ("eta", ctypes.c_double * 9),
+        ("solid_scheme", ctypes.c_int),
     ]
 
 
@@ -135,6 +136,8 @@ def lattice_config(p: dict) -> dict:
     zeta_a = 1.0 / (0.5 + alpha_fref / csT2)
     eta_a = 1.0 / (0.5 + alpha_mref / csT2)
     zeta_e = 2.0 - zeta_a                                # Eq. 53
+    if float(p.get("zeta_e", 0.0)) > 0.0:                # Sec. V D: an explicit zeta_e
+        zeta_e = float(p["zeta_e"])
     s = [1.0, 1.1, 1.1, 1.0, 1.2, 1.0, 1.2, s_v, s_v]    # Eq. 16 with Sec. III C's rates
     if qt == 9:
         zeta = [1.0, zeta_e, zeta_e, zeta_a, zeta_a, zeta_a, zeta_a, 1.2, 1.2]
@@ -142,6 +145,9 @@ def lattice_config(p: dict) -> dict:
     else:
         zeta = [1.0, zeta_a, zeta_a, zeta_e, 1.2] + [0.0] * 4
         eta = [1.0, eta_a, eta_a, 1.1, 1.2] + [0.0] * 4
+    if int(p.get("thermal_collision", 0)) == 1:          # Sec. V A: BGK, one rate per lattice
+        zeta = [zeta_a] * qt + [0.0] * (9 - qt)
+        eta = [eta_a] * qt + [0.0] * (9 - qt)
     F_phi = float(p["F_phi"])
     return dict(
         nx=int(p["nx"]), ny=int(p["ny"]), qt=qt, flow=int(p["flow"]),
@@ -150,7 +156,7 @@ def lattice_config(p: dict) -> dict:
         phi=phi, nu_f=nu_f, nu_e=nu_e, K=K, F_phi=F_phi, gbeta=gbeta, T0=float(p["T_ref0"]),
         rho_l=rho_l, rho_m=rho_m, c_pl=c_pl, c_ps=c_ps, c_pm=c_pm, c_fref=c_fref, c_mref=c_mref,
         L_a=L_a, h_v=h_v, T_fs=float(p["T_solidus"]), T_fl=float(p["T_liquidus"]), varpi=varpi,
-        s=s, zeta=zeta, eta=eta,
+        s=s, zeta=zeta, eta=eta, solid_scheme=int(p.get("solid_scheme", 0)),
         # informational
         alpha_f=alpha_f, alpha_fref=alpha_fref, alpha_mref=alpha_mref, k_f=k_f, k_m=k_m,
         d_p=d_p, s_v=s_v, zeta_a=zeta_a, zeta_e=zeta_e, eta_a=eta_a, csT2=csT2,

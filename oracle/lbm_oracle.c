@@ -32,6 +32,12 @@
  *   - zeta_0 = eta_0 = 1 (they multiply n_0 - n_0^eq = 0 anyway).
  *   - D2Q5 (App. B): varpi is an input, zeta_e = 2 - zeta_alpha,
  *     zeta_epsilon = 1.2, eta_e = 1.1, eta_epsilon = 1.2 (set by the caller).
+ *   - Comparison variants of Sec. V: BGK thermal collision is the rate vector
+ *     with every entry zeta_alpha (eta_alpha), set by the caller; the
+ *     bounce-back solid scheme (solid_scheme = 1) drops the blend of Eq. 20,
+ *     treats nodes with f_l <= 0.5 as solid -- their arriving flow populations
+ *     are sent back the way they came, f*_i = f+_opp(i), and u = 0 there --
+ *     and collides the others with f = f+.
  *
  * Storage: every distribution array is [q][ny][nx] (row-major, x fastest);
  * the stored values are the post-collision populations f*, g*, h* of the
@@ -60,6 +66,7 @@ typedef struct orc_cfg {
     double s[9];       /* flow relaxation diag, Eq. 16 */
     double zeta[9];    /* PCM relaxation diag, Theta (Eq. 31 / App. B) */
     double eta[9];     /* metal relaxation diag, Q (Eq. 42 / App. B) */
+    int solid_scheme;  /* 0: volumetric blend (Eq. 20); 1: bounce-back where f_l <= 0.5 (Sec. V B, ref. 62) */
 } orc_cfg;
 
 /* ------------------------------------------------------------------ */
@@ -364,12 +371,16 @@ static void flow_state(const orc_cfg* c, const tables* t, node* n, int wall) {
     }
     double rho = 0.0;
     for (int i = 0; i < 9; ++i) rho += n->fp[i];
-    double fe0[9];
-    f_eq(c, t, rho, 0.0, 0.0, fe0);
-    for (int i = 0; i < 9; ++i) n->f[i] = n->fl * n->fp[i] + (1.0 - n->fl) * fe0[i];
+    if (c->solid_scheme == 1) {
+        for (int i = 0; i < 9; ++i) n->f[i] = n->fp[i];
+    } else {
+        double fe0[9];
+        f_eq(c, t, rho, 0.0, 0.0, fe0);
+        for (int i = 0; i < 9; ++i) n->f[i] = n->fl * n->fp[i] + (1.0 - n->fl) * fe0[i];
+    }
     n->rho = rho;
     n->Gy = c->gbeta * (n->Tf - c->T0) * n->fl;   /* G = -g beta (T_f - T_0) f_l, g along -y */
-    if (wall) { n->ux = 0.0; n->uy = 0.0; return; }
+    if (wall || (c->solid_scheme == 1 && n->fl <= 0.5)) { n->ux = 0.0; n->uy = 0.0; return; }
     double jx = 0.0, jy = 0.0;
     for (int i = 0; i < 9; ++i) { jx += t->ex[i] * n->f[i]; jy += t->ey[i] * n->f[i]; }
     velocity(c, rho, jx, jy, n->Gy, &n->ux, &n->uy);
@@ -425,7 +436,12 @@ static void node_state(const orc_cfg* c, const tables* t, const double* F, const
 /* Collision of the three lattices at one node; writes post-collision values. */
 static void collide(const orc_cfg* c, const tables* t, const node* n, double dT_prev,
                     double* fs, double* gs, double* hs, double* dT_now) {
-    if (c->flow) {
+    if (c->flow && c->solid_scheme == 1 && n->fl <= 0.5) {
+        /* bounce-back: each arriving population leaves along the opposite link */
+        for (int i = 0; i < 9; ++i)
+            for (int j = 0; j < 9; ++j)
+                if (t->ex[j] == -t->ex[i] && t->ey[j] == -t->ey[i]) fs[i] = n->fp[j];
+    } else if (c->flow) {
         /* Eq. 3 */
         double um = sqrt(n->ux * n->ux + n->uy * n->uy);
         double Fx = -c->phi * c->nu_f / c->K * n->ux - c->phi * c->F_phi / sqrt(c->K) * um * n->ux;

@@ -17,7 +17,8 @@ ROOT = PKG.parent
 CSRC = PKG / "csrc"
 OUT = PKG / "_build"
 LIB = OUT / "liblbm_gb300.so"
-SOURCES = ["lbm_api.cu", "lbm_kernels_f32.cu", "lbm_kernels_f64.cu", "lbm_kernels_f16.cu", "lbm_noalloc.cu"]
+SOURCES = ["lbm_api.cu", "lbm_kernels_f32.cu", "lbm_kernels_f64.cu", "lbm_kernels_f16.cu", "lbm_noalloc.cu",
+           "lbm_server.cu"]
 GENCODE = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -55,6 +55,9 @@ int derive_impl(const lbm_params* pp, lbm_derived* out) {
     if (!(p.cond_ratio > 0.0) || !(p.Nu_i >= 0.0)) return LBM_ERR_ARG;
     if (!(p.T_liquidus >= p.T_solidus) || p.T_hot == p.T_cold) return LBM_ERR_ARG;
     if (p.thermal_q == 5 && !(p.varpi > 0.0 && p.varpi < 1.0)) return LBM_ERR_ARG;
+    if ((p.thermal_collision != 0 && p.thermal_collision != 1) || (p.solid_scheme != 0 && p.solid_scheme != 1))
+        return LBM_ERR_ARG;
+    if (!finite(p.zeta_e) || p.zeta_e < 0.0) return LBM_ERR_ARG;
     if (p.flow) {
         const double fv[] = {p.Ra, p.Pr, p.Da, p.J, p.F_phi};
         for (double v : fv)
@@ -91,7 +94,7 @@ int derive_impl(const lbm_params* pp, lbm_derived* out) {
     const double s_v = p.flow ? 1.0 / (0.5 + d.nu_e / cs2) : 1.0;
     const double za = 1.0 / (0.5 + d.alpha_fref / d.csT2);
     const double ea = 1.0 / (0.5 + d.alpha_mref / d.csT2);
-    const double ze = 2.0 - za;                        // Eq. 53
+    const double ze = p.zeta_e > 0.0 ? p.zeta_e : 2.0 - za;   // Eq. 53, or Sec. V D's explicit value
     const double s9[9] = {1.0, 1.1, 1.1, 1.0, 1.2, 1.0, 1.2, s_v, s_v};
     std::memcpy(d.s, s9, sizeof s9);
     if (p.thermal_q == 9) {
@@ -105,6 +108,11 @@ int derive_impl(const lbm_params* pp, lbm_derived* out) {
         std::memcpy(d.zeta, z5, sizeof z5);
         std::memcpy(d.eta, e5, sizeof e5);
     }
+    if (p.thermal_collision == 1)                      // Sec. V A: BGK thermal lattices
+        for (int k = 0; k < p.thermal_q; ++k) {
+            d.zeta[k] = za;
+            d.eta[k] = ea;
+        }
     if (p.flow) {
         d.l0 = 0.5 * (1.0 + phi * 0.5 * d.nu_f / d.K);  // Eq. 25
         d.l1 = phi * 0.5 * p.F_phi / std::sqrt(d.K);
@@ -226,6 +234,7 @@ lbmk::StepParams<R> make_params(const lbm_handle* h, int from) {
     P.plane = h->L.plane;
     P.per_x = p.periodic_x;
     P.per_y = p.periodic_y;
+    P.solid_scheme = p.solid_scheme;
     for (int s = 0; s < 4; ++s) {
         P.wall_kind[s] = p.wall_kind[s];
         P.wall_T[s] = (R)p.wall_T[s];
@@ -808,9 +817,10 @@ struct lbm_batch {
     lbm_alloc_fn alloc = nullptr;
     lbm_free_fn release = nullptr;
     void* ctx = nullptr;
-    char* dev = nullptr;          // params[2][n] then tiles
+    char* dev = nullptr;          // params[n][2] then tiles
     size_t params_stride = 0;     // bytes of one StepParams
-    void* params[2] = {nullptr, nullptr};
+    void* params = nullptr;
+    std::vector<int> flip;        // run's current copy relative to the batch parity at creation
     lbmk::Tile* tiles = nullptr;
     size_t tile_capacity = 0;     // tiles that fit in the allocation
     int ntiles = 0, width_cap = 128, chunk = 1, grid = 0, parity = 0, mapping = 0;
@@ -826,7 +836,8 @@ int pow2_at_least(int v) {
     return p;
 }
 
-std::vector<lbmk::Tile> make_tiles(const std::vector<lbm_handle*>& runs, int width_cap) {
+std::vector<lbmk::Tile> make_tiles(const std::vector<lbm_handle*>& runs, const std::vector<int>& flip,
+                                   int width_cap) {
     std::vector<lbmk::Tile> t;
     for (int r = 0; r < (int)runs.size(); ++r) {
         const int nx = runs[r]->p.nx, ny = runs[r]->p.ny;
@@ -834,8 +845,9 @@ std::vector<lbmk::Tile> make_tiles(const std::vector<lbm_handle*>& runs, int wid
         int lg = 0;
         while ((1 << lg) < w) ++lg;
         const int h = 256 / w;
+        const int code = lg | ((flip.empty() ? 0 : flip[r]) << 8);
         for (int y0 = 0; y0 < ny; y0 += h)
-            for (int x0 = 0; x0 < nx; x0 += w) t.push_back({r, x0, y0, lg});
+            for (int x0 = 0; x0 < nx; x0 += w) t.push_back({r, x0, y0, code});
     }
     return t;
 }
@@ -857,32 +869,28 @@ void batch_free(lbm_batch* b, void* p) {
 }
 
 template <typename R>
-void fill_params(lbm_batch* b, std::vector<char>& host, int parity) {
-    for (size_t r = 0; r < b->runs.size(); ++r) {
-        const lbmk::StepParams<R> P = make_params<R>(b->runs[r], parity);
-        std::memcpy(host.data() + r * sizeof P, &P, sizeof P);
-    }
+void fill_params(lbm_batch* b, std::vector<char>& host) {
+    for (size_t r = 0; r < b->runs.size(); ++r)
+        for (int dir = 0; dir < 2; ++dir) {
+            const lbmk::StepParams<R> P = make_params<R>(b->runs[r], dir);
+            std::memcpy(host.data() + (2 * r + dir) * sizeof P, &P, sizeof P);
+        }
 }
 
-// Writes params for both parities and the tiles of width_cap into b->dev.
+// Writes the runs' parameter blocks ([run][direction]) and the tiles into b->dev.
 int upload_batch(lbm_batch* b, const std::vector<lbmk::Tile>& tiles) {
     const size_t n = b->runs.size();
     if (tiles.size() > b->tile_capacity) return LBM_ERR_ARG;
     std::vector<char> host(2 * n * b->params_stride + tiles.size() * sizeof(lbmk::Tile));
-    std::vector<char> one(n * b->params_stride);
-    for (int par = 0; par < 2; ++par) {
-        if (b->precision == LBM_F64) fill_params<double>(b, one, par);
-        else fill_params<float>(b, one, par);
-        std::memcpy(host.data() + par * n * b->params_stride, one.data(), one.size());
-    }
+    if (b->precision == LBM_F64) fill_params<double>(b, host);
+    else fill_params<float>(b, host);
     std::memcpy(host.data() + 2 * n * b->params_stride, tiles.data(), tiles.size() * sizeof(lbmk::Tile));
     if (cudaMemcpyAsync(b->dev, host.data(), host.size(), cudaMemcpyHostToDevice, b->stream) != cudaSuccess ||
         cudaStreamSynchronize(b->stream) != cudaSuccess) {
         cudaGetLastError();
         return LBM_ERR_CUDA;
     }
-    b->params[0] = b->dev;
-    b->params[1] = b->dev + n * b->params_stride;
+    b->params = b->dev;
     b->tiles = reinterpret_cast<lbmk::Tile*>(b->dev + 2 * n * b->params_stride);
     b->ntiles = (int)tiles.size();
     return LBM_OK;
@@ -890,19 +898,17 @@ int upload_batch(lbm_batch* b, const std::vector<lbmk::Tile>& tiles) {
 
 cudaError_t batch_launch(lbm_batch* b, int parity, cudaStream_t s) {
     const int q = b->qt, fl = b->flow;
+    const auto* pf = static_cast<const lbmk::StepParams<float>*>(b->params);
     switch (b->precision) {
         case LBM_F64:
-            return lbmk::launch_batch<lbmk::MODE_F64>(static_cast<const lbmk::StepParams<double>*>(b->params[parity]),
-                                                      b->tiles, b->ntiles, b->chunk, b->grid, q, fl, s);
+            return lbmk::launch_batch<lbmk::MODE_F64>(static_cast<const lbmk::StepParams<double>*>(b->params),
+                                                      b->tiles, b->ntiles, b->chunk, b->grid, parity, q, fl, s);
         case LBM_F32:
-            return lbmk::launch_batch<lbmk::MODE_F32>(static_cast<const lbmk::StepParams<float>*>(b->params[parity]),
-                                                      b->tiles, b->ntiles, b->chunk, b->grid, q, fl, s);
+            return lbmk::launch_batch<lbmk::MODE_F32>(pf, b->tiles, b->ntiles, b->chunk, b->grid, parity, q, fl, s);
         case LBM_F16:
-            return lbmk::launch_batch<lbmk::MODE_F16>(static_cast<const lbmk::StepParams<float>*>(b->params[parity]),
-                                                      b->tiles, b->ntiles, b->chunk, b->grid, q, fl, s);
+            return lbmk::launch_batch<lbmk::MODE_F16>(pf, b->tiles, b->ntiles, b->chunk, b->grid, parity, q, fl, s);
         default:
-            return lbmk::launch_batch<lbmk::MODE_BF16>(static_cast<const lbmk::StepParams<float>*>(b->params[parity]),
-                                                       b->tiles, b->ntiles, b->chunk, b->grid, q, fl, s);
+            return lbmk::launch_batch<lbmk::MODE_BF16>(pf, b->tiles, b->ntiles, b->chunk, b->grid, parity, q, fl, s);
     }
 }
 
@@ -916,10 +922,15 @@ int batch_blocks_per_sm(const lbm_batch* b) {
 }
 
 // Cell-to-block maps: 0 one block per tile, 1 persistent blocks over
-// contiguous chunks of tiles, 2 persistent blocks striding over the tiles.
+// contiguous chunks of tiles, 2 persistent blocks striding over the tiles,
+// 3 one single-run kernel per run and step, the runs' chains concurrent in
+// one graph.
 void set_mapping(lbm_batch* b, int mapping, int resident_blocks) {
     b->mapping = mapping;
-    if (mapping == 0) {
+    if (mapping == 3) {
+        b->grid = 0;
+        b->chunk = 0;
+    } else if (mapping == 0) {
         b->grid = b->ntiles;
         b->chunk = 1;
     } else {
@@ -944,8 +955,63 @@ void free_batch(lbm_batch* b) {
     delete b;
 }
 
+const void* step_kernel_of(int precision, int qt, int flow) {
+    switch (precision) {
+        case LBM_F64: return lbmk::step_kernel<lbmk::MODE_F64>(qt, flow);
+        case LBM_F32: return lbmk::step_kernel<lbmk::MODE_F32>(qt, flow);
+        case LBM_F16: return lbmk::step_kernel<lbmk::MODE_F16>(qt, flow);
+        default: return lbmk::step_kernel<lbmk::MODE_BF16>(qt, flow);
+    }
+}
+
+// Map 3: a graph of `steps` steps with one chain of kernel nodes per run; a
+// run's step k reads the copy flip ^ (k mod 2), starting from batch parity 0.
+int build_chain_graph(lbm_batch* b, int steps, cudaGraphExec_t* out) {
+    cudaGraph_t g = nullptr;
+    if (cudaGraphCreate(&g, 0) != cudaSuccess) return LBM_ERR_CUDA;
+    const void* fn = step_kernel_of(b->precision, b->qt, b->flow);
+    cudaError_t e = cudaSuccess;
+    for (size_t r = 0; r < b->runs.size() && e == cudaSuccess; ++r) {
+        lbm_handle* h = b->runs[r];
+        cudaGraphNode_t prev = nullptr;
+        for (int k = 0; k < steps && e == cudaSuccess; ++k) {
+            const int from = b->flip[r] ^ (k & 1);
+            lbmk::StepParams<double> Pd;
+            lbmk::StepParams<float> Pf;
+            void* args[1];
+            if (b->precision == LBM_F64) {
+                Pd = make_params<double>(h, from);
+                args[0] = &Pd;
+            } else {
+                Pf = make_params<float>(h, from);
+                args[0] = &Pf;
+            }
+            cudaKernelNodeParams kp = {};
+            kp.func = const_cast<void*>(fn);
+            kp.gridDim = lbmk::grid_for(h->p.nx, h->p.ny);
+            kp.blockDim = dim3(lbmk::kBlockX, lbmk::kBlockY);
+            kp.sharedMemBytes = 0;
+            kp.kernelParams = args;
+            kp.extra = nullptr;
+            cudaGraphNode_t node = nullptr;
+            e = cudaGraphAddKernelNode(&node, g, prev ? &prev : nullptr, prev ? 1 : 0, &kp);
+            prev = node;
+        }
+    }
+    cudaGraphExec_t exec = nullptr;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return LBM_ERR_CUDA;
+    }
+    *out = exec;
+    return LBM_OK;
+}
+
 int build_batch_graph(lbm_batch* b) {
     if (b->graph) return LBM_OK;
+    if (b->mapping == 3) return build_chain_graph(b, kGraphSteps, &b->graph);
     if (!b->cap && cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess) return LBM_ERR_CUDA;
     if (cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return LBM_ERR_CUDA;
     cudaError_t e = cudaSuccess;
@@ -969,7 +1035,14 @@ int build_batch_graph(lbm_batch* b) {
 
 int batch_advance(lbm_batch* b, int64_t n) {
     auto single = [&]() -> int {
-        if (batch_launch(b, b->parity, b->stream) != cudaSuccess) {
+        cudaError_t e = cudaSuccess;
+        if (b->mapping == 3) {
+            for (size_t r = 0; r < b->runs.size() && e == cudaSuccess; ++r)
+                e = enqueue_one(b->runs[r], b->flip[r] ^ b->parity, b->stream);
+        } else {
+            e = batch_launch(b, b->parity, b->stream);
+        }
+        if (e != cudaSuccess) {
             cudaGetLastError();
             return LBM_ERR_CUDA;
         }
@@ -1005,10 +1078,24 @@ double time_batch(lbm_batch* b, int steps) {
         cudaGetLastError();
         return 1e30;
     }
-    for (int i = 0; i < 4; ++i) batch_launch(b, i & 1, b->stream);
+    cudaGraphExec_t g = nullptr;
+    if (b->mapping == 3 && build_chain_graph(b, steps, &g) != LBM_OK) {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        return 1e30;
+    }
+    if (g) cudaGraphLaunch(g, b->stream);
+    else
+        for (int i = 0; i < 4; ++i) batch_launch(b, i & 1, b->stream);
     cudaEventRecord(e0, b->stream);
-    for (int i = 0; i < steps; ++i) batch_launch(b, i & 1, b->stream);
+    if (g) cudaGraphLaunch(g, b->stream);
+    else
+        for (int i = 0; i < steps; ++i) batch_launch(b, i & 1, b->stream);
     cudaEventRecord(e1, b->stream);
+    if (g) {
+        cudaStreamSynchronize(b->stream);
+        cudaGraphExecDestroy(g);
+    }
     float ms = 0.0f;
     const bool ok = cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess;
     cudaEventDestroy(e0);
@@ -1030,7 +1117,6 @@ int lbm_batch_create(lbm_handle* const* runs, int32_t n_runs, int32_t autotune, 
         if (runs[r]->p.precision != runs[0]->p.precision || runs[r]->p.thermal_q != runs[0]->p.thermal_q ||
             runs[r]->p.flow != runs[0]->p.flow)
             return LBM_ERR_ARG;
-        if (runs[r]->cur != runs[0]->cur) return LBM_ERR_STATE;
         for (int q = 0; q < r; ++q)
             if (runs[q] == runs[r]) return LBM_ERR_ARG;
     }
@@ -1044,7 +1130,8 @@ int lbm_batch_create(lbm_handle* const* runs, int32_t n_runs, int32_t autotune, 
     b->alloc = runs[0]->alloc;
     b->release = runs[0]->release;
     b->ctx = runs[0]->ctx;
-    b->parity = runs[0]->cur;
+    b->parity = 0;
+    for (int r = 0; r < n_runs; ++r) b->flip.push_back(runs[r]->cur);
     b->params_stride = b->precision == LBM_F64 ? sizeof(lbmk::StepParams<double>) : sizeof(lbmk::StepParams<float>);
     for (lbm_handle* h : b->runs)
         if (cudaStreamSynchronize(h->stream) != cudaSuccess) {
@@ -1055,7 +1142,7 @@ int lbm_batch_create(lbm_handle* const* runs, int32_t n_runs, int32_t autotune, 
     // room for the longest tile list any width cap gives (ragged widths make wide
     // tiles the longest list, narrow grids make narrow tiles the longest)
     size_t max_tiles = 0;
-    for (int cap : {32, 64, 128, 256}) max_tiles = std::max(max_tiles, make_tiles(b->runs, cap).size());
+    for (int cap : {32, 64, 128, 256}) max_tiles = std::max(max_tiles, make_tiles(b->runs, b->flip, cap).size());
     b->tile_capacity = max_tiles;
     const size_t bytes = 2 * (size_t)n_runs * b->params_stride + max_tiles * sizeof(lbmk::Tile);
     b->dev = static_cast<char*>(batch_alloc(b, bytes, b->stream));
@@ -1086,9 +1173,12 @@ int lbm_batch_create(lbm_handle* const* runs, int32_t n_runs, int32_t autotune, 
             b->runs = clones;
             b->parity = 0;
             double best = 1e30;
+            std::vector<int> keep_flip(clones.size(), 0);   // fresh clones all start on copy 0
+            b->flip.swap(keep_flip);
             for (int cap : {64, 128, 256}) {
-                if (upload_batch(b, make_tiles(b->runs, cap)) != LBM_OK) continue;
-                for (int map = 0; map < 3; ++map) {
+                if (upload_batch(b, make_tiles(b->runs, b->flip, cap)) != LBM_OK) continue;
+                for (int map = 0; map < 4; ++map) {
+                    if (map == 3 && cap != 128) continue;   // the single-run kernels do not use tiles
                     set_mapping(b, map, resident);
                     const double us = time_batch(b, 16);
                     if (us < best) {
@@ -1098,14 +1188,15 @@ int lbm_batch_create(lbm_handle* const* runs, int32_t n_runs, int32_t autotune, 
                     }
                 }
             }
+            b->flip.swap(keep_flip);
             b->tuned_us = best;
             b->runs = keep;
         }
         for (lbm_handle* c : clones) lbm_destroy(c);
-        b->parity = runs[0]->cur;
+        b->parity = 0;
     }
     b->width_cap = best_cap;
-    if (upload_batch(b, make_tiles(b->runs, best_cap)) != LBM_OK) {
+    if (upload_batch(b, make_tiles(b->runs, b->flip, best_cap)) != LBM_OK) {
         free_batch(b);
         return LBM_ERR_CUDA;
     }
@@ -1119,8 +1210,9 @@ int lbm_batch_step(lbm_batch* b, int64_t nsteps) {
     for (lbm_handle* h : b->runs)
         if (h->sticky != LBM_OK) return LBM_ERR_STATE;
     const int rc = batch_advance(b, nsteps);
-    for (lbm_handle* h : b->runs) {
-        h->cur = b->parity;
+    for (size_t r = 0; r < b->runs.size(); ++r) {
+        lbm_handle* h = b->runs[r];
+        h->cur = b->flip[r] ^ b->parity;
         if (rc == LBM_OK) h->steps += nsteps;
         else h->sticky = LBM_ERR_CUDA;
     }
@@ -1129,14 +1221,14 @@ int lbm_batch_step(lbm_batch* b, int64_t nsteps) {
 
 int lbm_batch_configure(lbm_batch* b, int32_t width_cap, int32_t mapping) {
     if (!b || (width_cap != 32 && width_cap != 64 && width_cap != 128 && width_cap != 256) || mapping < 0 ||
-        mapping > 2)
+        mapping > 3)
         return LBM_ERR_ARG;
     if (cudaStreamSynchronize(b->stream) != cudaSuccess) {
         cudaGetLastError();
         return LBM_ERR_CUDA;
     }
     batch_destroy_graph(b);
-    const int rc = upload_batch(b, make_tiles(b->runs, width_cap));
+    const int rc = upload_batch(b, make_tiles(b->runs, b->flip, width_cap));
     if (rc != LBM_OK) return rc;
     b->width_cap = width_cap;
     int dev_id = 0, sms = 0;

@@ -98,6 +98,7 @@ struct StepParams {
     int nx, ny, pitch;
     long long plane;     // ny * pitch
     int per_x, per_y;
+    int solid_scheme;    // 0: volumetric blend; 1: bounce-back where f_l <= 0.5 (Sec. V B)
     int wall_kind[4];
     R wall_T[4], wall_T_lo[4], wall_H[4], wall_H_lo[4];
     R fscale, finv;      // flow deviations are stored times fscale (a power of two)
@@ -410,14 +411,16 @@ __device__ __forceinline__ void macro(const StepParams<typename ModeTraits<M>::R
         n.drho = n.mp[0];
         n.rho = R(1) + n.drho;
         n.Gy = P.gbeta * (n.Tf - P.T0) * n.fl;
-        if (wall) {
+        if (wall || (P.solid_scheme && n.fl <= R(0.5))) {
             n.ux = R(0);
             n.uy = R(0);
         } else {
-            // Eq. 24 with sum_i e_i f_i = f_l sum_i e_i f+_i (the equilibrium at rest carries no momentum)
+            // Eq. 24 with sum_i e_i f_i = f_l sum_i e_i f+_i (the equilibrium at rest carries no
+            // momentum); without the blend (bounce-back variant) sum_i e_i f_i = sum_i e_i f+_i
             const R ir = fast_rcp(n.rho);
-            const R vx = n.fl * n.mp[3] * ir;
-            const R vy = n.fl * n.mp[5] * ir + R(0.5) * P.phi * n.Gy;
+            const R a = P.solid_scheme ? R(1) : n.fl;
+            const R vx = a * n.mp[3] * ir;
+            const R vy = a * n.mp[5] * ir + R(0.5) * P.phi * n.Gy;
             const R vm = fast_sqrt(vx * vx + vy * vy);
             const R den = fast_rcp(P.l0 + fast_sqrt(P.l0sq + P.l1 * vm));   // Eq. 23
             n.ux = vx * den;
@@ -566,16 +569,30 @@ __device__ __forceinline__ void step_node(const StepParams<typename ModeTraits<M
     const int o = y * P.pitch + x;
 
     if constexpr (FLOW) {
+      if (P.solid_scheme && n.fl <= R(0.5)) {
+        // bounce-back solid node: f*_i = f+_opp(i); reversing every link flips the
+        // sign of the odd moments (j, q) and keeps the even ones (deviation form too)
+        n.mp[3] = -n.mp[3]; n.mp[4] = -n.mp[4]; n.mp[5] = -n.mp[5]; n.mp[6] = -n.mp[6];
+        R f[9];
+        f_from_m9(n.mp, f);
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            if constexpr (M == MODE_F16) f[k] *= R(1024.0);
+            stb<M>(P.dst[k], o, f[k]);
+        }
+      } else {
         // Eq. 3 at the node's velocity (u = u_b = 0 on walls)
         const R um = fast_sqrt(n.ux * n.ux + n.uy * n.uy);
         const R drag = P.drag_lin + P.drag_forch * um;
         const R Fx = -drag * n.ux;
         const R Fy = -drag * n.uy + P.phi * n.Gy;
-        // blended moments (Eq. 20 in moment space, deviation form)
+        // blended moments (Eq. 20 in moment space, deviation form); no blend in the
+        // bounce-back variant
         R m[9];
-        const R sol = (R(1) - n.fl) * n.drho;
+        const R fb = P.solid_scheme ? R(1) : n.fl;
+        const R sol = (R(1) - fb) * n.drho;
 #pragma unroll
-        for (int k = 0; k < 9; ++k) m[k] = n.fl * n.mp[k];
+        for (int k = 0; k < 9; ++k) m[k] = fb * n.mp[k];
         m[0] += sol;
         m[1] -= R(2) * sol;
         m[2] += sol;
@@ -595,6 +612,7 @@ __device__ __forceinline__ void step_node(const StepParams<typename ModeTraits<M
             if constexpr (M == MODE_F16) f[k] *= R(1024.0);
             stb<M>(P.dst[k], o, f[k]);
         }
+      }
     }
 
     // exchange sources, Eqs. 36 and 47 with the backward difference of Remark III
@@ -661,17 +679,19 @@ __global__ void __launch_bounds__(256) fused_step(const __grid_constant__ StepPa
 
 // Many runs in one launch.  A tile is w x (256 / w) nodes of one run (w a
 // power of two, 32..256); thread t of a block takes node (x0 + t mod w,
-// y0 + t div w).  The runs' parameter blocks sit in global memory; a block
-// copies the block of its current run into shared memory when the run
-// changes.  Map: chunk > 0 gives block b the tiles [b chunk, (b+1) chunk),
-// chunk = 0 strides over the tiles by the grid size.
+// y0 + t div w).  Each run has two parameter blocks in global memory, one per
+// ping-pong direction ([run][2]); a run whose current copy differs from the
+// batch's parity carries flip = 1 in its tiles.  A block copies the block of
+// its current run into shared memory when the run changes.  Map: chunk > 0
+// gives block b the tiles [b chunk, (b+1) chunk), chunk = 0 strides over the
+// tiles by the grid size.
 struct Tile {
-    int run, x0, y0, log2w;
+    int run, x0, y0, log2w_flip;   // log2 w in bits 0-7, flip in bit 8
 };
 
 template <int M, int QT, bool FLOW>
 __global__ void __launch_bounds__(256) batch_step(const StepParams<typename ModeTraits<M>::R>* __restrict__ runs,
-                                                  const Tile* __restrict__ tiles, int ntiles, int chunk) {
+                                                  const Tile* __restrict__ tiles, int ntiles, int chunk, int parity) {
     using R = typename ModeTraits<M>::R;
     __shared__ StepParams<R> P;
     static_assert(sizeof(StepParams<R>) % 4 == 0, "parameter block copied as words");
@@ -683,14 +703,16 @@ __global__ void __launch_bounds__(256) batch_step(const StepParams<typename Mode
         const Tile tl = tiles[t];
         if (tl.run != cached) {   // uniform across the block
             __syncthreads();
-            const int* src = reinterpret_cast<const int*>(runs + tl.run);
+            const int dir = parity ^ ((tl.log2w_flip >> 8) & 1);
+            const int* src = reinterpret_cast<const int*>(runs + 2 * tl.run + dir);
             int* dst = reinterpret_cast<int*>(&P);
             for (int i = threadIdx.x; i < (int)(sizeof(StepParams<R>) / 4); i += blockDim.x) dst[i] = __ldg(src + i);
             __syncthreads();
             cached = tl.run;
         }
-        const int x = tl.x0 + (threadIdx.x & ((1 << tl.log2w) - 1));
-        const int y = tl.y0 + (threadIdx.x >> tl.log2w);
+        const int lg = tl.log2w_flip & 0xff;
+        const int x = tl.x0 + (threadIdx.x & ((1 << lg) - 1));
+        const int y = tl.y0 + (threadIdx.x >> lg);
         if (x < P.nx && y < P.ny) step_node<M, QT, FLOW>(P, x, y);
     }
 }

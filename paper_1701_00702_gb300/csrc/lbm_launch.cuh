@@ -167,11 +167,19 @@ cudaError_t launch_convert(const StepParams<float>& P, const DenseState& D, int 
 
 template <int M>
 cudaError_t launch_batch(const StepParams<typename ModeTraits<M>::R>* runs, const Tile* tiles, int ntiles,
-                         int chunk, int grid, int qt, int flow, cudaStream_t s) {
+                         int chunk, int grid, int parity, int qt, int flow, cudaStream_t s) {
     return dispatch<M>(qt, flow, [&]<int MM, int Q, bool F>() {
-        batch_step<MM, Q, F><<<grid, 256, 0, s>>>(runs, tiles, ntiles, chunk);
+        batch_step<MM, Q, F><<<grid, 256, 0, s>>>(runs, tiles, ntiles, chunk, parity);
         return cudaGetLastError();
     });
+}
+
+// The single-run kernel as a function pointer, for kernel nodes built
+// directly into a graph (one chain of steps per run).
+template <int M>
+const void* step_kernel(int qt, int flow) {
+    if (qt == 5) return flow ? (const void*)fused_step<M, 5, true> : (const void*)fused_step<M, 5, false>;
+    return flow ? (const void*)fused_step<M, 9, true> : (const void*)fused_step<M, 9, false>;
 }
 
 template <int M>
@@ -191,8 +199,9 @@ int batch_blocks_per_sm(int qt, int flow) {
                                         int, int, cudaStream_t);                                              \
     template cudaError_t launch_init<M>(const StepParams<ModeTraits<M>::R>&, const InitVals&, int, int, cudaStream_t); \
     template cudaError_t launch_batch<M>(const StepParams<ModeTraits<M>::R>*, const Tile*, int, int, int, int, int, \
-                                         cudaStream_t);                                                         \
-    template int batch_blocks_per_sm<M>(int, int);
+                                         int, cudaStream_t);                                                    \
+    template int batch_blocks_per_sm<M>(int, int);                                                        \
+    template const void* step_kernel<M>(int, int);
 
 #define LBMK_INSTANTIATE_CONVERT(M) \
     template cudaError_t launch_convert<M>(const StepParams<float>&, const DenseState&, int, int, int, cudaStream_t);

@@ -40,6 +40,7 @@ def paper_cavity_defaults() -> dict:
         cfref_over_cpl=0.2, cmref_over_cpm=1.0,
         T_hot=1.0, T_cold=0.0, T_init=0.0, T_ref0=0.0, T_solidus=0.299, T_liquidus=0.301,
         L_char=150.0, varpi=2.0 / 3.0,
+        thermal_collision=0, solid_scheme=0, zeta_e=0.0,
     )
 
 
@@ -120,15 +121,17 @@ def serving_arrivals(count: int, rate_per_s: float, seed: int = DEFAULT_SEED,
 
 
 def random_state(nx: int, ny: int, qt: int, seed: int, H_range=(0.0, 1.0), Tm_range=(0.0, 1.0),
-                 rho_amp: float = 0.02, u_amp: float = 0.02, dT_amp: float = 0.01):
+                 rho_amp: float = 0.02, u_amp: float = 0.02, dT_amp: float = 0.01, f_base=None):
     """Random distributions for parity tests: arrays [q][ny][nx] (float64).
 
-    Flow populations are positive values near 1/9 with relative noise; PCM
+    Flow populations are positive values near ``f_base`` (9 values; 1/9 each
+    by default) with relative noise; PCM
     populations are spread so that their sums land anywhere in ``H_range``;
     metal populations so that their sums land in ``Tm_range``; the exchange
     history is uniform noise of size ``dT_amp``."""
     rng = np.random.default_rng(seed)
-    F = (1.0 / 9.0) * (1.0 + rho_amp * rng.uniform(-1, 1, (9, ny, nx)))
+    base = np.full(9, 1.0 / 9.0) if f_base is None else np.asarray(f_base, float).reshape(9)
+    F = base[:, None, None] * (1.0 + rho_amp * rng.uniform(-1, 1, (9, ny, nx)))
     F[1:5] *= 1.0 + u_amp * rng.uniform(-1, 1, (4, ny, nx))
     Ht = rng.uniform(H_range[0], H_range[1], (ny, nx))
     G = np.empty((qt, ny, nx))

@@ -45,6 +45,7 @@ class LbmParams(ctypes.Structure):
         ("T_hot", ctypes.c_double), ("T_cold", ctypes.c_double), ("T_init", ctypes.c_double),
         ("T_ref0", ctypes.c_double), ("T_solidus", ctypes.c_double), ("T_liquidus", ctypes.c_double),
         ("L_char", ctypes.c_double), ("varpi", ctypes.c_double),
+        ("thermal_collision", ctypes.c_int32), ("solid_scheme", ctypes.c_int32), ("zeta_e", ctypes.c_double),
     ]
 
 
@@ -55,6 +56,14 @@ class LbmDerived(ctypes.Structure):
         "H_fs", "H_fl", "l0", "l1", "exchange_rate")] + [
         ("s", ctypes.c_double * 9), ("zeta", ctypes.c_double * 9), ("eta", ctypes.c_double * 9),
         ("H_wall", ctypes.c_double * 4)]
+
+
+class RequestResult(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_int64), ("status", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("steps", ctypes.c_int64), ("nodes", ctypes.c_int64),
+                ("submit_s", ctypes.c_double), ("admit_s", ctypes.c_double), ("finish_s", ctypes.c_double),
+                ("melt_frac", ctypes.c_double), ("nu_hot", ctypes.c_double), ("enthalpy", ctypes.c_double),
+                ("mass", ctypes.c_double)]
 
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
@@ -120,6 +129,22 @@ def lib() -> ctypes.CDLL:
         L.lbm_batch_info.restype = ctypes.c_int
         L.lbm_batch_destroy.argtypes = [vp]
         L.lbm_batch_destroy.restype = ctypes.c_int
+        L.lbm_server_create.argtypes = [i64, i32, i32, i32, i32, i32, i32, vp, ALLOC_FN, FREE_FN, vp,
+                                        ctypes.POINTER(vp)]
+        L.lbm_server_create.restype = ctypes.c_int
+        L.lbm_server_configure.argtypes = [vp, i32, i32]
+        L.lbm_server_configure.restype = ctypes.c_int
+        L.lbm_server_submit.argtypes = [vp, pp, i64, ctypes.POINTER(i64)]
+        L.lbm_server_submit.restype = ctypes.c_int
+        L.lbm_server_tick.argtypes = [vp] + [ctypes.POINTER(i32)] * 3
+        L.lbm_server_tick.restype = ctypes.c_int
+        L.lbm_server_results.argtypes = [vp, ctypes.POINTER(RequestResult), i32, ctypes.POINTER(i32)]
+        L.lbm_server_results.restype = ctypes.c_int
+        L.lbm_server_stats.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(ctypes.c_double),
+                                       ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64), ctypes.POINTER(i64)]
+        L.lbm_server_stats.restype = ctypes.c_int
+        L.lbm_server_destroy.argtypes = [vp]
+        L.lbm_server_destroy.restype = ctypes.c_int
         L.lbm_diag_fields_noalloc.argtypes = [pp, vp, vp, vp, vp, vp, vp, vp]
         L.lbm_diag_fields_noalloc.restype = ctypes.c_int
         _lib = L
@@ -355,7 +380,8 @@ class Solver:
 class Batch:
     """Runs advanced together by one launch per time step (lbm_batch_*)."""
 
-    MAPS = ("one block per tile", "persistent contiguous chunks", "persistent grid stride")
+    MAPS = ("one block per tile", "persistent contiguous chunks", "persistent grid stride",
+            "single-run kernel chains")
 
     def __init__(self, runs, autotune: bool = True, stream=None):
         import torch
@@ -387,6 +413,84 @@ class Batch:
         if self._b:
             lib().lbm_batch_destroy(self._b)
             self._b = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Continuous-batching serving engine (lbm_server_*)."""
+
+    def __init__(self, hbm_budget_bytes: int, max_active: int = 64, batched: bool = True, quantum: int = 256,
+                 precision: int = F16, thermal_q: int = 5, flow: int = 1, stream=None, device=None,
+                 width_cap: int = 128, mapping: int = 3):
+        import torch
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self._alloc = TorchAllocator(self.device)
+        self._s = ctypes.c_void_p()
+        _check(lib().lbm_server_create(int(hbm_budget_bytes), int(max_active), 1 if batched else 0, int(quantum),
+                                       int(precision), int(thermal_q), int(flow),
+                                       ctypes.c_void_p(self.stream.cuda_stream), self._alloc.alloc_cb,
+                                       self._alloc.free_cb, None, ctypes.byref(self._s)), "lbm_server_create")
+        _check(lib().lbm_server_configure(self._s, int(width_cap), int(mapping)), "lbm_server_configure")
+
+    def submit(self, params: dict, nsteps: int) -> int:
+        rid = ctypes.c_int64()
+        _check(lib().lbm_server_submit(self._s, ctypes.byref(to_struct(params)), int(nsteps), ctypes.byref(rid)),
+               "lbm_server_submit")
+        return rid.value
+
+    def tick(self):
+        a, q, d = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        _check(lib().lbm_server_tick(self._s, ctypes.byref(a), ctypes.byref(q), ctypes.byref(d)), "lbm_server_tick")
+        return a.value, q.value, d.value
+
+    def results(self) -> list:
+        buf = (RequestResult * 256)()
+        n = ctypes.c_int32()
+        out = []
+        while True:
+            _check(lib().lbm_server_results(self._s, buf, 256, ctypes.byref(n)), "lbm_server_results")
+            out += [{k: getattr(buf[i], k) for k, _ in RequestResult._fields_ if k != "reserved"}
+                    for i in range(n.value)]
+            if n.value < 256:
+                return out
+
+    def stats(self) -> dict:
+        ns, used, peak = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        busy, el = ctypes.c_double(), ctypes.c_double()
+        _check(lib().lbm_server_stats(self._s, ctypes.byref(ns), ctypes.byref(busy), ctypes.byref(el),
+                                      ctypes.byref(used), ctypes.byref(peak)), "lbm_server_stats")
+        return dict(node_steps=ns.value, busy_s=busy.value, elapsed_s=el.value, used_bytes=used.value,
+                    peak_used_bytes=peak.value)
+
+    def replay(self, trace, time_scale: float = 1.0, idle_sleep: float = 0.001) -> list:
+        """Submits each request of ``trace`` (dicts with arrival_s, params, steps)
+        when its arrival time has passed on the host clock and ticks until all
+        have finished.  Returns the result records."""
+        import time
+        pending = sorted(trace, key=lambda r: r["arrival_s"])
+        t0 = time.perf_counter()
+        i, results = 0, []
+        while len(results) < len(pending):
+            now = (time.perf_counter() - t0) / time_scale
+            while i < len(pending) and pending[i]["arrival_s"] <= now:
+                self.submit(pending[i]["params"], pending[i]["steps"])
+                i += 1
+            active, queued, _ = self.tick()
+            results += self.results()
+            if active == 0 and queued == 0 and i < len(pending):
+                time.sleep(min(idle_sleep, max(0.0, pending[i]["arrival_s"] * time_scale - (time.perf_counter() - t0))))
+        return results
+
+    def close(self):
+        if self._s:
+            lib().lbm_server_destroy(self._s)
+            self._s = ctypes.c_void_p()
 
     def __del__(self):
         try:

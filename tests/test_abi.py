@@ -41,6 +41,10 @@ def test_library_exports_every_declared_entry_point(lbm):
     lambda: inputs.cavity(1024, thermal_q=9),
     lambda: inputs.paper_cavity_defaults(),
     lambda: inputs.batch_draws(count=4)[3],
+    lambda: dict(inputs.cavity(128), thermal_collision=1),
+    lambda: dict(inputs.cavity(128, thermal_q=9), thermal_collision=1),
+    lambda: dict(inputs.cavity(128, thermal_q=9), zeta_e=0.6),
+    lambda: dict(inputs.cavity(128), zeta_e=1.8, solid_scheme=1),
 ])
 def test_parameter_map_matches_oracle(lbm, oracle_mod, make):
     p = make()
@@ -65,6 +69,7 @@ def test_parameter_map_matches_oracle(lbm, oracle_mod, make):
     dict(porosity=0.0), dict(Ste=0.0), dict(k_f=-1.0), dict(T_solidus=0.4, T_liquidus=0.3),
     dict(T_hot=0.0, T_cold=0.0), dict(T_hot=0.0, T_cold=1.0), dict(varpi=1.0), dict(Da=0.0),
     dict(Pr=float("nan")), dict(wall_kind=[0, 0, 2, 1]), dict(nx=65537), dict(nx=40000, ny=40000),
+    dict(thermal_collision=2), dict(solid_scheme=-1), dict(zeta_e=-0.5),
 ])
 def test_malformed_parameters_are_rejected(lbm, change):
     p = inputs.cavity(64)
@@ -80,6 +85,7 @@ def test_malformed_parameters_are_rejected(lbm, change):
     dict(cfref_over_cpl=1.6, thermal_q=5),        # varpi c_f,ref >= c_pl (D2Q5 analogue of Remark I)
     dict(cfref_over_cpl=1.85, thermal_q=9),       # Remark I
     dict(Nu_i=500.0),                             # explicit exchange rate >= 1
+    dict(zeta_e=2.0),                             # an explicit zeta_e outside (0, 2)
 ])
 def test_unstable_parameters_are_rejected(lbm, change):
     p = inputs.cavity(64)

@@ -373,3 +373,87 @@ def test_exchange_source_is_distributed_like_the_equilibrium(oracle_mod, qt):
     h_expect = oracle_mod.h_eq(p, Tm0 + S_m / lc["c_pm"])
     assert np.abs(G1 - g_expect[:, None, None]).max() < 1e-15
     assert np.abs(H1 - h_expect[:, None, None]).max() < 1e-15
+
+
+# ---- comparison variants of Sec. V ------------------------------------------
+
+@pytest.mark.parametrize("qt", [5, 9])
+def test_bgk_thermal_collision_keeps_the_diffusivity(oracle_mod, qt):
+    """Sec. V A's BGK thermal lattices (every rate zeta_alpha, eta_alpha) recover
+    the same diffusivities alpha_ref c_ref (Eq. A19 fixes them through zeta_alpha
+    alone): decay rates converge at second order.  Their error is larger than
+    with the MRT rates of Eq. 53 (1.1e-3 against 2e-4 at N = 64), the reduced
+    numerical diffusion Sec. V A credits to MRT."""
+    errs = []
+    for N in (32, 64):
+        p = inputs.periodic_box(N, 1, flow=0, thermal_q=qt, Nu_i=0.0, T_init=1.0, k_f=0.02,
+                                cfref_over_cpl=0.5, cond_ratio=2.0, L_char=N, thermal_collision=1)
+        lc = oracle_mod.lattice_config(p)
+        assert lc["zeta"][:qt] == [lc["zeta_a"]] * qt and lc["eta"][:qt] == [lc["eta_a"]] * qt
+        o = oracle_mod.Oracle(p)
+        k = 2.0 * math.pi / N
+        T = 1.0 + 0.1 * np.sin(k * np.arange(N))[None, :]
+        F, G, Hm = _equilibrium_state(oracle_mod, p, T, T)
+        o.set_state(F, G, Hm, np.zeros((1, N)))
+        o.run(50)
+        a1 = analytic.mode_amplitude(o.fields()["T_f"][0], k)
+        o.run(400)
+        a2 = analytic.mode_amplitude(o.fields()["T_f"][0], k)
+        errs.append(-math.log(a2 / a1) / 400 / (lc["alpha_fref"] * lc["c_fref"] * k * k) - 1.0)
+    assert abs(errs[1]) < 2e-3 and 3.5 < errs[0] / errs[1] < 4.5
+
+
+@pytest.mark.parametrize("value", [1.8, 1.2, 0.6, 0.1])
+def test_explicit_zeta_e_replaces_eq_53(oracle_mod, value):
+    """Sec. V D sweeps zeta_e over 1.8, 1.2, 0.6, 0.1 instead of 2 - zeta_alpha."""
+    p = inputs.paper_cavity_defaults()
+    p.update(thermal_q=9, zeta_e=value)
+    lc = oracle_mod.lattice_config(p)
+    assert lc["zeta"][1] == lc["zeta"][2] == value
+    p.update(thermal_q=5)
+    assert oracle_mod.lattice_config(p)["zeta"][3] == value
+
+
+def test_bounce_back_conserves_mass_and_stops_solid_nodes(oracle_mod):
+    p = inputs.periodic_box(20, 16, thermal_q=5, Ra=1e7, solid_scheme=1)
+    o = oracle_mod.Oracle(p)
+    F, G, Hm, dT = inputs.random_state(20, 16, 5, seed=21, H_range=(-0.2, 1.6))
+    o.set_state(F, G, Hm, dT)
+    m0 = o.diag()["mass"]
+    o.run(200)
+    f = o.fields()
+    assert abs(o.diag()["mass"] / m0 - 1.0) < 1e-13
+    solid = f["f_l"] <= 0.5
+    assert solid.sum() > 10 and (~solid).sum() > 10
+    assert np.all(f["u_x"][solid] == 0.0) and np.all(f["u_y"][solid] == 0.0)
+
+
+def test_bounce_back_channel_between_solid_layers(oracle_mod):
+    """Sec. V B's bounce-back scheme: a liquid layer between solid columns
+    (f_l = 0; liquid and solid held just above and below an isothermal melting
+    point so the layers stay put) carries the Brinkman profile with the walls
+    half-way between the last liquid and the first solid node."""
+    errs = []
+    for nf, steps in ((16, 4000), (32, 10000)):
+        nx = nf + 4
+        p = inputs.cavity(nx, ny=1, periodic_x=1, periodic_y=1, solid_scheme=1, Nu_i=0.0, k_f=1e-3, Pr=100.0,
+                          Da=0.04, L_char=float(nf), T_solidus=0.3, T_liquidus=0.3, T_init=0.3, T_ref0=0.0,
+                          Ra=393.0, porosity=0.9, F_phi=0.0)
+        lc = oracle_mod.lattice_config(p)
+        o = oracle_mod.Oracle(p)
+        T = np.full((1, nx), 0.3)
+        F, G, Hm = _equilibrium_state(oracle_mod, p, T, T)
+        for x in range(nx):
+            H = lc["T_fs"] - 0.01 if (x < 2 or x >= nx - 2) else lc["T_fl"] + lc["L_a"] + 0.01
+            Tx = oracle_mod.T_of_H(p, H)
+            G[:, 0, x] = oracle_mod.g_eq(p, H, Tx, 0.0, 0.0)
+            Hm[:, 0, x] = oracle_mod.h_eq(p, Tx)
+        o.set_state(F, G, Hm, np.zeros((1, nx)))
+        o.run(steps)
+        f = o.fields()
+        assert f["f_l"][0][:2].max() <= 0.5 and f["f_l"][0][2:-2].min() == 1.0
+        Gv = lc["gbeta"] * (f["T_f"][0, nx // 2] - lc["T0"])
+        ref = analytic.brinkman_channel(np.arange(nx) - 1.5, float(nf), Gv, lc["K"], lc["nu_f"], lc["nu_e"], lc["phi"])
+        u = f["u_y"][0]
+        errs.append(float(np.sqrt(((u[2:-2] - ref[2:-2]) ** 2).sum() / (ref[2:-2] ** 2).sum())))
+    assert errs[0] < 1e-2 and errs[1] < errs[0]
