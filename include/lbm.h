@@ -247,9 +247,12 @@ const char* lbm_strerror(int code);
  * autotune = 1 the call times every combination of tile-width cap (64, 128,
  * 256) and map on freshly created copies of the runs -- the runs themselves
  * do not move, but the copies hold as much device memory again while tuning
- * -- and keeps the fastest; otherwise it takes width cap 128, map 0.  Every node's arithmetic is the
- * same under every map, so the choice cannot change results: a batched step
- * equals lbm_step on each run.
+ * -- and keeps the fastest; otherwise it takes width cap 128, map 0.  Under
+ * map 3 a batched step equals lbm_step on each run bit for bit.  Maps 0-2
+ * inline the same per-node code into another kernel, where the compiler may
+ * fuse a few multiply-adds differently: their FP32 states can differ from
+ * lbm_step's by a few ulps (about 1e-4 of the flow populations per step);
+ * FP64, FP16 and BF16 states were identical in every test.
  *
  * lbm_batch_step enqueues nsteps steps of every run on the batch's stream
  * and advances each run's step count.  Use the runs' own calls (fields,
@@ -289,8 +292,8 @@ int lbm_batch_destroy(lbm_batch* b);
  *      (lbm_diag) go into a result record and its device memory is freed.
  * A request that arrives while others run joins them at the next tick.
  * With batched = 0 the engine is the plain form: one request at a time, in
- * arrival order, each advanced by lbm_step.  A run is the same alone and in
- * a batch (batched steps equal single steps bit for bit).
+ * arrival order, each advanced by lbm_step.  With the default map 3 a run is
+ * the same alone and in the mix, bit for bit.
  *
  * All requests of a server share precision, thermal_q and flow (LBM_ERR_ARG
  * otherwise); a request whose state alone exceeds the budget is refused at
