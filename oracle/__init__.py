@@ -65,6 +65,8 @@ class OrcCfg(ctypes.Structure):
         ("T_fs", ctypes.c_double), ("T_fl", ctypes.c_double), ("varpi", ctypes.c_double),
         ("s", ctypes.c_double * 9), ("zeta", ctypes.c_double * 9), ("eta", ctypes.c_double * 9),
         ("solid_scheme", ctypes.c_int),
+        ("phase_k", ctypes.c_int), ("zeta_role", ctypes.c_int * 9),
+        ("k_l", ctypes.c_double), ("k_s", ctypes.c_double), ("csT2", ctypes.c_double),
     ]
 
 
@@ -103,7 +105,8 @@ def lib():
 
 # ---------------------------------------------------------------------------
 # Parameter map: Eq. 54 with delta_x = delta_t = c = 1, rho_l = 1 and
-# c_pl = c_ps = c_pm = 1 (Sec. IV).  Input keys follow the C ABI's lbm_params.
+# c_pl = c_pm = 1 (Sec. IV); c_ps = c_pl and k_s = k_l unless the Eq. 9
+# variant sets them apart.  Input keys follow the C ABI's lbm_params.
 # ---------------------------------------------------------------------------
 
 def lattice_config(p: dict) -> dict:
@@ -111,9 +114,11 @@ def lattice_config(p: dict) -> dict:
     qt = int(p["thermal_q"])
     L = float(p["L_char"])
     dT = float(p["T_hot"]) - float(p["T_cold"])
-    c_pl = c_ps = c_pm = 1.0
+    c_pl = c_pm = 1.0
+    c_ps = float(p.get("cps_over_cpl", 1.0)) * c_pl       # Eq. 9: solid specific heat
     rho_l = 1.0
-    k_f = float(p["k_f"])
+    k_f = float(p["k_f"])                                # the liquid conductivity k_l of Eq. 9
+    k_s = float(p.get("ks_over_kl", 1.0)) * k_f
     phi = float(p["porosity"])
     alpha_f = k_f / (rho_l * c_pl)                       # alpha_f = k_f/(rho c_p)_f
     nu_f = float(p["Pr"]) * alpha_f                      # Pr = nu_f/alpha_f
@@ -139,15 +144,19 @@ def lattice_config(p: dict) -> dict:
     if float(p.get("zeta_e", 0.0)) > 0.0:                # Sec. V D: an explicit zeta_e
         zeta_e = float(p["zeta_e"])
     s = [1.0, 1.1, 1.1, 1.0, 1.2, 1.0, 1.2, s_v, s_v]    # Eq. 16 with Sec. III C's rates
+    e_role = 0 if float(p.get("zeta_e", 0.0)) > 0.0 else 2   # rate roles for the Eq. 9 variant
     if qt == 9:
         zeta = [1.0, zeta_e, zeta_e, zeta_a, zeta_a, zeta_a, zeta_a, 1.2, 1.2]
         eta = [1.0, 1.1, 1.1, eta_a, eta_a, eta_a, eta_a, 1.2, 1.2]
+        role = [0, e_role, e_role, 1, 1, 1, 1, 0, 0]
     else:
         zeta = [1.0, zeta_a, zeta_a, zeta_e, 1.2] + [0.0] * 4
         eta = [1.0, eta_a, eta_a, 1.1, 1.2] + [0.0] * 4
+        role = [0, 1, 1, e_role, 0] + [0] * 4
     if int(p.get("thermal_collision", 0)) == 1:          # Sec. V A: BGK, one rate per lattice
         zeta = [zeta_a] * qt + [0.0] * (9 - qt)
         eta = [eta_a] * qt + [0.0] * (9 - qt)
+        role = [1] * qt + [0] * (9 - qt)
     F_phi = float(p["F_phi"])
     return dict(
         nx=int(p["nx"]), ny=int(p["ny"]), qt=qt, flow=int(p["flow"]),
@@ -157,6 +166,7 @@ def lattice_config(p: dict) -> dict:
         rho_l=rho_l, rho_m=rho_m, c_pl=c_pl, c_ps=c_ps, c_pm=c_pm, c_fref=c_fref, c_mref=c_mref,
         L_a=L_a, h_v=h_v, T_fs=float(p["T_solidus"]), T_fl=float(p["T_liquidus"]), varpi=varpi,
         s=s, zeta=zeta, eta=eta, solid_scheme=int(p.get("solid_scheme", 0)),
+        phase_k=int(k_s != k_f), zeta_role=role, k_l=k_f, k_s=k_s,
         # informational
         alpha_f=alpha_f, alpha_fref=alpha_fref, alpha_mref=alpha_mref, k_f=k_f, k_m=k_m,
         d_p=d_p, s_v=s_v, zeta_a=zeta_a, zeta_e=zeta_e, eta_a=eta_a, csT2=csT2,
@@ -168,7 +178,7 @@ def make_cfg(lc: dict) -> OrcCfg:
     c = OrcCfg()
     for name, _ in OrcCfg._fields_:
         v = lc[name]
-        if name in ("wall_kind", "wall_T", "s", "zeta", "eta"):
+        if name in ("wall_kind", "wall_T", "s", "zeta", "eta", "zeta_role"):
             arr = getattr(c, name)
             for i, x in enumerate(v):
                 arr[i] = x
@@ -261,7 +271,9 @@ def diagnostics(fields: dict, lc: dict) -> dict:
 
     The paper defines no Nusselt number; the reading used throughout is the
     left-wall heat flux of both phases, second-order one-sided difference,
-    scaled by L/(k_e dT) with k_e = phi k_f + (1 - phi) k_m (Eq. 10)."""
+    scaled by L/(k_e dT) with k_e = phi k_f + (1 - phi) k_m (Eq. 10), k_f the
+    liquid conductivity.  Under the Eq. 9 variant the PCM flux takes the
+    conductivity of each wall node's own liquid fraction."""
     Tf, Tm = fields["T_f"], fields["T_m"]
     phi = lc["phi"]
     k_e = phi * lc["k_f"] + (1.0 - phi) * lc["k_m"]
@@ -269,7 +281,11 @@ def diagnostics(fields: dict, lc: dict) -> dict:
     if Tf.shape[1] >= 3:
         dTf = (3.0 * Tf[:, 0] - 4.0 * Tf[:, 1] + Tf[:, 2]) / 2.0   # -dT/dx at x = 0
         dTm = (3.0 * Tm[:, 0] - 4.0 * Tm[:, 1] + Tm[:, 2]) / 2.0
-        q = phi * lc["k_f"] * dTf + (1.0 - phi) * lc["k_m"] * dTm
+        k_wall = lc["k_f"]
+        if lc["phase_k"]:
+            fl0 = fields["f_l"][:, 0]
+            k_wall = fl0 * lc["k_l"] + (1.0 - fl0) * lc["k_s"]     # Eq. 9
+        q = phi * k_wall * dTf + (1.0 - phi) * lc["k_m"] * dTm
         nu = float(lc["L"] / (k_e * lc["dT"]) * q.mean())
     enthalpy = float(np.sum(phi * lc["rho_l"] * fields["H_f"] + (1.0 - phi) * lc["rho_m"] * lc["c_pm"] * Tm))
     return dict(melt_frac=float(fields["f_l"].mean()), nu_hot=nu, enthalpy=enthalpy,

@@ -38,6 +38,12 @@
  *     treats nodes with f_l <= 0.5 as solid -- their arriving flow populations
  *     are sent back the way they came, f*_i = f+_opp(i), and u = 0 there --
  *     and collides the others with f = f+.
+ *   - Phase-dependent PCM properties (Eq. 9): with phase_k = 1 the PCM
+ *     conductivity is k_f = f_l k_l + (1 - f_l) k_s at the node's current
+ *     liquid fraction, and the PCM rates that depend on it are rebuilt per
+ *     node: zeta_alpha from Eq. A19, zeta_e = 2 - zeta_alpha (Eq. 53); which
+ *     entries of the rate vector are which is set by the caller
+ *     (zeta_role).  The specific heats c_ps, c_pl enter through Eq. 38.
  *
  * Storage: every distribution array is [q][ny][nx] (row-major, x fastest);
  * the stored values are the post-collision populations f*, g*, h* of the
@@ -67,6 +73,10 @@ typedef struct orc_cfg {
     double zeta[9];    /* PCM relaxation diag, Theta (Eq. 31 / App. B) */
     double eta[9];     /* metal relaxation diag, Q (Eq. 42 / App. B) */
     int solid_scheme;  /* 0: volumetric blend (Eq. 20); 1: bounce-back where f_l <= 0.5 (Sec. V B, ref. 62) */
+    int phase_k;       /* 1: PCM conductivity from Eq. 9 at each node, rates rebuilt per node */
+    int zeta_role[9];  /* per PCM rate: 0 the fixed zeta[k], 1 zeta_alpha, 2 zeta_e = 2 - zeta_alpha */
+    double k_l, k_s;   /* liquid and solid PCM conductivities (Eq. 9) */
+    double csT2;       /* c_sT^2 of the thermal lattice (Eq. A19) */
 } orc_cfg;
 
 /* ------------------------------------------------------------------ */
@@ -277,6 +287,22 @@ static void source_dir(const orc_cfg* c, double* s) {
 }
 
 /* Eq. 38 */
+/* PCM relaxation rates at a node of liquid fraction fl.  With phase_k the
+ * conductivity follows Eq. 9, the reference diffusivity alpha_f,ref =
+ * k_f/(rho_l c_f,ref) of Eq. A19 fixes zeta_alpha = 1/(1/2 + alpha_f,ref/c_sT^2),
+ * and zeta_e = 2 - zeta_alpha (Eq. 53) where the caller asks for it. */
+static void pcm_rates(const orc_cfg* c, double fl, double zeta[9]) {
+    for (int k = 0; k < 9; ++k) zeta[k] = c->zeta[k];
+    if (!c->phase_k) return;
+    double kf = fl * c->k_l + (1.0 - fl) * c->k_s;                   /* Eq. 9 */
+    double alpha_ref = kf / (c->rho_l * c->c_fref);                  /* Eq. A19 */
+    double za = 1.0 / (0.5 + alpha_ref / c->csT2);
+    for (int k = 0; k < 9; ++k) {
+        if (c->zeta_role[k] == 1) zeta[k] = za;
+        else if (c->zeta_role[k] == 2) zeta[k] = 2.0 - za;
+    }
+}
+
 static double T_of_H(const orc_cfg* c, double H) {
     double Hfs = c->c_ps * c->T_fs, Hfl = c->c_pl * c->T_fl + c->L_a;
     if (H <= Hfs) return H / c->c_ps;
@@ -470,10 +496,12 @@ static void collide(const orc_cfg* c, const tables* t, const node* n, double dT_
     double Srm_prev = c->h_v * (-dT_prev) / ((1.0 - c->phi) * c->rho_m);
     double S_met = Srm + 0.5 * (Srm - Srm_prev);
 
+    double zeta[9];
+    pcm_rates(c, n->fl, zeta);
     double nv[9], ne[9], ns[9];
     matvec(Q, M, n->g, nv);                                            /* Eq. 32 */
     ng_eq(c, n->H, n->Tf, n->ux, n->uy, ne);
-    for (int k = 0; k < Q; ++k) ns[k] = nv[k] - c->zeta[k] * (nv[k] - ne[k]) + S_pcm * dir[k];
+    for (int k = 0; k < Q; ++k) ns[k] = nv[k] - zeta[k] * (nv[k] - ne[k]) + S_pcm * dir[k];
     matvec(Q, Mi, ns, gs);
 
     matvec(Q, M, n->h, nv);                                            /* Eq. 43 */

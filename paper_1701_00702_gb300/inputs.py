@@ -40,7 +40,7 @@ def paper_cavity_defaults() -> dict:
         cfref_over_cpl=0.2, cmref_over_cpm=1.0,
         T_hot=1.0, T_cold=0.0, T_init=0.0, T_ref0=0.0, T_solidus=0.299, T_liquidus=0.301,
         L_char=150.0, varpi=2.0 / 3.0,
-        thermal_collision=0, solid_scheme=0, zeta_e=0.0,
+        thermal_collision=0, solid_scheme=0, zeta_e=0.0, ks_over_kl=1.0, cps_over_cpl=1.0,
     )
 
 

@@ -23,6 +23,26 @@ def stefan_kappa(St: float) -> float:
     return 0.5 * (lo + hi)
 
 
+def neumann_two_phase(St_l: float, St_s: float, nu: float) -> float:
+    """Root lambda of the two-phase Neumann melting problem: liquid heated at
+    x = 0 (Stefan number St_l = c_l (T_w - T_m)/L), subcooled solid far away
+    (St_s = c_s (T_m - T_i)/L), nu = sqrt(alpha_l/alpha_s); the front is at
+    s = 2 lambda sqrt(alpha_l t).  The interface balance reads
+    lambda sqrt(pi) = St_l exp(-lambda^2)/erf(lambda)
+                      - St_s exp(-nu^2 lambda^2)/(nu erfc(nu lambda))."""
+    def resid(lam):
+        return (St_l * math.exp(-lam * lam) / math.erf(lam)
+                - St_s * math.exp(-nu * nu * lam * lam) / (nu * math.erfc(nu * lam)) - lam * math.sqrt(math.pi))
+    lo, hi = 1e-9, 5.0          # resid(lo) > 0 > resid(hi); resid decreases
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        if resid(mid) > 0.0:
+            lo = mid
+        else:
+            hi = mid
+    return 0.5 * (lo + hi)
+
+
 def brinkman_channel(x, H, G, K, nu_f, nu_e, phi):
     """Steady unidirectional flow between no-slip walls at x = 0 and x = H under a
     uniform body acceleration G, Forchheimer term off:

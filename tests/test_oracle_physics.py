@@ -457,3 +457,100 @@ def test_bounce_back_channel_between_solid_layers(oracle_mod):
         u = f["u_y"][0]
         errs.append(float(np.sqrt(((u[2:-2] - ref[2:-2]) ** 2).sum() / (ref[2:-2] ** 2).sum())))
     assert errs[0] < 1e-2 and errs[1] < errs[0]
+
+
+# ---- phase-dependent PCM properties (Eq. 9) ----------------------------------
+
+@pytest.mark.parametrize("qt", [5, 9])
+@pytest.mark.parametrize("phase", ["solid", "liquid"])
+def test_eq9_conductivity_sets_the_decay_of_each_phase(oracle_mod, qt, phase):
+    """With k_s = k_l/2 and c_ps = 1.5 c_pl, a temperature mode inside one
+    phase decays at k k^2/c_p of that phase (Eq. 28 with Eq. 9): the per-node
+    zeta_alpha of Eq. A19 carries k_s or k_l, and Eq. 38 carries c_ps or c_pl.
+    Second-order convergence, as for the constant-property lattice."""
+    T0 = 0.1 if phase == "solid" else 0.6          # below T_fs = 0.299 or above T_fl = 0.301
+    errs = []
+    for N in (32, 64):
+        p = inputs.periodic_box(N, 1, flow=0, thermal_q=qt, Nu_i=0.0, T_init=T0, k_f=0.02,
+                                cfref_over_cpl=0.5, cond_ratio=2.0, L_char=N, ks_over_kl=0.5, cps_over_cpl=1.5)
+        lc = oracle_mod.lattice_config(p)
+        assert lc["phase_k"] == 1 and lc["c_ps"] == 1.5 and lc["k_s"] == 0.01
+        o = oracle_mod.Oracle(p)
+        k = 2.0 * math.pi / N
+        T = T0 + 0.05 * np.sin(k * np.arange(N))[None, :]
+        F, G, Hm = _equilibrium_state(oracle_mod, p, T, T)
+        o.set_state(F, G, Hm, np.zeros((1, N)))
+        o.run(50)
+        a1 = analytic.mode_amplitude(o.fields()["T_f"][0], k)
+        o.run(400)
+        f = o.fields()
+        assert np.all(f["f_l"] == (0.0 if phase == "solid" else 1.0))
+        a2 = analytic.mode_amplitude(f["T_f"][0], k)
+        kc = (lc["k_s"] / lc["c_ps"]) if phase == "solid" else (lc["k_l"] / lc["c_pl"])
+        errs.append(-math.log(a2 / a1) / 400 / (kc * k * k) - 1.0)
+    assert abs(errs[1]) < 1e-3 and 3.5 < errs[0] / errs[1] < 4.5
+
+
+@pytest.mark.parametrize("qt", [5, 9])
+def test_eq9_two_phase_neumann_front(oracle_mod, qt):
+    """Melting into a subcooled solid with k_s = 2 k_l and c_ps = 1.5 c_pl
+    (H_v = 0, u = 0): the front follows the two-phase Neumann solution
+    s = 2 lambda sqrt(alpha_l t), and both temperature profiles follow
+    their erf / erfc forms."""
+    from scipy.special import erf, erfc
+    nx, n, Ti = 400, 40000, -0.3
+    p = inputs.conduction_1d(nx=nx, ny=1, thermal_q=qt, Nu_i=0.0, cond_ratio=10.0, L_char=100.0,
+                             T_init=Ti, wall_T=[1.0, Ti, 0.0, 0.0], ks_over_kl=2.0, cps_over_cpl=1.5)
+    o = oracle_mod.Oracle(p).run(n)
+    lc = o.lc
+    f = o.fields()
+    a_l = lc["k_l"] / (lc["rho_l"] * lc["c_pl"])
+    a_s = lc["k_s"] / (lc["rho_l"] * lc["c_ps"])
+    nu = math.sqrt(a_l / a_s)
+    lam = analytic.neumann_two_phase(lc["c_pl"] * 1.0 / lc["L_a"], lc["c_ps"] * (0.0 - Ti) / lc["L_a"], nu)
+    lam_one = analytic.stefan_kappa(lc["c_pl"] / lc["L_a"])
+    s_exact = 2.0 * lam * math.sqrt(a_l * n)
+    assert 2.0 * lam_one * math.sqrt(a_l * n) - s_exact > 4.0     # subcooling slows the front visibly
+    s_lb = f["f_l"][0].sum() - 0.5
+    assert abs(s_lb - s_exact) < 1.0
+    x = np.arange(nx, dtype=float)
+    liquid = x < s_exact - 2.0
+    solid = x > s_exact + 2.0
+    T_l = 1.0 - erf(x / (2.0 * math.sqrt(a_l * n))) / math.erf(lam)
+    T_s = Ti + (0.0 - Ti) * erfc(x / (2.0 * math.sqrt(a_s * n))) / math.erfc(nu * lam)
+    assert np.abs(f["T_f"][0][liquid] - T_l[liquid]).max() < 1e-2
+    assert np.abs(f["T_f"][0][solid] - T_s[solid]).max() < 1e-2
+
+
+def test_eq9_variant_conserves_mass_and_enthalpy(oracle_mod):
+    p = inputs.periodic_box(24, 20, thermal_q=5, Ra=1e7, ks_over_kl=0.4, cps_over_cpl=1.3)
+    o = oracle_mod.Oracle(p)
+    F, G, Hm, dT = inputs.random_state(24, 20, 5, seed=13, H_range=(0.0, 1.6), Tm_range=(0.0, 1.0))
+    o.set_state(F, G, Hm, dT)
+    d0 = o.diag()
+    o.run(300)
+    d1 = o.diag()
+    assert abs(d1["mass"] / d0["mass"] - 1.0) < 1e-12
+    assert abs(d1["enthalpy"] / d0["enthalpy"] - 1.0) < 1e-12
+
+
+def test_eq9_two_step_hand_calculation_d2q5(oracle_mod):
+    """The two-step hand calculation above with k_s = 3 k_l: node x=1 collides
+    at f_l = a/L_a (isothermal mushy zone), so by Eq. 9 its conductivity is
+    k = f_l k_l + (1 - f_l) k_s, by Eq. A19 zeta_a' = 1/(1/2 + k/(c_fref c_sT^2))
+    and by Eq. 53 zeta_e' = 2 - zeta_a'.  The g_1 it sends to x=2 is
+    a(4 - zeta_e' - z_eps - 2 zeta_a')/4 = a(2 - zeta_a' - z_eps)/4."""
+    p = inputs.conduction_1d(nx=12, ny=1, thermal_q=5, Nu_i=0.0, ks_over_kl=3.0)
+    o = oracle_mod.Oracle(p)
+    lc = o.lc
+    a = lc["varpi"] * lc["c_fref"] * 1.0 / 4.0
+    o.run(1)
+    assert abs(o.fields()["H_f"][0][1] - a) < 1e-15
+    o.run(1)
+    fl1 = a / lc["L_a"]
+    k = fl1 * lc["k_l"] + (1.0 - fl1) * lc["k_s"]
+    za = 1.0 / (0.5 + k / (lc["rho_l"] * lc["c_fref"] * lc["csT2"]))
+    ze = 2.0 - za
+    expect = a * (4.0 - ze - lc["zeta"][4] - 2.0 * za) / 4.0
+    assert abs(o.fields()["H_f"][0][2] - expect) < 1e-15
+    assert abs(za - lc["zeta_a"]) > 0.1                  # the node's rate is not the liquid one
