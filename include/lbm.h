@@ -122,6 +122,13 @@ typedef struct lbm_params {
     int32_t thermal_collision; /* 0: MRT (Sec. III B); 1: BGK, every thermal rate = ζ_α (η_α) (Sec. V A) */
     int32_t solid_scheme;      /* 0: volumetric blend (Eq. 20); 1: bounce-back where f_l <= 0.5, no blend (Sec. V B) */
     double  zeta_e;            /* 0: ζ_e = 2 - ζ_α (Eq. 53); > 0: this ζ_e (and ζ_ε for D2Q9) instead (Sec. V D) */
+    /* Phase-dependent PCM properties (Eq. 9): k_f = f_l k_l + (1 - f_l) k_s with
+     * k_l = k_f above, and c_ps in Eq. 38.  With ks_over_kl != 1 every node
+     * takes its own ζ_α (Eq. A19 at its liquid fraction) and ζ_e = 2 - ζ_α
+     * (Eq. 53, unless zeta_e is given).  1 and 1 give the constant-property
+     * method of Sec. IV. */
+    double  ks_over_kl;        /* k_s / k_l, > 0 */
+    double  cps_over_cpl;      /* c_ps / c_pl, > 0 */
 } lbm_params;
 
 /* Lattice-unit constants derived from lbm_params (output of lbm_derive). */
@@ -135,6 +142,8 @@ typedef struct lbm_derived {
     double zeta[9];            /* PCM rates Θ (first thermal_q entries) */
     double eta[9];             /* metal rates Q (first thermal_q entries) */
     double H_wall[4];          /* enthalpy of each Dirichlet wall, inverse of Eq. 38 */
+    double k_s, c_ps;          /* solid PCM conductivity and specific heat (Eq. 9) */
+    double zeta_a_solid;       /* ζ_α of a fully solid node (Eq. A19 with k_s); = zeta_a of liquid when k_s = k_l */
 } lbm_derived;
 
 typedef struct lbm_handle lbm_handle;
@@ -250,9 +259,10 @@ const char* lbm_strerror(int code);
  * -- and keeps the fastest; otherwise it takes width cap 128, map 0.  Under
  * map 3 a batched step equals lbm_step on each run bit for bit.  Maps 0-2
  * inline the same per-node code into another kernel, where the compiler may
- * fuse a few multiply-adds differently: their FP32 states can differ from
- * lbm_step's by a few ulps (about 1e-4 of the flow populations per step);
- * FP64, FP16 and BF16 states were identical in every test.
+ * fuse a few multiply-adds differently: their states can differ from
+ * lbm_step's by a few roundings of the arithmetic (FP32: 1-3 ulps in about
+ * 1e-4 of the flow populations per step), which a 16-bit store sometimes
+ * carries into the last stored bit.
  *
  * lbm_batch_step enqueues nsteps steps of every run on the batch's stream
  * and advances each run's step count.  Use the runs' own calls (fields,

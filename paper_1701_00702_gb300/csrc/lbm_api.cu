@@ -21,7 +21,7 @@ bool finite(double v) { return std::isfinite(v); }
 
 // Inverse of Eq. 38: T <= T_fs is solid, T >= T_fl (above T_fs) liquid, else mushy.
 double enthalpy_of_T(const lbm_params& p, double L_a, double T) {
-    const double c_ps = 1.0, c_pl = 1.0;
+    const double c_ps = p.cps_over_cpl, c_pl = 1.0;
     const double Hfs = c_ps * p.T_solidus, Hfl = c_pl * p.T_liquidus + L_a;
     if (T <= p.T_solidus) return c_ps * T;
     if (T >= p.T_liquidus) return Hfl + c_pl * (T - p.T_liquidus);
@@ -46,13 +46,14 @@ int derive_impl(const lbm_params* pp, lbm_derived* out) {
     }
     const double vals[] = {p.porosity, p.Ste, p.cond_ratio, p.Nu_i, p.sigma_hat, p.dp_over_L, p.k_f,
                            p.cfref_over_cpl, p.cmref_over_cpm, p.T_hot, p.T_cold, p.T_init, p.T_ref0,
-                           p.T_solidus, p.T_liquidus, p.L_char};
+                           p.T_solidus, p.T_liquidus, p.L_char, p.ks_over_kl, p.cps_over_cpl};
     for (double v : vals)
         if (!finite(v)) return LBM_ERR_ARG;
     if (!(p.porosity > 0.0 && p.porosity < 1.0)) return LBM_ERR_ARG;
     if (!(p.Ste > 0.0) || !(p.k_f > 0.0) || !(p.L_char > 0.0) || !(p.dp_over_L > 0.0)) return LBM_ERR_ARG;
     if (!(p.cfref_over_cpl > 0.0) || !(p.cmref_over_cpm > 0.0) || !(p.sigma_hat > 0.0)) return LBM_ERR_ARG;
     if (!(p.cond_ratio > 0.0) || !(p.Nu_i >= 0.0)) return LBM_ERR_ARG;
+    if (!(p.ks_over_kl > 0.0) || !(p.cps_over_cpl > 0.0)) return LBM_ERR_ARG;
     if (!(p.T_liquidus >= p.T_solidus) || p.T_hot == p.T_cold) return LBM_ERR_ARG;
     if (p.thermal_q == 5 && !(p.varpi > 0.0 && p.varpi < 1.0)) return LBM_ERR_ARG;
     if ((p.thermal_collision != 0 && p.thermal_collision != 1) || (p.solid_scheme != 0 && p.solid_scheme != 1))
@@ -65,7 +66,8 @@ int derive_impl(const lbm_params* pp, lbm_derived* out) {
         if (!(p.Pr > 0.0) || !(p.Da > 0.0) || !(p.J > 0.0) || !(p.F_phi >= 0.0) || !(p.Ra >= 0.0)) return LBM_ERR_ARG;
     }
 
-    // Eq. 54 with delta_x = delta_t = c = 1, rho_l = 1, c_pl = c_ps = c_pm = 1.
+    // Eq. 54 with delta_x = delta_t = c = 1, rho_l = 1, c_pl = c_pm = 1; c_ps and
+    // k_s from the Eq. 9 ratios (1 and 1 in Sec. IV).
     lbm_derived d;
     std::memset(&d, 0, sizeof d);
     const double rho_l = 1.0, c_pl = 1.0, c_pm = 1.0;
@@ -87,12 +89,16 @@ int derive_impl(const lbm_params* pp, lbm_derived* out) {
     d.alpha_mref = d.k_m / (d.rho_m * d.c_mref);
     const double cs2 = 1.0 / 3.0;
     d.csT2 = p.thermal_q == 9 ? cs2 : 0.5 * p.varpi;
-    d.H_fs = 1.0 * p.T_solidus;
+    d.c_ps = p.cps_over_cpl * c_pl;
+    d.k_s = p.ks_over_kl * p.k_f;
+    d.H_fs = d.c_ps * p.T_solidus;
     d.H_fl = c_pl * p.T_liquidus + d.L_a;
     d.exchange_rate = d.h_v * (1.0 / (phi * rho_l) + 1.0 / ((1.0 - phi) * d.rho_m));
 
     const double s_v = p.flow ? 1.0 / (0.5 + d.nu_e / cs2) : 1.0;
     const double za = 1.0 / (0.5 + d.alpha_fref / d.csT2);
+    const double za_s = 1.0 / (0.5 + d.k_s / (rho_l * d.c_fref) / d.csT2);   // Eq. A19 with k_s
+    d.zeta_a_solid = za_s;
     const double ea = 1.0 / (0.5 + d.alpha_mref / d.csT2);
     const double ze = p.zeta_e > 0.0 ? p.zeta_e : 2.0 - za;   // Eq. 53, or Sec. V D's explicit value
     const double s9[9] = {1.0, 1.1, 1.1, 1.0, 1.2, 1.0, 1.2, s_v, s_v};
@@ -123,8 +129,9 @@ int derive_impl(const lbm_params* pp, lbm_derived* out) {
     auto in02 = [](double r) { return r > 0.0 && r < 2.0; };
     if (p.flow && (!in02(s_v) || !(d.l0 > 0.0))) return LBM_ERR_STABILITY;
     if (!in02(za) || !in02(ea) || !in02(ze)) return LBM_ERR_STABILITY;
+    if (!in02(za_s) || !(p.zeta_e > 0.0 || in02(2.0 - za_s))) return LBM_ERR_STABILITY;
     const double cap = p.thermal_q == 9 ? 9.0 / 5.0 : 1.0 / p.varpi;   // Remark I (and its D2Q5 analogue)
-    if (!(d.c_fref < cap * c_pl) || !(d.c_mref < cap * c_pm)) return LBM_ERR_STABILITY;
+    if (!(d.c_fref < cap * std::min(c_pl, d.c_ps)) || !(d.c_mref < cap * c_pm)) return LBM_ERR_STABILITY;
     if (!(d.exchange_rate < 1.0)) return LBM_ERR_STABILITY;
     if (out) *out = d;
     return LBM_OK;
@@ -253,7 +260,7 @@ lbmk::StepParams<R> make_params(const lbm_handle* h, int from) {
         const double g0fs = d.H_fs - om * d.c_fref * p.T_solidus, g0fl = d.H_fl - om * d.c_fref * p.T_liquidus;
         P.g0_fs = (R)g0fs;
         P.g0_fl = (R)g0fl;
-        P.tg_solid = (R)(1.0 / (1.0 - om * d.c_fref));
+        P.tg_solid = (R)(1.0 / (d.c_ps - om * d.c_fref));
         P.tg_liquid = (R)(1.0 / (1.0 - om * d.c_fref));
         P.tg_mushy = (R)((p.T_liquidus - p.T_solidus) / (g0fl - g0fs));
         P.kappa_m = (R)(d.c_mref / (1.0 - om * d.c_mref));
@@ -281,7 +288,7 @@ lbmk::StepParams<R> make_params(const lbm_handle* h, int from) {
     P.mush_slope = (R)((p.T_liquidus - p.T_solidus) / (d.H_fl - d.H_fs));
     P.T_fs = (R)p.T_solidus;
     P.T_fl = (R)p.T_liquidus;
-    P.inv_c_ps = (R)1.0;
+    P.inv_c_ps = (R)(1.0 / d.c_ps);
     P.inv_c_pl = (R)1.0;
     P.c_pl = (R)1.0;
     P.c_fref = (R)d.c_fref;
@@ -290,6 +297,25 @@ lbmk::StepParams<R> make_params(const lbm_handle* h, int from) {
     P.inv_c_pm = (R)1.0;
     P.varpi = (R)p.varpi;
     P.a_f = (R)(d.h_v / (phi * 1.0));
+    // Eq. 9 variant: per-node zeta_alpha = 1/(1/2 + k_f(f_l)/(rho_l c_fref c_sT^2)) (Eq. A19);
+    // rate k of the PCM lattice is zr_a[k] + zr_b[k] zeta_alpha (fixed, zeta_alpha, or 2 - zeta_alpha)
+    P.phase_k = d.k_s != p.k_f ? 1 : 0;
+    P.kl_c = (R)(p.k_f / (d.c_fref * d.csT2));
+    P.ks_c = (R)(d.k_s / (d.c_fref * d.csT2));
+    {
+        const int Q = p.thermal_q, e_role = p.zeta_e > 0.0 ? 0 : 2;
+        int role[9] = {0, 1, 1, e_role, 0, 0, 0, 0, 0};
+        if (Q == 9) {
+            const int r9[9] = {0, e_role, e_role, 1, 1, 1, 1, 0, 0};
+            std::memcpy(role, r9, sizeof r9);
+        }
+        if (p.thermal_collision == 1)
+            for (int k = 0; k < Q; ++k) role[k] = 1;
+        for (int k = 0; k < 9; ++k) {
+            P.zr_a[k] = role[k] == 0 ? (R)d.zeta[k] : (role[k] == 1 ? (R)0.0 : (R)2.0);
+            P.zr_b[k] = role[k] == 0 ? (R)0.0 : (role[k] == 1 ? (R)1.0 : (R)-1.0);
+        }
+    }
     P.a_m = (R)(d.h_v / ((1.0 - phi) * d.rho_m));
     return P;
 }
@@ -425,6 +451,8 @@ void lbm_params_default(lbm_params* p) {
     p->T_liquidus = 0.301;
     p->L_char = 150.0;
     p->varpi = 2.0 / 3.0;
+    p->ks_over_kl = 1.0;
+    p->cps_over_cpl = 1.0;
 }
 
 int lbm_derive(const lbm_params* p, lbm_derived* d) { return derive_impl(p, d); }
@@ -569,6 +597,7 @@ int lbm_diag(lbm_handle* h, double* melt_frac, double* nu_hot, double* enthalpy,
     C.rho_m = h->d.rho_m;
     C.c_pm = 1.0;
     C.k_f = p.k_f;
+    C.k_s = h->d.k_s;
     C.k_m = h->d.k_m;
     C.left_wall = (!p.periodic_x && p.nx >= 3) ? 1 : 0;
     cudaError_t e;

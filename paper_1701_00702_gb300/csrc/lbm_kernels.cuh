@@ -115,6 +115,10 @@ struct StepParams {
     R c_pl, c_fref, c_mref, c_pm, inv_c_pm, varpi;
     R zeta[9], eta[9];
     R a_f, a_m;          // h_v/(phi rho_l), h_v/((1 - phi) rho_m)
+    // Eq. 9 variant: PCM rates from the node's liquid fraction
+    int phase_k;         // 1: k_s != k_l, rates per node
+    R kl_c, ks_c;        // k_l, k_s over (rho_l c_fref c_sT^2)
+    R zr_a[9], zr_b[9];  // PCM rate k = zr_a[k] + zr_b[k] zeta_alpha
 };
 
 enum : unsigned int { STATUS_UNSTABLE = 1u };
@@ -625,8 +629,15 @@ __device__ __forceinline__ void step_node(const StepParams<typename ModeTraits<M
     {
         R ne[QT];
         neq_pcm<R, QT>(P, n.H, n.Tf, n.ux, n.uy, ne);
+        if (P.phase_k) {
+            // Eq. 9 at the node's liquid fraction -> zeta_alpha (Eq. A19) -> zeta_e (Eq. 53)
+            const R za = fast_rcp(R(0.5) + P.ks_c + n.fl * (P.kl_c - P.ks_c));
 #pragma unroll
-        for (int k = 1; k < QT; ++k) n.ng[k] -= P.zeta[k] * (n.ng[k] - ne[k]);
+            for (int k = 1; k < QT; ++k) n.ng[k] -= (P.zr_a[k] + P.zr_b[k] * za) * (n.ng[k] - ne[k]);
+        } else {
+#pragma unroll
+            for (int k = 1; k < QT; ++k) n.ng[k] -= P.zeta[k] * (n.ng[k] - ne[k]);
+        }
         if constexpr (QT == 9) {
             n.ng[1] -= R(2) * S_pcm; n.ng[2] += S_pcm;
         } else {
@@ -745,7 +756,7 @@ __global__ void __launch_bounds__(256) fields_kernel(const __grid_constant__ Ste
 // Diagnostics: per-block FP64 partial sums of f_l, enthalpy, mass and the
 // left-wall heat flux, written to scratch[block][4] in a fixed order.
 struct DiagConst {
-    double phi, rho_l, rho_m, c_pm, k_f, k_m;
+    double phi, rho_l, rho_m, c_pm, k_f, k_s, k_m;   // k_f: liquid PCM conductivity, k_s: solid (Eq. 9)
     int left_wall;  // 1 when x = 0 is a wall (Nusselt number defined)
 };
 
@@ -771,7 +782,9 @@ __global__ void __launch_bounds__(256) diag_partial(const __grid_constant__ Step
             node_state<M, QT, FLOW>(P, 2, y, n2, w2);
             const double gf = 0.5 * (3.0 * (double)n.Tf - 4.0 * (double)n1.Tf + (double)n2.Tf);
             const double gm = 0.5 * (3.0 * (double)n.Tm - 4.0 * (double)n1.Tm + (double)n2.Tm);
-            v[3] = C.phi * C.k_f * gf + (1.0 - C.phi) * C.k_m * gm;
+            // PCM conductivity of the wall node's own liquid fraction (Eq. 9)
+            const double kw = C.k_s == C.k_f ? C.k_f : (double)n.fl * C.k_f + (1.0 - (double)n.fl) * C.k_s;
+            v[3] = C.phi * kw * gf + (1.0 - C.phi) * C.k_m * gm;
         }
     }
     __shared__ double red[4][32];

@@ -25,7 +25,7 @@ constexpr int kMaxDevices = 64;
 static __device__ __align__(256) double g_partials[kMaxBlocks * 4];
 
 struct Consts {
-    double phi, rho_l, rho_m, c_pm, k_f, k_m;
+    double phi, rho_l, rho_m, c_pm, k_f, k_s, k_m;   // k_f liquid, k_s solid PCM conductivity (Eq. 9)
     double nu_scale;   // L / (k_e dT) / ny, or NaN when x = 0 is not a wall
     int nx, ny, left_wall;
 };
@@ -47,7 +47,8 @@ __global__ void __launch_bounds__(kThreads) partial_sums(const R* __restrict__ T
         if (C.left_wall && k % C.nx == 0) {
             const double gf = 0.5 * (3.0 * (double)Tf[k] - 4.0 * (double)Tf[k + 1] + (double)Tf[k + 2]);
             const double gm = 0.5 * (3.0 * (double)Ts[k] - 4.0 * (double)Ts[k + 1] + (double)Ts[k + 2]);
-            v[3] += C.phi * C.k_f * gf + (1.0 - C.phi) * C.k_m * gm;
+            const double kw = C.k_s == C.k_f ? C.k_f : (double)fl[k] * C.k_f + (1.0 - (double)fl[k]) * C.k_s;
+            v[3] += C.phi * kw * gf + (1.0 - C.phi) * C.k_m * gm;
         }
     }
     __shared__ double red[4][kThreads / 32];
@@ -130,6 +131,7 @@ extern "C" int lbm_diag_fields_noalloc(const lbm_params* p, const void* T_f, con
     C.rho_m = d.rho_m;
     C.c_pm = 1.0;
     C.k_f = p->k_f;
+    C.k_s = d.k_s;
     C.k_m = d.k_m;
     C.nx = p->nx;
     C.ny = p->ny;

@@ -46,6 +46,7 @@ class LbmParams(ctypes.Structure):
         ("T_ref0", ctypes.c_double), ("T_solidus", ctypes.c_double), ("T_liquidus", ctypes.c_double),
         ("L_char", ctypes.c_double), ("varpi", ctypes.c_double),
         ("thermal_collision", ctypes.c_int32), ("solid_scheme", ctypes.c_int32), ("zeta_e", ctypes.c_double),
+        ("ks_over_kl", ctypes.c_double), ("cps_over_cpl", ctypes.c_double),
     ]
 
 
@@ -55,7 +56,8 @@ class LbmDerived(ctypes.Structure):
         "alpha_f", "alpha_fref", "alpha_mref", "c_fref", "c_mref", "csT2",
         "H_fs", "H_fl", "l0", "l1", "exchange_rate")] + [
         ("s", ctypes.c_double * 9), ("zeta", ctypes.c_double * 9), ("eta", ctypes.c_double * 9),
-        ("H_wall", ctypes.c_double * 4)]
+        ("H_wall", ctypes.c_double * 4), ("k_s", ctypes.c_double), ("c_ps", ctypes.c_double),
+        ("zeta_a_solid", ctypes.c_double)]
 
 
 class RequestResult(ctypes.Structure):

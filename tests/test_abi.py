@@ -45,6 +45,9 @@ def test_library_exports_every_declared_entry_point(lbm):
     lambda: dict(inputs.cavity(128, thermal_q=9), thermal_collision=1),
     lambda: dict(inputs.cavity(128, thermal_q=9), zeta_e=0.6),
     lambda: dict(inputs.cavity(128), zeta_e=1.8, solid_scheme=1),
+    lambda: dict(inputs.cavity(128), ks_over_kl=0.5, cps_over_cpl=1.4, wall_T=[1.0, 0.1, 0.0, 0.0]),
+    lambda: inputs.conduction_1d(thermal_q=9, ks_over_kl=2.0, cps_over_cpl=1.5, T_init=-0.3,
+                                 wall_T=[1.0, -0.3, 0.0, 0.0]),
 ])
 def test_parameter_map_matches_oracle(lbm, oracle_mod, make):
     p = make()
@@ -62,6 +65,10 @@ def test_parameter_map_matches_oracle(lbm, oracle_mod, make):
         assert d["s"] == pytest.approx(lc["s"], rel=1e-15)
     for side in range(4):
         assert d["H_wall"][side] == pytest.approx(oracle_mod.H_of_T(p, p["wall_T"][side]), rel=1e-15, abs=1e-15)
+    assert math.isclose(d["k_s"], lc["k_s"], rel_tol=1e-15) and math.isclose(d["c_ps"], lc["c_ps"], rel_tol=1e-15)
+    assert math.isclose(d["H_fs"], lc["c_ps"] * lc["T_fs"], rel_tol=1e-15, abs_tol=1e-300)
+    za_s = 1.0 / (0.5 + lc["k_s"] / (lc["rho_l"] * lc["c_fref"]) / lc["csT2"])      # Eq. A19 with k_s
+    assert math.isclose(d["zeta_a_solid"], za_s, rel_tol=1e-15)
 
 
 @pytest.mark.parametrize("change", [
@@ -69,7 +76,8 @@ def test_parameter_map_matches_oracle(lbm, oracle_mod, make):
     dict(porosity=0.0), dict(Ste=0.0), dict(k_f=-1.0), dict(T_solidus=0.4, T_liquidus=0.3),
     dict(T_hot=0.0, T_cold=0.0), dict(T_hot=0.0, T_cold=1.0), dict(varpi=1.0), dict(Da=0.0),
     dict(Pr=float("nan")), dict(wall_kind=[0, 0, 2, 1]), dict(nx=65537), dict(nx=40000, ny=40000),
-    dict(thermal_collision=2), dict(solid_scheme=-1), dict(zeta_e=-0.5),
+    dict(thermal_collision=2), dict(solid_scheme=-1), dict(zeta_e=-0.5), dict(ks_over_kl=0.0),
+    dict(cps_over_cpl=-1.0), dict(ks_over_kl=float("inf")),
 ])
 def test_malformed_parameters_are_rejected(lbm, change):
     p = inputs.cavity(64)

@@ -296,7 +296,10 @@ def test_lbm_create_with_cuda_allocator(lbm):
 
 
 VARIANTS = {"bgk": dict(thermal_collision=1), "bounce_back": dict(solid_scheme=1), "zeta_e": dict(zeta_e=0.6),
-            "bounce_back_bgk": dict(solid_scheme=1, thermal_collision=1)}
+            "bounce_back_bgk": dict(solid_scheme=1, thermal_collision=1),
+            "eq9": dict(ks_over_kl=0.5, cps_over_cpl=1.4),
+            "eq9_bgk": dict(ks_over_kl=2.0, cps_over_cpl=0.8, thermal_collision=1),
+            "eq9_zeta_e": dict(ks_over_kl=0.5, zeta_e=0.6)}
 
 
 @pytest.mark.parametrize("variant", sorted(VARIANTS))
@@ -304,7 +307,8 @@ VARIANTS = {"bgk": dict(thermal_collision=1), "bounce_back": dict(solid_scheme=1
 @pytest.mark.parametrize("qt", [5, 9])
 def test_paper_variants_from_random_state(lbm, oracle_mod, variant, prec, qt):
     """The comparison variants of Sec. V (BGK thermal collision, bounce-back
-    solid, explicit zeta_e) against the oracle, walled and periodic sides.
+    solid, explicit zeta_e) and the phase-dependent PCM properties of Eq. 9
+    against the oracle, walled and periodic sides.
     Flow populations start near the rest equilibrium: without the blend the
     bounce-back scheme does not damp a state as far from equilibrium as
     f_i = 1/9 (the oracle and the kernel both reach |u| > 0.3 from it)."""
@@ -323,3 +327,25 @@ def test_paper_variants_from_random_state(lbm, oracle_mod, variant, prec, qt):
             scale = max(np.abs(fo[key]).max(), 1e-3)
             assert np.abs(fs[name].astype(np.float64) - fo[key]).max() / scale < (1e-12 if prec == 0 else 5e-6)
         s.close()
+
+
+@pytest.mark.parametrize("prec,tol", [(0, 1e-10), (1, 1e-5)])
+@pytest.mark.parametrize("qt", [5, 9])
+def test_eq9_two_phase_melting_matches_oracle(lbm, oracle_mod, prec, tol, qt):
+    """Melting into a subcooled solid with k_s = 2 k_l and c_ps = 1.5 c_pl
+    (Eq. 9), exchange on: 6000 steps of the 200 x 4 conduction set-up."""
+    p = inputs.conduction_1d(precision=prec, thermal_q=qt, T_init=-0.3, wall_T=[1.0, -0.3, 0.0, 0.0],
+                             ks_over_kl=2.0, cps_over_cpl=1.5)
+    s = lbm.Solver(p)
+    o = oracle_mod.Oracle(p)
+    s.step(6000)
+    o.run(6000)
+    fs, fo = s.fields(device=False), o.fields()
+    for name in ("T_f", "T_s", "f_l"):
+        key = "T_m" if name == "T_s" else name
+        assert rel_l2(fs[name], fo[key]) < tol, name
+    ds, do = s.diag(), o.diag()
+    for k in ("melt_frac", "nu_hot", "enthalpy"):
+        assert abs(ds[k] / do[k] - 1.0) < (1e-10 if prec == 0 else 1e-5), k
+    assert 0.05 < do["melt_frac"] < 0.5
+    s.close()
