@@ -302,6 +302,11 @@ def bench_batched(args, lbm, inputs, torch, stream, steps_per_solve: int = 10_00
         b = lbm.Batch(runs, autotune=True, stream=stream)
         ms = timed(lambda: b.step(chunk))
         info = b.info()
+        if info["mapping"] == "single-run kernel chains":
+            shapes = {}
+            for bx, by in b.blocks():
+                shapes[f"{bx}x{by}"] = shapes.get(f"{bx}x{by}", 0) + 1
+            info["block_shapes"] = shapes
         ok = all(r.status() == 0 for r in runs)
         b.close()
         for r in runs:

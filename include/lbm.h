@@ -252,11 +252,15 @@ const char* lbm_strerror(int code);
  * per tile, 1 persistent blocks over contiguous chunks of the list, 2
  * persistent blocks striding over the list.  Map 3 launches lbm_step's own
  * kernel once per run and step, each run a chain of kernel nodes in one
- * graph and the chains independent, so small runs overlap large ones.  With
- * autotune = 1 the call times every combination of tile-width cap (64, 128,
- * 256) and map on freshly created copies of the runs -- the runs themselves
- * do not move, but the copies hold as much device memory again while tuning
- * -- and keeps the fastest; otherwise it takes width cap 128, map 0.  Under
+ * graph and the chains independent, so small runs overlap large ones; each
+ * run's kernel takes a block shape of 128 x 2, 64 x 4, 32 x 8 or 256 x 1
+ * threads.  With autotune = 1 the call times, on freshly created copies of
+ * the runs (the runs themselves do not move, but the copies hold as much
+ * device memory again while tuning), map 3 with the block shape chosen per
+ * size class (grid width <= 64, <= 128, <= 256, wider; one class at a time,
+ * keeping the fastest shape) and every combination of tile-width cap (64,
+ * 128, 256) and map 0-2, and keeps the fastest; otherwise it takes width cap
+ * 128, map 0, every block 128 x 2.  Under
  * map 3 a batched step equals lbm_step on each run bit for bit.  Maps 0-2
  * inline the same per-node code into another kernel, where the compiler may
  * fuse a few multiply-adds differently: their states can differ from
@@ -283,6 +287,11 @@ int lbm_batch_step(lbm_batch* b, int64_t nsteps);
 int lbm_batch_configure(lbm_batch* b, int32_t width_cap, int32_t mapping);
 int lbm_batch_info(const lbm_batch* b, int32_t* n_tiles, int32_t* width_cap, int32_t* mapping, int32_t* grid,
                    double* tuned_us_per_step);
+/* Block shape of run `run` under map 3: one of 128 x 2, 64 x 4, 32 x 8,
+ * 256 x 1 (LBM_ERR_ARG otherwise).  The shape changes no result.  set
+ * synchronises the batch's stream. */
+int lbm_batch_set_block(lbm_batch* b, int32_t run, int32_t block_x, int32_t block_y);
+int lbm_batch_get_block(const lbm_batch* b, int32_t run, int32_t* block_x, int32_t* block_y);
 int lbm_batch_destroy(lbm_batch* b);
 
 /*

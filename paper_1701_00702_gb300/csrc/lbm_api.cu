@@ -216,6 +216,9 @@ void dev_free(lbm_handle* h, void* p) {
     else cudaFreeAsync(p, h->stream);
 }
 
+// 1 when the run takes the Eq. 9 per-node PCM rates (k_s != k_l).
+int phase_k_of(const lbm_handle* h) { return h->d.k_s != h->p.k_f ? 1 : 0; }
+
 template <typename R>
 lbmk::StepParams<R> make_params(const lbm_handle* h, int from) {
     const lbm_params& p = h->p;
@@ -299,7 +302,7 @@ lbmk::StepParams<R> make_params(const lbm_handle* h, int from) {
     P.a_f = (R)(d.h_v / (phi * 1.0));
     // Eq. 9 variant: per-node zeta_alpha = 1/(1/2 + k_f(f_l)/(rho_l c_fref c_sT^2)) (Eq. A19);
     // rate k of the PCM lattice is zr_a[k] + zr_b[k] zeta_alpha (fixed, zeta_alpha, or 2 - zeta_alpha)
-    P.phase_k = d.k_s != p.k_f ? 1 : 0;
+    P.phase_k = phase_k_of(h);
     P.kl_c = (R)(p.k_f / (d.c_fref * d.csT2));
     P.ks_c = (R)(d.k_s / (d.c_fref * d.csT2));
     {
@@ -850,6 +853,7 @@ struct lbm_batch {
     size_t params_stride = 0;     // bytes of one StepParams
     void* params = nullptr;
     std::vector<int> flip;        // run's current copy relative to the batch parity at creation
+    std::vector<int> shape;       // map 3: block shape of each run (index into kShapes)
     lbmk::Tile* tiles = nullptr;
     size_t tile_capacity = 0;     // tiles that fit in the allocation
     int ntiles = 0, width_cap = 128, chunk = 1, grid = 0, parity = 0, mapping = 0;
@@ -858,6 +862,17 @@ struct lbm_batch {
 };
 
 namespace {
+
+// Block shapes of the single-run kernel under map 3 (threads in x, in y).
+constexpr int kNumShapes = 4;
+constexpr int kShapes[kNumShapes][2] = {{128, 2}, {64, 4}, {32, 8}, {256, 1}};
+constexpr int kNumClasses = 4;
+
+// Size class of a run for the shape tuner: by grid width, <= 64, <= 128, <= 256, wider.
+int width_class(const lbm_handle* h) {
+    const int nx = h->p.nx;
+    return nx <= 64 ? 0 : (nx <= 128 ? 1 : (nx <= 256 ? 2 : 3));
+}
 
 int pow2_at_least(int v) {
     int p = 32;
@@ -925,28 +940,40 @@ int upload_batch(lbm_batch* b, const std::vector<lbmk::Tile>& tiles) {
     return LBM_OK;
 }
 
+// 1 when a run of the batch uses the Eq. 9 per-node rates (the tile kernel then
+// compiles them in; runs without them still take their constant rates).
+int batch_phase(const lbm_batch* b) {
+    for (const lbm_handle* h : b->runs)
+        if (phase_k_of(h)) return 1;
+    return 0;
+}
+
 cudaError_t batch_launch(lbm_batch* b, int parity, cudaStream_t s) {
-    const int q = b->qt, fl = b->flow;
+    const int q = b->qt, fl = b->flow, ph = batch_phase(b);
     const auto* pf = static_cast<const lbmk::StepParams<float>*>(b->params);
     switch (b->precision) {
         case LBM_F64:
             return lbmk::launch_batch<lbmk::MODE_F64>(static_cast<const lbmk::StepParams<double>*>(b->params),
-                                                      b->tiles, b->ntiles, b->chunk, b->grid, parity, q, fl, s);
+                                                      b->tiles, b->ntiles, b->chunk, b->grid, parity, q, fl, ph, s);
         case LBM_F32:
-            return lbmk::launch_batch<lbmk::MODE_F32>(pf, b->tiles, b->ntiles, b->chunk, b->grid, parity, q, fl, s);
+            return lbmk::launch_batch<lbmk::MODE_F32>(pf, b->tiles, b->ntiles, b->chunk, b->grid, parity, q, fl, ph,
+                                                      s);
         case LBM_F16:
-            return lbmk::launch_batch<lbmk::MODE_F16>(pf, b->tiles, b->ntiles, b->chunk, b->grid, parity, q, fl, s);
+            return lbmk::launch_batch<lbmk::MODE_F16>(pf, b->tiles, b->ntiles, b->chunk, b->grid, parity, q, fl, ph,
+                                                      s);
         default:
-            return lbmk::launch_batch<lbmk::MODE_BF16>(pf, b->tiles, b->ntiles, b->chunk, b->grid, parity, q, fl, s);
+            return lbmk::launch_batch<lbmk::MODE_BF16>(pf, b->tiles, b->ntiles, b->chunk, b->grid, parity, q, fl, ph,
+                                                       s);
     }
 }
 
 int batch_blocks_per_sm(const lbm_batch* b) {
+    const int ph = batch_phase(b);
     switch (b->precision) {
-        case LBM_F64: return lbmk::batch_blocks_per_sm<lbmk::MODE_F64>(b->qt, b->flow);
-        case LBM_F32: return lbmk::batch_blocks_per_sm<lbmk::MODE_F32>(b->qt, b->flow);
-        case LBM_F16: return lbmk::batch_blocks_per_sm<lbmk::MODE_F16>(b->qt, b->flow);
-        default: return lbmk::batch_blocks_per_sm<lbmk::MODE_BF16>(b->qt, b->flow);
+        case LBM_F64: return lbmk::batch_blocks_per_sm<lbmk::MODE_F64>(b->qt, b->flow, ph);
+        case LBM_F32: return lbmk::batch_blocks_per_sm<lbmk::MODE_F32>(b->qt, b->flow, ph);
+        case LBM_F16: return lbmk::batch_blocks_per_sm<lbmk::MODE_F16>(b->qt, b->flow, ph);
+        default: return lbmk::batch_blocks_per_sm<lbmk::MODE_BF16>(b->qt, b->flow, ph);
     }
 }
 
@@ -984,12 +1011,12 @@ void free_batch(lbm_batch* b) {
     delete b;
 }
 
-const void* step_kernel_of(int precision, int qt, int flow) {
+const void* step_kernel_of(int precision, int qt, int flow, int ph) {
     switch (precision) {
-        case LBM_F64: return lbmk::step_kernel<lbmk::MODE_F64>(qt, flow);
-        case LBM_F32: return lbmk::step_kernel<lbmk::MODE_F32>(qt, flow);
-        case LBM_F16: return lbmk::step_kernel<lbmk::MODE_F16>(qt, flow);
-        default: return lbmk::step_kernel<lbmk::MODE_BF16>(qt, flow);
+        case LBM_F64: return lbmk::step_kernel<lbmk::MODE_F64>(qt, flow, ph);
+        case LBM_F32: return lbmk::step_kernel<lbmk::MODE_F32>(qt, flow, ph);
+        case LBM_F16: return lbmk::step_kernel<lbmk::MODE_F16>(qt, flow, ph);
+        default: return lbmk::step_kernel<lbmk::MODE_BF16>(qt, flow, ph);
     }
 }
 
@@ -998,10 +1025,10 @@ const void* step_kernel_of(int precision, int qt, int flow) {
 int build_chain_graph(lbm_batch* b, int steps, cudaGraphExec_t* out) {
     cudaGraph_t g = nullptr;
     if (cudaGraphCreate(&g, 0) != cudaSuccess) return LBM_ERR_CUDA;
-    const void* fn = step_kernel_of(b->precision, b->qt, b->flow);
     cudaError_t e = cudaSuccess;
     for (size_t r = 0; r < b->runs.size() && e == cudaSuccess; ++r) {
         lbm_handle* h = b->runs[r];
+        const void* fn = step_kernel_of(b->precision, b->qt, b->flow, phase_k_of(h));
         cudaGraphNode_t prev = nullptr;
         for (int k = 0; k < steps && e == cudaSuccess; ++k) {
             const int from = b->flip[r] ^ (k & 1);
@@ -1015,10 +1042,11 @@ int build_chain_graph(lbm_batch* b, int steps, cudaGraphExec_t* out) {
                 Pf = make_params<float>(h, from);
                 args[0] = &Pf;
             }
+            const int bx = kShapes[b->shape[r]][0], by = kShapes[b->shape[r]][1];
             cudaKernelNodeParams kp = {};
             kp.func = const_cast<void*>(fn);
-            kp.gridDim = lbmk::grid_for(h->p.nx, h->p.ny);
-            kp.blockDim = dim3(lbmk::kBlockX, lbmk::kBlockY);
+            kp.gridDim = dim3((unsigned)((h->p.nx + bx - 1) / bx), (unsigned)((h->p.ny + by - 1) / by), 1u);
+            kp.blockDim = dim3((unsigned)bx, (unsigned)by, 1u);
             kp.sharedMemBytes = 0;
             kp.kernelParams = args;
             kp.extra = nullptr;
@@ -1161,6 +1189,7 @@ int lbm_batch_create(lbm_handle* const* runs, int32_t n_runs, int32_t autotune, 
     b->ctx = runs[0]->ctx;
     b->parity = 0;
     for (int r = 0; r < n_runs; ++r) b->flip.push_back(runs[r]->cur);
+    b->shape.assign(n_runs, 0);
     b->params_stride = b->precision == LBM_F64 ? sizeof(lbmk::StepParams<double>) : sizeof(lbmk::StepParams<float>);
     for (lbm_handle* h : b->runs)
         if (cudaStreamSynchronize(h->stream) != cudaSuccess) {
@@ -1204,10 +1233,35 @@ int lbm_batch_create(lbm_handle* const* runs, int32_t n_runs, int32_t autotune, 
             double best = 1e30;
             std::vector<int> keep_flip(clones.size(), 0);   // fresh clones all start on copy 0
             b->flip.swap(keep_flip);
+            // map 3: the block shape of each width class, by coordinate descent
+            if (upload_batch(b, make_tiles(b->runs, b->flip, 128)) == LBM_OK) {
+                set_mapping(b, 3, resident);
+                double t3 = time_batch(b, 16);
+                for (int c = 0; c < kNumClasses; ++c) {
+                    std::vector<int> members;
+                    for (size_t r = 0; r < b->runs.size(); ++r)
+                        if (width_class(b->runs[r]) == c) members.push_back((int)r);
+                    if (members.empty()) continue;
+                    int chosen = 0;
+                    for (int sh = 1; sh < kNumShapes; ++sh) {
+                        for (int r : members) b->shape[r] = sh;
+                        const double us = time_batch(b, 16);
+                        if (us < t3) {
+                            t3 = us;
+                            chosen = sh;
+                        }
+                    }
+                    for (int r : members) b->shape[r] = chosen;
+                }
+                if (t3 < best) {
+                    best = t3;
+                    best_cap = 128;
+                    best_map = 3;
+                }
+            }
             for (int cap : {64, 128, 256}) {
                 if (upload_batch(b, make_tiles(b->runs, b->flip, cap)) != LBM_OK) continue;
-                for (int map = 0; map < 4; ++map) {
-                    if (map == 3 && cap != 128) continue;   // the single-run kernels do not use tiles
+                for (int map = 0; map < 3; ++map) {
                     set_mapping(b, map, resident);
                     const double us = time_batch(b, 16);
                     if (us < best) {
@@ -1275,6 +1329,28 @@ int lbm_batch_info(const lbm_batch* b, int32_t* n_tiles, int32_t* width_cap, int
     if (mapping) *mapping = b->mapping;
     if (grid) *grid = b->grid;
     if (tuned_us_per_step) *tuned_us_per_step = b->tuned_us;
+    return LBM_OK;
+}
+
+int lbm_batch_set_block(lbm_batch* b, int32_t run, int32_t block_x, int32_t block_y) {
+    if (!b || run < 0 || run >= (int32_t)b->runs.size()) return LBM_ERR_ARG;
+    int id = -1;
+    for (int k = 0; k < kNumShapes; ++k)
+        if (kShapes[k][0] == block_x && kShapes[k][1] == block_y) id = k;
+    if (id < 0) return LBM_ERR_ARG;
+    if (cudaStreamSynchronize(b->stream) != cudaSuccess) {
+        cudaGetLastError();
+        return LBM_ERR_CUDA;
+    }
+    batch_destroy_graph(b);
+    b->shape[run] = id;
+    return LBM_OK;
+}
+
+int lbm_batch_get_block(const lbm_batch* b, int32_t run, int32_t* block_x, int32_t* block_y) {
+    if (!b || run < 0 || run >= (int32_t)b->runs.size()) return LBM_ERR_ARG;
+    if (block_x) *block_x = kShapes[b->shape[run]][0];
+    if (block_y) *block_y = kShapes[b->shape[run]][1];
     return LBM_OK;
 }
 

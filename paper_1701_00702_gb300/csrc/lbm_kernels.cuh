@@ -561,8 +561,11 @@ __device__ __forceinline__ void store_thermal(const StepParams<typename ModeTrai
 // ---------------------------------------------------------------------------
 
 // One time step of node (x, y): steps a1-a9 (pull, walls, state, blend,
+// velocity, three collisions, store).  PH = true compiles the Eq. 9 variant's
+// per-node PCM rates in (taken where P.phase_k is set); PH = false leaves them
+// out of the kernel altogether.
 // velocity, three collisions, store).
-template <int M, int QT, bool FLOW>
+template <int M, int QT, bool FLOW, bool PH = false>
 __device__ __forceinline__ void step_node(const StepParams<typename ModeTraits<M>::R>& P, int x, int y) {
     using R = typename ModeTraits<M>::R;
     using PL = Planes<M, QT, FLOW>;
@@ -629,7 +632,7 @@ __device__ __forceinline__ void step_node(const StepParams<typename ModeTraits<M
     {
         R ne[QT];
         neq_pcm<R, QT>(P, n.H, n.Tf, n.ux, n.uy, ne);
-        if (P.phase_k) {
+        if (PH && P.phase_k) {
             // Eq. 9 at the node's liquid fraction -> zeta_alpha (Eq. A19) -> zeta_e (Eq. 53)
             const R za = fast_rcp(R(0.5) + P.ks_c + n.fl * (P.kl_c - P.ks_c));
 #pragma unroll
@@ -679,13 +682,21 @@ __device__ __forceinline__ void step_node(const StepParams<typename ModeTraits<M
     if (bad) atomicOr(P.status, STATUS_UNSTABLE);
 }
 
-// One run: one thread per node, 128 x 2 threads per block.
+// Blocks of 256 threads each SM must hold, which caps the registers per
+// thread: six for FP32 D2Q5 with flow (bandwidth-bound; 40 registers), five for
+// the 16-bit forms (issue-bound; 48 registers); the others take what their
+// registers allow.
 template <int M, int QT, bool FLOW>
-__global__ void __launch_bounds__(256) fused_step(const __grid_constant__ StepParams<typename ModeTraits<M>::R> P) {
+constexpr int kMinBlocks = (QT == 5 && FLOW) ? (M == MODE_F32 ? 6 : (M == MODE_F64 ? 1 : 5)) : 1;
+
+// One run: one thread per node, 256 threads per block (128 x 2 by default;
+// the batch's map 3 may take other shapes).
+template <int M, int QT, bool FLOW, bool PH>
+__global__ void __launch_bounds__(256, (kMinBlocks<M, QT, FLOW>)) fused_step(const __grid_constant__ StepParams<typename ModeTraits<M>::R> P) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     if (x >= P.nx || y >= P.ny) return;
-    step_node<M, QT, FLOW>(P, x, y);
+    step_node<M, QT, FLOW, PH>(P, x, y);
 }
 
 // Many runs in one launch.  A tile is w x (256 / w) nodes of one run (w a
@@ -700,7 +711,7 @@ struct Tile {
     int run, x0, y0, log2w_flip;   // log2 w in bits 0-7, flip in bit 8
 };
 
-template <int M, int QT, bool FLOW>
+template <int M, int QT, bool FLOW, bool PH>
 __global__ void __launch_bounds__(256) batch_step(const StepParams<typename ModeTraits<M>::R>* __restrict__ runs,
                                                   const Tile* __restrict__ tiles, int ntiles, int chunk, int parity) {
     using R = typename ModeTraits<M>::R;
@@ -724,7 +735,7 @@ __global__ void __launch_bounds__(256) batch_step(const StepParams<typename Mode
         const int lg = tl.log2w_flip & 0xff;
         const int x = tl.x0 + (threadIdx.x & ((1 << lg) - 1));
         const int y = tl.y0 + (threadIdx.x >> lg);
-        if (x < P.nx && y < P.ny) step_node<M, QT, FLOW>(P, x, y);
+        if (x < P.nx && y < P.ny) step_node<M, QT, FLOW, PH>(P, x, y);
     }
 }
 

@@ -113,11 +113,19 @@ inline cudaError_t dispatch(int qt, int flow, Fn&& fn) {
     return flow ? fn.template operator()<M, 9, true>() : fn.template operator()<M, 9, false>();
 }
 
+// The step kernels also take PH (the Eq. 9 per-node rates compiled in or not).
+template <int M, typename Fn>
+inline cudaError_t dispatch_step(int qt, int flow, int ph, Fn&& fn) {
+    return dispatch<M>(qt, flow, [&]<int MM, int Q, bool F>() {
+        return ph ? fn.template operator()<MM, Q, F, true>() : fn.template operator()<MM, Q, F, false>();
+    });
+}
+
 template <int M>
 cudaError_t launch_step(const StepParams<typename ModeTraits<M>::R>& P, int qt, int flow, cudaStream_t s) {
     const dim3 g = grid_for(P.nx, P.ny), b(kBlockX, kBlockY);
-    return dispatch<M>(qt, flow, [&]<int MM, int Q, bool F>() {
-        fused_step<MM, Q, F><<<g, b, 0, s>>>(P);
+    return dispatch_step<M>(qt, flow, P.phase_k, [&]<int MM, int Q, bool F, bool PH>() {
+        fused_step<MM, Q, F, PH><<<g, b, 0, s>>>(P);
         return cudaGetLastError();
     });
 }
@@ -165,11 +173,12 @@ cudaError_t launch_convert(const StepParams<float>& P, const DenseState& D, int 
     });
 }
 
+// ph: some run of the batch uses the Eq. 9 per-node rates.
 template <int M>
 cudaError_t launch_batch(const StepParams<typename ModeTraits<M>::R>* runs, const Tile* tiles, int ntiles,
-                         int chunk, int grid, int parity, int qt, int flow, cudaStream_t s) {
-    return dispatch<M>(qt, flow, [&]<int MM, int Q, bool F>() {
-        batch_step<MM, Q, F><<<grid, 256, 0, s>>>(runs, tiles, ntiles, chunk, parity);
+                         int chunk, int grid, int parity, int qt, int flow, int ph, cudaStream_t s) {
+    return dispatch_step<M>(qt, flow, ph, [&]<int MM, int Q, bool F, bool PH>() {
+        batch_step<MM, Q, F, PH><<<grid, 256, 0, s>>>(runs, tiles, ntiles, chunk, parity);
         return cudaGetLastError();
     });
 }
@@ -177,16 +186,20 @@ cudaError_t launch_batch(const StepParams<typename ModeTraits<M>::R>* runs, cons
 // The single-run kernel as a function pointer, for kernel nodes built
 // directly into a graph (one chain of steps per run).
 template <int M>
-const void* step_kernel(int qt, int flow) {
-    if (qt == 5) return flow ? (const void*)fused_step<M, 5, true> : (const void*)fused_step<M, 5, false>;
-    return flow ? (const void*)fused_step<M, 9, true> : (const void*)fused_step<M, 9, false>;
+const void* step_kernel(int qt, int flow, int ph) {
+    const void* fn = nullptr;
+    dispatch_step<M>(qt, flow, ph, [&]<int MM, int Q, bool F, bool PH>() {
+        fn = (const void*)fused_step<MM, Q, F, PH>;
+        return cudaSuccess;
+    });
+    return fn;
 }
 
 template <int M>
-int batch_blocks_per_sm(int qt, int flow) {
+int batch_blocks_per_sm(int qt, int flow, int ph) {
     int n = 0;
-    dispatch<M>(qt, flow, [&]<int MM, int Q, bool F>() {
-        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_step<MM, Q, F>, 256, 0);
+    dispatch_step<M>(qt, flow, ph, [&]<int MM, int Q, bool F, bool PH>() {
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_step<MM, Q, F, PH>, 256, 0);
     });
     return n;
 }
@@ -199,9 +212,9 @@ int batch_blocks_per_sm(int qt, int flow) {
                                         int, int, cudaStream_t);                                              \
     template cudaError_t launch_init<M>(const StepParams<ModeTraits<M>::R>&, const InitVals&, int, int, cudaStream_t); \
     template cudaError_t launch_batch<M>(const StepParams<ModeTraits<M>::R>*, const Tile*, int, int, int, int, int, \
-                                         int, cudaStream_t);                                                    \
-    template int batch_blocks_per_sm<M>(int, int);                                                        \
-    template const void* step_kernel<M>(int, int);
+                                         int, int, cudaStream_t);                                               \
+    template int batch_blocks_per_sm<M>(int, int, int);                                                   \
+    template const void* step_kernel<M>(int, int, int);
 
 #define LBMK_INSTANTIATE_CONVERT(M) \
     template cudaError_t launch_convert<M>(const StepParams<float>&, const DenseState&, int, int, int, cudaStream_t);

@@ -127,6 +127,10 @@ def lib() -> ctypes.CDLL:
         L.lbm_batch_step.restype = ctypes.c_int
         L.lbm_batch_configure.argtypes = [vp, i32, i32]
         L.lbm_batch_configure.restype = ctypes.c_int
+        L.lbm_batch_set_block.argtypes = [vp, i32, i32, i32]
+        L.lbm_batch_set_block.restype = ctypes.c_int
+        L.lbm_batch_get_block.argtypes = [vp, i32, ctypes.POINTER(i32), ctypes.POINTER(i32)]
+        L.lbm_batch_get_block.restype = ctypes.c_int
         L.lbm_batch_info.argtypes = [vp] + [ctypes.POINTER(i32)] * 4 + [ctypes.POINTER(ctypes.c_double)]
         L.lbm_batch_info.restype = ctypes.c_int
         L.lbm_batch_destroy.argtypes = [vp]
@@ -380,7 +384,7 @@ class Solver:
 
 
 class Batch:
-    """Runs advanced together by one launch per time step (lbm_batch_*)."""
+    """Runs advanced together from CUDA graphs (lbm_batch_*)."""
 
     MAPS = ("one block per tile", "persistent contiguous chunks", "persistent grid stride",
             "single-run kernel chains")
@@ -403,6 +407,20 @@ class Batch:
     def configure(self, width_cap: int, mapping: int) -> "Batch":
         _check(lib().lbm_batch_configure(self._b, int(width_cap), int(mapping)), "lbm_batch_configure")
         return self
+
+    def set_block(self, run: int, block_x: int, block_y: int) -> "Batch":
+        """Block shape of one run under map 3 (128x2, 64x4, 32x8 or 256x1)."""
+        _check(lib().lbm_batch_set_block(self._b, int(run), int(block_x), int(block_y)), "lbm_batch_set_block")
+        return self
+
+    def blocks(self) -> list:
+        """Block shape (x, y) of every run under map 3."""
+        out = []
+        for r in range(len(self.runs)):
+            bx, by = ctypes.c_int32(), ctypes.c_int32()
+            _check(lib().lbm_batch_get_block(self._b, r, ctypes.byref(bx), ctypes.byref(by)), "lbm_batch_get_block")
+            out.append((bx.value, by.value))
+        return out
 
     def info(self) -> dict:
         v = [ctypes.c_int32() for _ in range(4)]

@@ -173,3 +173,35 @@ def test_batch_from_random_states(lbm, prec, qt, mapping):
     b.close()
     for s in runs + solo:
         s.close()
+
+
+def test_block_shapes_under_map_3_change_no_result(lbm):
+    """Per-run block shapes under map 3 (the tuner's per-size-class choice)
+    leave every run bit for bit equal to lbm_step."""
+    shapes = [(131, 7, 0, 0), (70, 33, 1, 0), (64, 64, 1, 1), (300, 45, 0, 0)]
+    ps = [inputs.cavity(nx, ny=ny, precision=1, periodic_x=px, periodic_y=py, L_char=100.0, Ra=1e7)
+          for nx, ny, px, py in shapes]
+    runs, solo = [], []
+    for k, p in enumerate(ps):
+        F, G, Hm, dT = inputs.random_state(p["nx"], p["ny"], 5, seed=60 + k, H_range=(-0.2, 1.6), f_base=W9.ravel())
+        for dst in (runs, solo):
+            s = lbm.Solver(p)
+            s.set_state(F - W9, G, Hm, dT)
+            dst.append(s)
+    b = lbm.Batch(runs, autotune=False).configure(128, 3)
+    for r, blk in enumerate([(64, 4), (32, 8), (256, 1), (128, 2)]):
+        b.set_block(r, *blk)
+    assert b.blocks() == [(64, 4), (32, 8), (256, 1), (128, 2)]
+    with pytest.raises(lbm.LbmError):
+        b.set_block(0, 16, 16)
+    b.step(70)
+    for s in solo:
+        s.step(70)
+    for r, s in zip(runs, solo):
+        assert np.array_equal(r.save(), s.save())
+    b.close()
+    tuned = lbm.Batch(runs, autotune=True)
+    assert all(blk in [(128, 2), (64, 4), (32, 8), (256, 1)] for blk in tuned.blocks())
+    tuned.close()
+    for s in runs + solo:
+        s.close()
