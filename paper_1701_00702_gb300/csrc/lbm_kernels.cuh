@@ -522,7 +522,10 @@ __device__ __forceinline__ void store_thermal(const StepParams<typename ModeTrai
     if constexpr (kSplit<M>) {
         // reference from the provisional rest population, 16-bit deviations,
         // then the rest population that closes the balance with the movers as
-        // readers will rebuild them
+        // encoded here.  Readers rebuild the reference from the stored rest
+        // population, which differs from the provisional one by the movers'
+        // 16-bit roundings, so the balance as read holds to those roundings
+        // times the slope of the reference (about a sixth of one rounding)
         using B = typename ModeTraits<M>::B;
         float sm = v[1];
 #pragma unroll
