@@ -183,6 +183,7 @@ def time_oracle(p: dict, budget_s: float, max_steps: int):
     """Times the FP64 oracle on cavity p for about budget_s seconds of CPU work."""
     import oracle
     o = oracle.Oracle(p)
+    o.run(1)                                  # starts the thread pool
     t0 = time.perf_counter()
     o.run(2)
     per = max((time.perf_counter() - t0) / 2.0, 1e-6)
@@ -190,10 +191,27 @@ def time_oracle(p: dict, budget_s: float, max_steps: int):
     t0 = time.perf_counter()
     o.run(n)
     dt = time.perf_counter() - t0
+    per = dt / n
     cells = p["nx"] * p["ny"]
-    return {"value": cells * n / dt / 1e6, "unit": UNIT, "cores": o.threads, "kind": "oracle",
-            "sample": f"{n} time steps of the {p['nx']}x{p['ny']} cavity from the uniform start "
-                      f"({dt:.1f} s, FP64 oracle, OpenMP over rows)"}
+    out = {"value": cells * n / dt / 1e6, "unit": UNIT, "cores": o.threads, "kind": "oracle",
+           "sample": f"{n} time steps of the {p['nx']}x{p['ny']} cavity from the uniform start "
+                     f"({dt:.1f} s, FP64 oracle, OpenMP over rows)"}
+    cores = o.threads
+    # one thread on the same cavity, then the 200 x 4 conduction case in full (20,000 steps)
+    o1 = oracle.Oracle(p, threads=1)
+    n1 = int(max(2, min(max_steps, budget_s / 4.0 / (per * cores))))
+    t0 = time.perf_counter()
+    o1.run(n1)
+    d1 = time.perf_counter() - t0
+    out["single_thread"] = {"value": cells * n1 / d1 / 1e6, "unit": UNIT,
+                            "sample": f"{n1} time steps of the same cavity on one thread ({d1:.1f} s)"}
+    oracle.lib().orc_set_threads(cores)
+    from paper_1701_00702_gb300 import inputs
+    oc = oracle.Oracle(inputs.conduction_1d())
+    t0 = time.perf_counter()
+    oc.run(20_000)
+    out["conduction_200x4_20000_steps_s"] = time.perf_counter() - t0
+    return out
 
 
 def run_reference(args):
