@@ -113,6 +113,24 @@ def dist_env():
     return rank, world, local
 
 
+def max_over_ranks(x: float, world: int) -> float:
+    """The largest of every rank's x (the slowest rank's time); x itself at N = 1."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_mlups(world: int, cells: int, lb_steps: int, steps: int, seconds: float) -> float:
+    """Whole-job throughput of `world` replicas, each updating `cells` nodes
+    `lb_steps` times per benchmark step for `steps` steps, over the slowest
+    rank's `seconds`."""
+    return world * cells * lb_steps * steps / seconds / 1e6
+
+
 def workload_config(args, p, chunk):
     return {
         "workload": f"square-cavity melting with natural convection {p['nx']}x{p['ny']} {PREC_NAMES[p['precision']].upper()}",
@@ -388,12 +406,8 @@ def main():
         clk = clocks.stop()
         if s.status() != 0:
             raise SystemExit("solver reported an unstable state")
-        total_ms = sum(times_ms)
-        if world > 1:
-            t = torch.tensor([total_ms], dtype=torch.float64)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            total_ms = float(t.item())
-        value = world * cells * chunk * args.steps / (total_ms / 1e3) / 1e6
+        total_ms = max_over_ranks(sum(times_ms), world)
+        value = replica_mlups(world, cells, chunk, args.steps, total_ms / 1e3)
         launch_ms_small = total_ms / (args.steps * chunk)
 
         # end to end through the C ABI with host buffers
@@ -420,12 +434,8 @@ def main():
                 s.set_state(pin["f"], pin["g"], pin["h"], pin["dT"])
                 s.step(chunk)
                 s.fields_into(outs)
-            e2e_s = time.perf_counter() - t0
-            if world > 1:
-                t = torch.tensor([e2e_s], dtype=torch.float64)
-                torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-                e2e_s = float(t.item())
-            e2e = {"value": world * cells * chunk * args.steps / e2e_s / 1e6, "unit": UNIT,
+            e2e_s = max_over_ranks(time.perf_counter() - t0, world)
+            e2e = {"value": replica_mlups(world, cells, chunk, args.steps, e2e_s), "unit": UNIT,
                    "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
         s.close()
         del flush

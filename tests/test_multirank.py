@@ -1,0 +1,62 @@
+"""The multi-GPU path is replicas only: each rank runs its own cavity, and the
+only cross-rank traffic is the barrier and the maximum of the timings.  This
+checks that host-side logic with two gloo ranks on the CPU, and that the
+reference arm leaves every rank but 0 without work."""
+import os
+import socket
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port() -> int:
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank(rank: int, world: int, port: int, q):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    import torch.distributed as dist
+    sys.path.insert(0, ROOT)
+    import bench
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    local = [1.5, 4.0][rank]                       # the second rank is the slow one
+    slowest = bench.max_over_ranks(local, world)
+    dist.barrier()
+    q.put((rank, slowest, bench.replica_mlups(world, 65536, 2000, 5, slowest)))
+    dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_take_the_slowest_time():
+    import torch.multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    got = sorted(q.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for rank, slowest, mlups in got:
+        assert slowest == 4.0
+        assert mlups == pytest.approx(2 * 65536 * 2000 * 5 / 4.0 / 1e6)
+
+
+def test_single_rank_needs_no_process_group():
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.max_over_ranks(2.5, 1) == 2.5
+    assert bench.replica_mlups(1, 100, 10, 2, 1.0) == pytest.approx(2e-3)
+
+
+def test_reference_arm_on_other_ranks_exits_without_work():
+    env = dict(os.environ, RANK="1", WORLD_SIZE="2", LOCAL_RANK="1")
+    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "1", "--warmup", "3"],
+                       cwd=ROOT, env=env, capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0 and r.stdout.strip() == ""
