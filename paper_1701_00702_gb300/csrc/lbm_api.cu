@@ -139,10 +139,11 @@ int derive_impl(const lbm_params* pp, lbm_derived* out) {
 
 struct Layout {
     int pitch, nplanes, nwide;
-    long long plane;
+    int cpr;          // chunks of lbmk::kChunk nodes per row
+    size_t chunk_bytes;   // one chunk: every plane of kChunk nodes
     size_t elem;      // bytes of one bulk element (8, 4 or 2)
     size_t relem;     // bytes of one arithmetic element (8 or 4): history, fields, state I/O
-    size_t copy_bytes, wide_off, dT_bytes, off_buf1, off_dT, off_status, off_scratch, off_out, total;
+    size_t copy_bytes, dT_bytes, off_buf1, off_dT, off_status, off_scratch, off_out, total;
     int nblocks;
 };
 
@@ -153,18 +154,18 @@ Layout layout_of(const lbm_params& p) {
     const bool split = split_mode(p.precision);
     L.elem = p.precision == LBM_F64 ? 8 : (split ? 2 : 4);
     L.relem = p.precision == LBM_F64 ? 8 : 4;
-    const int align_elems = (int)(128 / L.elem);
-    L.pitch = (p.nx + align_elems - 1) / align_elems * align_elems;
-    L.plane = (long long)L.pitch * p.ny;
     // bulk planes: flow (9, deviations), PCM and metal populations; FP32 adds the low
     // part of the PCM rest population; 16-bit modes keep both rest populations in
-    // two FP32 "wide" planes after the bulk planes of each copy
+    // two FP32 "wide" planes.  A copy is [ny][cpr] chunks, each [plane][kChunk]
+    // (the bulk planes, then the wide planes); the history is [ny][pitch].
     const int fb = p.flow ? 9 : 0;
     L.nplanes = split ? fb + 2 * (p.thermal_q - 1) : fb + 2 * p.thermal_q + (p.precision == LBM_F32 ? 1 : 0);
     L.nwide = split ? 2 : 0;
-    L.wide_off = align_up((size_t)L.nplanes * (size_t)L.plane * L.elem);
-    L.copy_bytes = L.wide_off + align_up((size_t)L.nwide * (size_t)L.plane * 4);
-    L.dT_bytes = align_up((size_t)L.plane * L.relem);
+    L.cpr = (p.nx + lbmk::kChunk - 1) / lbmk::kChunk;
+    L.pitch = L.cpr * lbmk::kChunk;
+    L.chunk_bytes = (size_t)lbmk::kChunk * (L.nplanes * L.elem + L.nwide * 4);
+    L.copy_bytes = align_up((size_t)L.cpr * p.ny * L.chunk_bytes);
+    L.dT_bytes = align_up((size_t)L.pitch * p.ny * L.relem);
     L.nblocks = lbmk::diag_blocks(p.nx, p.ny);
     L.off_buf1 = L.copy_bytes;
     L.off_dT = 2 * L.copy_bytes;
@@ -225,23 +226,14 @@ lbmk::StepParams<R> make_params(const lbm_handle* h, int from) {
     const lbm_derived& d = h->d;
     lbmk::StepParams<R> P;
     std::memset(&P, 0, sizeof P);
-    char* cur = static_cast<char*>(h->buf[from]);
-    char* nxt = static_cast<char*>(h->buf[1 - from]);
-    const size_t pb = (size_t)h->L.plane * h->L.elem;
-    for (int q = 0; q < h->L.nplanes; ++q) {
-        P.src[q] = cur + q * pb;
-        P.dst[q] = nxt + q * pb;
-    }
-    for (int w = 0; w < h->L.nwide; ++w) {
-        P.src[h->L.nplanes + w] = cur + h->L.wide_off + (size_t)w * h->L.plane * 4;
-        P.dst[h->L.nplanes + w] = nxt + h->L.wide_off + (size_t)w * h->L.plane * 4;
-    }
+    P.src = static_cast<const char*>(h->buf[from]);
+    P.dst = static_cast<char*>(h->buf[1 - from]);
+    P.cpr = h->L.cpr;
     P.dT = static_cast<R*>(h->dT);
     P.status = h->status;
     P.nx = p.nx;
     P.ny = p.ny;
     P.pitch = h->L.pitch;
-    P.plane = h->L.plane;
     P.per_x = p.periodic_x;
     P.per_y = p.periodic_y;
     P.solid_scheme = p.solid_scheme;
@@ -321,6 +313,13 @@ lbmk::StepParams<R> make_params(const lbm_handle* h, int from) {
     }
     P.a_m = (R)(d.h_v / ((1.0 - phi) * d.rho_m));
     return P;
+}
+
+template <int M>
+cudaError_t launch_convert_mode(lbm_handle* h, const lbmk::DenseState<typename lbmk::ModeTraits<M>::R>& D,
+                                int to_dense) {
+    using R = typename lbmk::ModeTraits<M>::R;
+    return lbmk::launch_convert<M>(make_params<R>(h, h->cur), D, to_dense, h->p.thermal_q, h->p.flow, h->stream);
 }
 
 int cuda_fail(lbm_handle* h) {
@@ -631,48 +630,59 @@ int lbm_diag(lbm_handle* h, double* melt_frac, double* nu_hot, double* enthalpy,
     return rc;
 }
 
-static int copy_planes(lbm_handle* h, void* host_or_dev, int first_plane, int nplanes, bool to_state, int on_device,
-                       void* state_base, size_t el) {
-    if (!host_or_dev || nplanes == 0) return LBM_OK;
-    char* s = static_cast<char*>(state_base) + (size_t)first_plane * h->L.plane * el;
+// Copies the exchange history [ny][nx] in or out of its [ny][pitch] array.
+static int copy_history(lbm_handle* h, void* host_or_dev, bool to_state, int on_device) {
+    if (!host_or_dev) return LBM_OK;
+    const size_t el = h->L.relem;
     const size_t dpitch = (size_t)h->p.nx * el, spitch = (size_t)h->L.pitch * el;
-    const size_t rows = (size_t)nplanes * h->p.ny;
     cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : (to_state ? cudaMemcpyHostToDevice
                                                                            : cudaMemcpyDeviceToHost);
-    cudaError_t e = to_state ? cudaMemcpy2DAsync(s, spitch, host_or_dev, dpitch, dpitch, rows, kind, h->stream)
-                             : cudaMemcpy2DAsync(host_or_dev, dpitch, s, spitch, dpitch, rows, kind, h->stream);
+    cudaError_t e = to_state ? cudaMemcpy2DAsync(h->dT, spitch, host_or_dev, dpitch, dpitch, h->p.ny, kind, h->stream)
+                             : cudaMemcpy2DAsync(host_or_dev, dpitch, h->dT, spitch, dpitch, h->p.ny, kind, h->stream);
     return e == cudaSuccess ? LBM_OK : cuda_fail(h);
 }
 
-// 16-bit runs: the state goes through dense FP32 arrays [q][ny][nx] on the device.
-static int convert_state_io(lbm_handle* h, void* f, void* g, void* hm, int to_state, int on_device) {
+// The state goes through dense arrays [q][ny][nx] of the run's arithmetic type
+// on the device; the conversion kernel moves them to or from the chunked copy.
+static int convert_state_io(lbm_handle* h, void* f, void* g, void* hm, void* lo, int to_state, int on_device) {
     const int Q = h->p.thermal_q;
-    const size_t n = (size_t)h->p.nx * h->p.ny;
+    const size_t n = (size_t)h->p.nx * h->p.ny, el = h->L.relem;
     const size_t nf = h->p.flow ? 9 : 0;
-    float* stage = static_cast<float*>(dev_alloc(h, align_up((nf + 2 * Q) * n * sizeof(float))));
+    const bool has_lo = h->p.precision == LBM_F32;
+    char* stage = static_cast<char*>(dev_alloc(h, align_up((nf + 2 * Q + (has_lo ? 1 : 0)) * n * el)));
     if (!stage) return LBM_ERR_OOM;
-    lbmk::DenseState D;
-    D.f = (h->p.flow && f) ? stage : nullptr;
-    D.g = g ? stage + nf * n : nullptr;
-    D.h = hm ? stage + (nf + Q) * n : nullptr;
+    void* Df = (h->p.flow && f) ? stage : nullptr;
+    void* Dg = g ? stage + nf * n * el : nullptr;
+    void* Dh = hm ? stage + (nf + Q) * n * el : nullptr;
+    void* Dl = (has_lo && lo) ? stage + (nf + 2 * Q) * n * el : nullptr;
     const cudaMemcpyKind in = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     const cudaMemcpyKind out = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
     cudaError_t e = cudaSuccess;
     if (to_state) {
-        if (D.f) e = cudaMemcpyAsync(D.f, f, 9 * n * sizeof(float), in, h->stream);
-        if (e == cudaSuccess && D.g) e = cudaMemcpyAsync(D.g, g, Q * n * sizeof(float), in, h->stream);
-        if (e == cudaSuccess && D.h) e = cudaMemcpyAsync(D.h, hm, Q * n * sizeof(float), in, h->stream);
+        if (Df) e = cudaMemcpyAsync(Df, f, 9 * n * el, in, h->stream);
+        if (e == cudaSuccess && Dg) e = cudaMemcpyAsync(Dg, g, Q * n * el, in, h->stream);
+        if (e == cudaSuccess && Dh) e = cudaMemcpyAsync(Dh, hm, Q * n * el, in, h->stream);
+        if (e == cudaSuccess && Dl) e = cudaMemcpyAsync(Dl, lo, n * el, in, h->stream);
     }
     if (e == cudaSuccess) {
-        const lbmk::StepParams<float> P = make_params<float>(h, h->cur);
-        e = h->p.precision == LBM_F16
-                ? lbmk::launch_convert<lbmk::MODE_F16>(P, D, to_state ? 0 : 1, Q, h->p.flow, h->stream)
-                : lbmk::launch_convert<lbmk::MODE_BF16>(P, D, to_state ? 0 : 1, Q, h->p.flow, h->stream);
+        const int td = to_state ? 0 : 1;
+        if (h->p.precision == LBM_F64) {
+            lbmk::DenseState<double> D{static_cast<double*>(Df), static_cast<double*>(Dg), static_cast<double*>(Dh),
+                                       nullptr};
+            e = launch_convert_mode<lbmk::MODE_F64>(h, D, td);
+        } else {
+            lbmk::DenseState<float> D{static_cast<float*>(Df), static_cast<float*>(Dg), static_cast<float*>(Dh),
+                                      static_cast<float*>(Dl)};
+            if (h->p.precision == LBM_F32) e = launch_convert_mode<lbmk::MODE_F32>(h, D, td);
+            else if (h->p.precision == LBM_F16) e = launch_convert_mode<lbmk::MODE_F16>(h, D, td);
+            else e = launch_convert_mode<lbmk::MODE_BF16>(h, D, td);
+        }
     }
     if (!to_state && e == cudaSuccess) {
-        if (D.f) e = cudaMemcpyAsync(f, D.f, 9 * n * sizeof(float), out, h->stream);
-        if (e == cudaSuccess && D.g) e = cudaMemcpyAsync(g, D.g, Q * n * sizeof(float), out, h->stream);
-        if (e == cudaSuccess && D.h) e = cudaMemcpyAsync(hm, D.h, Q * n * sizeof(float), out, h->stream);
+        if (Df) e = cudaMemcpyAsync(f, Df, 9 * n * el, out, h->stream);
+        if (e == cudaSuccess && Dg) e = cudaMemcpyAsync(g, Dg, Q * n * el, out, h->stream);
+        if (e == cudaSuccess && Dh) e = cudaMemcpyAsync(hm, Dh, Q * n * el, out, h->stream);
+        if (e == cudaSuccess && Dl) e = cudaMemcpyAsync(lo, Dl, n * el, out, h->stream);
     }
     if (cudaStreamSynchronize(h->stream) != cudaSuccess) e = cudaErrorUnknown;
     dev_free(h, stage);
@@ -682,20 +692,9 @@ static int convert_state_io(lbm_handle* h, void* f, void* g, void* hm, int to_st
 int lbm_get_state(lbm_handle* h, void* f, void* g, void* hm, void* dT, void* g0_lo, int32_t on_device) {
     if (!h) return LBM_ERR_ARG;
     if (h->sticky == LBM_ERR_CUDA) return LBM_ERR_STATE;
-    const int Q = h->p.thermal_q, base = h->p.flow ? 9 : 0;
-    void* cur = h->buf[h->cur];
-    const size_t el = h->L.elem, rel = h->L.relem;
     int rc = LBM_OK;
-    if (split_mode(h->p.precision)) {
-        rc = convert_state_io(h, f, g, hm, 0, on_device);
-    } else {
-        if (h->p.flow) rc = copy_planes(h, f, 0, 9, false, on_device, cur, el);
-        if (rc == LBM_OK) rc = copy_planes(h, g, base, Q, false, on_device, cur, el);
-        if (rc == LBM_OK) rc = copy_planes(h, hm, base + Q, Q, false, on_device, cur, el);
-        if (rc == LBM_OK && h->p.precision == LBM_F32)
-            rc = copy_planes(h, g0_lo, base + 2 * Q, 1, false, on_device, cur, el);
-    }
-    if (rc == LBM_OK) rc = copy_planes(h, dT, 0, 1, false, on_device, h->dT, rel);
+    if (f || g || hm || g0_lo) rc = convert_state_io(h, f, g, hm, g0_lo, 0, on_device);
+    if (rc == LBM_OK) rc = copy_history(h, dT, false, on_device);
     if (rc != LBM_OK) return rc;
     return sync_and_check(h);
 }
@@ -704,24 +703,11 @@ int lbm_set_state(lbm_handle* h, const void* f, const void* g, const void* hm, c
                   int32_t on_device) {
     if (!h) return LBM_ERR_ARG;
     if (h->sticky == LBM_ERR_CUDA) return LBM_ERR_STATE;
-    const int Q = h->p.thermal_q, base = h->p.flow ? 9 : 0;
-    void* cur = h->buf[h->cur];
-    const size_t el = h->L.elem, rel = h->L.relem;
     int rc = LBM_OK;
-    if (split_mode(h->p.precision)) {
-        rc = convert_state_io(h, const_cast<void*>(f), const_cast<void*>(g), const_cast<void*>(hm), 1, on_device);
-    } else {
-        if (h->p.flow) rc = copy_planes(h, const_cast<void*>(f), 0, 9, true, on_device, cur, el);
-        if (rc == LBM_OK) rc = copy_planes(h, const_cast<void*>(g), base, Q, true, on_device, cur, el);
-        if (rc == LBM_OK) rc = copy_planes(h, const_cast<void*>(hm), base + Q, Q, true, on_device, cur, el);
-        if (rc == LBM_OK && h->p.precision == LBM_F32) {
-            char* lo = static_cast<char*>(cur) + (size_t)(base + 2 * Q) * h->L.plane * el;
-            if (g0_lo) rc = copy_planes(h, const_cast<void*>(g0_lo), base + 2 * Q, 1, true, on_device, cur, el);
-            else if (g && cudaMemsetAsync(lo, 0, (size_t)h->L.plane * el, h->stream) != cudaSuccess)
-                rc = cuda_fail(h);
-        }
-    }
-    if (rc == LBM_OK) rc = copy_planes(h, const_cast<void*>(dT), 0, 1, true, on_device, h->dT, rel);
+    if (f || g || hm || g0_lo)
+        rc = convert_state_io(h, const_cast<void*>(f), const_cast<void*>(g), const_cast<void*>(hm),
+                              const_cast<void*>(g0_lo), 1, on_device);
+    if (rc == LBM_OK) rc = copy_history(h, const_cast<void*>(dT), true, on_device);
     if (rc != LBM_OK) return rc;
     if (cudaStreamSynchronize(h->stream) != cudaSuccess) return cuda_fail(h);
     return h->sticky;
@@ -740,7 +726,7 @@ CkptHeader header_of(const lbm_handle* h) {
     CkptHeader c;
     std::memset(&c, 0, sizeof c);
     std::memcpy(c.magic, kMagic, 8);
-    c.version = 1;
+    c.version = 2;   // 2: chunked state layout
     c.precision = h->p.precision;
     c.thermal_q = h->p.thermal_q;
     c.flow = h->p.flow;
@@ -786,7 +772,7 @@ int lbm_load(lbm_handle* h, const void* src, int32_t on_device) {
         std::memcpy(&c, src, sizeof c);
     }
     const CkptHeader want = header_of(h);
-    if (std::memcmp(c.magic, kMagic, 8) != 0 || c.version != 1 || c.precision != want.precision ||
+    if (std::memcmp(c.magic, kMagic, 8) != 0 || c.version != 2 || c.precision != want.precision ||
         c.thermal_q != want.thermal_q || c.flow != want.flow || c.nx != want.nx || c.ny != want.ny ||
         c.pitch != want.pitch || c.nplanes != want.nplanes || c.copy_bytes != want.copy_bytes ||
         c.dT_bytes != want.dT_bytes || c.steps < 0)

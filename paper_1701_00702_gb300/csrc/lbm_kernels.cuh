@@ -35,6 +35,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 namespace lbmk {
 
 // Storage modes.  Arithmetic is FP64 for MODE_F64 and FP32 otherwise.
@@ -82,21 +84,35 @@ struct Planes {
     __host__ __device__ static constexpr int met(int q) { return kSplit<M> ? fb + (QT - 1) + q - 1 : fb + QT + q; }
     static constexpr int lo = fb + 2 * QT;                                                  // MODE_F32 only
     static constexpr int bulk = kSplit<M> ? fb + 2 * (QT - 1) : fb + 2 * QT + (kComp<M> ? 1 : 0);
+    static constexpr int wide = kSplit<M> ? 2 : 0;
 };
 
-// Planes per state copy at most: 9 flow + 2 x 9 thermal + 1 low part, + 2 wide.
-constexpr int kMaxPlanes = 30;
+// State layout: each row is cut into chunks of kChunk nodes along x, and a
+// chunk holds every plane of its nodes, [chunk][plane][kChunk]: the bulk
+// planes (the mode's storage type), then the wide planes (FP32).  A node's
+// element in plane q lies kChunk * q elements after its element in plane 0,
+// so one pointer per pulled neighbour reaches all of that neighbour's planes
+// through constant offsets.  Chunk y * cpr + x / kChunk holds node (x, y).
+constexpr int kChunk = 128;
+constexpr int kChunkShift = 7;
 
-// Per-run constants, passed by value (__grid_constant__).  A node's element
-// in every plane is at the same 32-bit offset y * pitch + x.
+template <int M, int QT, bool FLOW>
+struct Chunk {
+    using B = typename ModeTraits<M>::B;
+    using PL = Planes<M, QT, FLOW>;
+    static constexpr int wide_off = PL::bulk * kChunk * (int)sizeof(B);        // bytes to wide plane 0
+    static constexpr int bytes = wide_off + PL::wide * kChunk * (int)sizeof(float);
+};
+
+// Per-run constants, passed by value (__grid_constant__).
 template <typename R>
 struct StepParams {
-    const void* src[kMaxPlanes];   // plane base pointers of the current copy (bulk, then wide)
-    void* dst[kMaxPlanes];         // plane base pointers of the next copy
+    const char* src;     // current state copy, [chunk][plane][kChunk]
+    char* dst;           // next state copy
     R* dT;               // [ny][pitch] exchange history T_m - T_f of the previous step
     unsigned int* status;
-    int nx, ny, pitch;
-    long long plane;     // ny * pitch
+    int nx, ny, pitch;   // pitch = cpr * kChunk
+    int cpr;             // chunks per row
     int per_x, per_y;
     int solid_scheme;    // 0: volumetric blend; 1: bounce-back where f_l <= 0.5 (Sec. V B)
     int wall_kind[4];
@@ -335,15 +351,36 @@ struct NodeState {
 };
 
 template <int M>
-__device__ __forceinline__ typename ModeTraits<M>::R ldb(const void* plane, int i) {
-    using B = typename ModeTraits<M>::B;
-    return to_f(__ldg(static_cast<const B*>(plane) + i));
+__device__ __forceinline__ typename ModeTraits<M>::R ldb(const typename ModeTraits<M>::B* p) {
+    return to_f(__ldg(p));
 }
 
 template <int M, typename R>
-__device__ __forceinline__ void stb(void* plane, int i, R v) {
+__device__ __forceinline__ void stb(typename ModeTraits<M>::B* p, R v) {
     using B = typename ModeTraits<M>::B;
-    static_cast<B*>(plane)[i] = from_f<B>(v);
+    *p = from_f<B>(v);
+}
+
+// Byte offset, within a state copy, of the chunk holding node (x, y).
+template <int M, int QT, bool FLOW, typename R>
+__device__ __forceinline__ long long chunk_at(const StepParams<R>& P, int x, int y) {
+    return (long long)(y * P.cpr + (x >> kChunkShift)) * Chunk<M, QT, FLOW>::bytes;
+}
+
+// Node (x, y)'s element in bulk plane 0 and in wide plane 0 of a copy; plane q
+// follows at q * kChunk elements.
+template <int M, int QT, bool FLOW, typename R, typename C>
+__device__ __forceinline__ auto bulk_at(C* base, const StepParams<R>& P, int x, int y) {
+    using B = typename ModeTraits<M>::B;
+    using T = std::conditional_t<std::is_const_v<C>, const B, B>;
+    return reinterpret_cast<T*>(base + chunk_at<M, QT, FLOW>(P, x, y)) + (x & (kChunk - 1));
+}
+
+template <int M, int QT, bool FLOW, typename R, typename C>
+__device__ __forceinline__ auto wide_at(C* base, const StepParams<R>& P, int x, int y) {
+    using T = std::conditional_t<std::is_const_v<C>, const float, float>;
+    return reinterpret_cast<T*>(base + chunk_at<M, QT, FLOW>(P, x, y) + Chunk<M, QT, FLOW>::wide_off) +
+           (x & (kChunk - 1));
 }
 
 // Pull streaming around node (xs, ys): the population along e_i comes from
@@ -353,41 +390,46 @@ template <int M, int QT, bool FLOW>
 __device__ __forceinline__ void pull_moments(const StepParams<typename ModeTraits<M>::R>& P, int xs, int ys,
                                              NodeState<M, QT, FLOW>& n) {
     using R = typename ModeTraits<M>::R;
+    using B = typename ModeTraits<M>::B;
     using PL = Planes<M, QT, FLOW>;
+    constexpr int ND = FLOW ? 9 : QT;   // directions pulled
     const int xm = xs == 0 ? P.nx - 1 : xs - 1;
     const int xp = xs == P.nx - 1 ? 0 : xs + 1;
     const int ym = ys == 0 ? P.ny - 1 : ys - 1;
     const int yp = ys == P.ny - 1 ? 0 : ys + 1;
-    const int r0 = ys * P.pitch, rm = ym * P.pitch, rp = yp * P.pitch;
-    // source offset of the population along e_q (D2Q9 order of Eq. 11)
-    const int off[9] = {r0 + xs, r0 + xm, rm + xs, r0 + xp, rp + xs, rm + xm, rm + xp, rp + xp, rp + xm};
+    const int xc[3] = {xm, xs, xp}, yr[3] = {ym, ys, yp};
+    // source column and row (x - e_x, y - e_y) of direction q, D2Q9 order of Eq. 11
+    constexpr int ci[9] = {1, 0, 1, 2, 1, 0, 2, 2, 0};
+    constexpr int ri[9] = {1, 1, 0, 1, 2, 0, 0, 2, 2};
+    const B* sb[ND];   // the source node's element in bulk plane 0
+#pragma unroll
+    for (int q = 0; q < ND; ++q) sb[q] = bulk_at<M, QT, FLOW>(P.src, P, xc[ci[q]], yr[ri[q]]);
     if constexpr (FLOW) {
         R f[9];
 #pragma unroll
         for (int q = 0; q < 9; ++q) {
-            f[q] = ldb<M>(P.src[q], off[q]);
+            f[q] = ldb<M>(sb[q] + q * kChunk);
             if constexpr (M == MODE_F16) f[q] *= R(1.0 / 1024.0);
         }
         m_from_f9(f, n.mp);
     }
     R g[QT], h[QT];
     if constexpr (kSplit<M>) {
-        const float* G0 = static_cast<const float*>(P.src[PL::bulk]);
-        const float* M0 = static_cast<const float*>(P.src[PL::bulk + 1]);
-        g[0] = __ldg(G0 + off[0]);
-        h[0] = __ldg(M0 + off[0]);
+        const float* sw[QT];   // the source node's element in wide plane 0 (PCM rest; metal rest follows)
+#pragma unroll
+        for (int q = 0; q < QT; ++q) sw[q] = wide_at<M, QT, FLOW>(P.src, P, xc[ci[q]], yr[ri[q]]);
+        g[0] = __ldg(sw[0]);
+        h[0] = __ldg(sw[0] + kChunk);
 #pragma unroll
         for (int q = 1; q < QT; ++q) {   // deviation + reference of the sending node
-            g[q] = ldb<M>(P.src[PL::pcm(q)], off[q]) + P.w_move[q] * pcm_ref(P, __ldg(G0 + off[q]));
-            h[q] = ldb<M>(P.src[PL::met(q)], off[q]) + P.w_move[q] * P.kappa_m * __ldg(M0 + off[q]);
+            g[q] = ldb<M>(sb[q] + PL::pcm(q) * kChunk) + P.w_move[q] * pcm_ref(P, __ldg(sw[q]));
+            h[q] = ldb<M>(sb[q] + PL::met(q) * kChunk) + P.w_move[q] * P.kappa_m * __ldg(sw[q] + kChunk);
         }
     } else {
-        g[0] = ldb<M>(P.src[PL::pcm(0)], off[0]);
-        h[0] = ldb<M>(P.src[PL::met(0)], off[0]);
 #pragma unroll
-        for (int q = 1; q < QT; ++q) {
-            g[q] = ldb<M>(P.src[PL::pcm(q)], off[q]);
-            h[q] = ldb<M>(P.src[PL::met(q)], off[q]);
+        for (int q = 0; q < QT; ++q) {
+            g[q] = ldb<M>(sb[q] + PL::pcm(q) * kChunk);
+            h[q] = ldb<M>(sb[q] + PL::met(q) * kChunk);
         }
     }
     fwd<R, QT>(g, n.ng);
@@ -396,7 +438,7 @@ __device__ __forceinline__ void pull_moments(const StepParams<typename ModeTrait
     n.Elo = R(0);
     if constexpr (kComp<M>) {
         // H = (g_0 hi + g_0 lo) + sum of movers, without rounding loss
-        const float lo = ldb<M>(P.src[PL::lo], off[0]);
+        const float lo = ldb<M>(sb[0] + PL::lo * kChunk);
         const FF H = ff_add(FF{g[0], lo}, ff_sum_movers<QT>(g));
         n.ng[0] = H.hi;
         n.Hlo = H.lo;
@@ -510,11 +552,15 @@ __device__ __forceinline__ void node_state(const StepParams<typename ModeTraits<
 // stored populations carry exactly the enthalpy (internal energy) that the
 // collision produced: to float-float accuracy with FP32 storage, to one FP32
 // rounding with 16-bit movers, to FP64 rounding with FP64 storage.
+// db and dw point at the node's element in bulk plane 0 and wide plane 0 of the
+// next copy; rest_plane is a wide plane in the 16-bit modes, a bulk plane
+// otherwise.
 template <int M, int QT>
 __device__ __forceinline__ void store_thermal(const StepParams<typename ModeTraits<M>::R>& P,
                                               typename ModeTraits<M>::R* nm, typename ModeTraits<M>::R n0hi,
-                                              typename ModeTraits<M>::R n0lo, int o, int rest_plane,
-                                              int mover_plane1, int lo_plane, bool remainder, bool is_pcm) {
+                                              typename ModeTraits<M>::R n0lo, typename ModeTraits<M>::B* db,
+                                              float* dw, int rest_plane, int mover_plane1, int lo_plane,
+                                              bool remainder, bool is_pcm) {
     using R = typename ModeTraits<M>::R;
     R v[QT];
     nm[0] = n0hi;
@@ -537,24 +583,24 @@ __device__ __forceinline__ void store_thermal(const StepParams<typename ModeTrai
         for (int k = 1; k < QT; ++k) {
             const float r = P.w_move[k] * ref;
             const B b = from_f<B>(v[k] - r);
-            static_cast<B*>(P.dst[mover_plane1 + k - 1])[o] = b;
+            db[(mover_plane1 + k - 1) * kChunk] = b;
             st += to_f(b) + r;
         }
-        static_cast<float*>(P.dst[rest_plane])[o] = n0hi - st;
+        dw[rest_plane * kChunk] = n0hi - st;
     } else {
 #pragma unroll
-        for (int k = 1; k < QT; ++k) stb<M>(P.dst[mover_plane1 + k - 1], o, v[k]);
+        for (int k = 1; k < QT; ++k) stb<M>(db + (mover_plane1 + k - 1) * kChunk, v[k]);
         if (!remainder) {
-            stb<M>(P.dst[rest_plane], o, v[0]);
+            stb<M>(db + rest_plane * kChunk, v[0]);
         } else if constexpr (kComp<M>) {
             const FF r = ff_add(FF{n0hi, n0lo}, ff_neg(ff_sum_movers<QT>(v)));
-            stb<M>(P.dst[rest_plane], o, r.hi);
-            stb<M>(P.dst[lo_plane], o, r.lo);
+            stb<M>(db + rest_plane * kChunk, r.hi);
+            stb<M>(db + lo_plane * kChunk, r.lo);
         } else {
             R sm = v[1];
 #pragma unroll
             for (int k = 2; k < QT; ++k) sm += v[k];
-            stb<M>(P.dst[rest_plane], o, n0hi - sm);
+            stb<M>(db + rest_plane * kChunk, n0hi - sm);
         }
     }
 }
@@ -576,7 +622,10 @@ __device__ __forceinline__ void step_node(const StepParams<typename ModeTraits<M
     bool wall;
     node_state<M, QT, FLOW>(P, x, y, n, wall);
 
-    const int o = y * P.pitch + x;
+    const int o = y * P.pitch + x;                                  // exchange history
+    typename ModeTraits<M>::B* db = bulk_at<M, QT, FLOW>(P.dst, P, x, y);   // this node in the next copy
+    float* dw = nullptr;
+    if constexpr (kSplit<M>) dw = wide_at<M, QT, FLOW>(P.dst, P, x, y);
 
     if constexpr (FLOW) {
       if (P.solid_scheme && n.fl <= R(0.5)) {
@@ -588,7 +637,7 @@ __device__ __forceinline__ void step_node(const StepParams<typename ModeTraits<M
 #pragma unroll
         for (int k = 0; k < 9; ++k) {
             if constexpr (M == MODE_F16) f[k] *= R(1024.0);
-            stb<M>(P.dst[k], o, f[k]);
+            stb<M>(db + k * kChunk, f[k]);
         }
       } else {
         // Eq. 3 at the node's velocity (u = u_b = 0 on walls)
@@ -620,7 +669,7 @@ __device__ __forceinline__ void step_node(const StepParams<typename ModeTraits<M
 #pragma unroll
         for (int k = 0; k < 9; ++k) {
             if constexpr (M == MODE_F16) f[k] *= R(1024.0);
-            stb<M>(P.dst[k], o, f[k]);
+            stb<M>(db + k * kChunk, f[k]);
         }
       }
     }
@@ -659,7 +708,7 @@ __device__ __forceinline__ void step_node(const StepParams<typename ModeTraits<M
             hi = n.ng[0] + S_pcm;
             lo = R(0);
         }
-        store_thermal<M, QT>(P, n.ng, hi, lo, o, kSplit<M> ? PL::bulk : PL::pcm(0), PL::pcm(1), PL::lo, true, true);
+        store_thermal<M, QT>(P, n.ng, hi, lo, db, dw, kSplit<M> ? 0 : PL::pcm(0), PL::pcm(1), PL::lo, true, true);
     }
     {
         R ne[QT];
@@ -674,7 +723,7 @@ __device__ __forceinline__ void step_node(const StepParams<typename ModeTraits<M
         R hi;
         if constexpr (kSplit<M>) hi = n.nh[0] + S_met;
         else hi = n.nh[0] - P.eta[0] * (n.nh[0] - ne[0]) + S_met;
-        store_thermal<M, QT>(P, n.nh, hi, R(0), o, kSplit<M> ? PL::bulk + 1 : PL::met(0), PL::met(1), PL::lo,
+        store_thermal<M, QT>(P, n.nh, hi, R(0), db, dw, kSplit<M> ? 1 : PL::met(0), PL::met(1), PL::lo,
                              kSplit<M>, false);
     }
     P.dT[o] = dTn;

@@ -4,4 +4,5 @@
 
 namespace lbmk {
 LBMK_INSTANTIATE(MODE_F32)
+LBMK_INSTANTIATE_CONVERT(MODE_F32)
 }  // namespace lbmk

@@ -4,6 +4,7 @@
 
 namespace lbmk {
 LBMK_INSTANTIATE(MODE_F64)
+LBMK_INSTANTIATE_CONVERT(MODE_F64)
 
 // Fixed-order sum of the per-block partials: thread t adds blocks t, t+256, ...
 // then a shared-memory tree combines the 256 thread sums; out[0..3] =

@@ -33,76 +33,99 @@ __global__ void init_kernel(const __grid_constant__ StepParams<typename ModeTrai
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     if (x >= P.nx || y >= P.ny) return;
-    const int o = y * P.pitch + x;
+    auto* db = bulk_at<M, QT, FLOW>(const_cast<char*>(P.src), P, x, y);
     if constexpr (FLOW)
-        for (int q = 0; q < 9; ++q) stb<M>(const_cast<void*>(P.src[q]), o, (R)(V.f[q] * (double)P.fscale));
+        for (int q = 0; q < 9; ++q) stb<M>(db + q * kChunk, (R)(V.f[q] * (double)P.fscale));
     if constexpr (kSplit<M>) {
+        float* dw = wide_at<M, QT, FLOW>(const_cast<char*>(P.src), P, x, y);
         const float g0 = (float)V.g[0], h0 = (float)V.h[0];
-        static_cast<float*>(const_cast<void*>(P.src[PL::bulk]))[o] = g0;
-        static_cast<float*>(const_cast<void*>(P.src[PL::bulk + 1]))[o] = h0;
+        dw[0] = g0;
+        dw[kChunk] = h0;
         for (int q = 1; q < QT; ++q) {
-            stb<M>(const_cast<void*>(P.src[PL::pcm(q)]), o, (float)V.g[q] - P.w_move[q] * pcm_ref(P, g0));
-            stb<M>(const_cast<void*>(P.src[PL::met(q)]), o, (float)V.h[q] - P.w_move[q] * P.kappa_m * h0);
+            stb<M>(db + PL::pcm(q) * kChunk, (float)V.g[q] - P.w_move[q] * pcm_ref(P, g0));
+            stb<M>(db + PL::met(q) * kChunk, (float)V.h[q] - P.w_move[q] * P.kappa_m * h0);
         }
     } else {
-        for (int q = 1; q < QT; ++q) {
-            stb<M>(const_cast<void*>(P.src[PL::pcm(q)]), o, (R)V.g[q]);
-            stb<M>(const_cast<void*>(P.src[PL::met(q)]), o, (R)V.h[q]);
+        for (int q = 0; q < QT; ++q) {
+            stb<M>(db + PL::pcm(q) * kChunk, (R)V.g[q]);
+            stb<M>(db + PL::met(q) * kChunk, (R)V.h[q]);
         }
-        stb<M>(const_cast<void*>(P.src[PL::pcm(0)]), o, (R)V.g[0]);
-        stb<M>(const_cast<void*>(P.src[PL::met(0)]), o, (R)V.h[0]);
-        if constexpr (kComp<M>) stb<M>(const_cast<void*>(P.src[PL::lo]), o, (R)V.g0_lo);
+        if constexpr (kComp<M>) stb<M>(db + PL::lo * kChunk, (R)V.g0_lo);
     }
-    P.dT[o] = R(0);
+    P.dT[y * P.pitch + x] = R(0);
 }
 
-// Dense float/double copy of the state, [q][ny][nx] per lattice, for the
-// 16-bit modes (state I/O converts through it).  to_dense = 1 reads the
-// current copy into dense arrays, 0 writes dense arrays into the copy.
+// Dense copy of the state, [q][ny][nx] per lattice in the run's arithmetic
+// type (state I/O converts through it).  to_dense = 1 reads the current copy
+// into the dense arrays, 0 writes the dense arrays into the copy; a null
+// array is skipped.  The 16-bit modes decode (encode) the moving thermal
+// populations with the reference of their node; FP32 carries the low part
+// of the PCM rest population in lo (taken as zero on writing when lo is null
+// and g is given).
+template <typename R>
 struct DenseState {
-    float* f;    // 9 planes (deviations f_i - w_i), may be null
-    float* g;    // Q planes
-    float* h;    // Q planes
+    R* f;      // 9 planes (deviations f_i - w_i)
+    R* g;      // Q planes
+    R* h;      // Q planes
+    R* lo;     // FP32 only: low part of g_0
 };
 
 template <int M, int QT, bool FLOW>
-__global__ void convert_state(const __grid_constant__ StepParams<float> P, const __grid_constant__ DenseState D,
-                              int to_dense) {
-    using PL = Planes<M, QT, FLOW>;
+__global__ void convert_state(const __grid_constant__ StepParams<typename ModeTraits<M>::R> P,
+                              const __grid_constant__ DenseState<typename ModeTraits<M>::R> D, int to_dense) {
+    using R = typename ModeTraits<M>::R;
     using B = typename ModeTraits<M>::B;
+    using PL = Planes<M, QT, FLOW>;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     if (x >= P.nx || y >= P.ny) return;
-    const int o = y * P.pitch + x;
     const long long k = (long long)y * P.nx + x, dpl = (long long)P.nx * P.ny;
-    auto bulk = [&](int plane) { return static_cast<B*>(const_cast<void*>(P.src[plane])); };
-    float* wg = static_cast<float*>(const_cast<void*>(P.src[PL::bulk]));
-    float* wh = static_cast<float*>(const_cast<void*>(P.src[PL::bulk + 1]));
+    B* db = bulk_at<M, QT, FLOW>(const_cast<char*>(P.src), P, x, y);
     if (to_dense) {
         if (FLOW && D.f)
-            for (int q = 0; q < 9; ++q) D.f[q * dpl + k] = to_f(bulk(q)[o]) * P.finv;
-        if (D.g) {
-            const float rg = pcm_ref(P, wg[o]);
-            D.g[k] = wg[o];
-            for (int q = 1; q < QT; ++q) D.g[q * dpl + k] = to_f(bulk(PL::pcm(q))[o]) + P.w_move[q] * rg;
-        }
-        if (D.h) {
-            const float rm = P.kappa_m * wh[o];
-            D.h[k] = wh[o];
-            for (int q = 1; q < QT; ++q) D.h[q * dpl + k] = to_f(bulk(PL::met(q))[o]) + P.w_move[q] * rm;
+            for (int q = 0; q < 9; ++q) D.f[q * dpl + k] = to_f(db[q * kChunk]) * P.finv;
+        if constexpr (kSplit<M>) {
+            const float* dw = wide_at<M, QT, FLOW>(P.src, P, x, y);
+            if (D.g) {
+                const float rg = pcm_ref(P, dw[0]);
+                D.g[k] = dw[0];
+                for (int q = 1; q < QT; ++q) D.g[q * dpl + k] = to_f(db[PL::pcm(q) * kChunk]) + P.w_move[q] * rg;
+            }
+            if (D.h) {
+                const float rm = P.kappa_m * dw[kChunk];
+                D.h[k] = dw[kChunk];
+                for (int q = 1; q < QT; ++q) D.h[q * dpl + k] = to_f(db[PL::met(q) * kChunk]) + P.w_move[q] * rm;
+            }
+        } else {
+            if (D.g)
+                for (int q = 0; q < QT; ++q) D.g[q * dpl + k] = to_f(db[PL::pcm(q) * kChunk]);
+            if (D.h)
+                for (int q = 0; q < QT; ++q) D.h[q * dpl + k] = to_f(db[PL::met(q) * kChunk]);
+            if constexpr (kComp<M>)
+                if (D.lo) D.lo[k] = db[PL::lo * kChunk];
         }
     } else {
         if (FLOW && D.f)
-            for (int q = 0; q < 9; ++q) bulk(q)[o] = from_f<B>(D.f[q * dpl + k] * P.fscale);
-        if (D.g) {
-            const float rg = pcm_ref(P, D.g[k]);
-            wg[o] = D.g[k];
-            for (int q = 1; q < QT; ++q) bulk(PL::pcm(q))[o] = from_f<B>(D.g[q * dpl + k] - P.w_move[q] * rg);
-        }
-        if (D.h) {
-            const float rm = P.kappa_m * D.h[k];
-            wh[o] = D.h[k];
-            for (int q = 1; q < QT; ++q) bulk(PL::met(q))[o] = from_f<B>(D.h[q * dpl + k] - P.w_move[q] * rm);
+            for (int q = 0; q < 9; ++q) db[q * kChunk] = from_f<B>(D.f[q * dpl + k] * P.fscale);
+        if constexpr (kSplit<M>) {
+            float* dw = wide_at<M, QT, FLOW>(const_cast<char*>(P.src), P, x, y);
+            if (D.g) {
+                const float rg = pcm_ref(P, D.g[k]);
+                dw[0] = D.g[k];
+                for (int q = 1; q < QT; ++q) db[PL::pcm(q) * kChunk] = from_f<B>(D.g[q * dpl + k] - P.w_move[q] * rg);
+            }
+            if (D.h) {
+                const float rm = P.kappa_m * D.h[k];
+                dw[kChunk] = D.h[k];
+                for (int q = 1; q < QT; ++q) db[PL::met(q) * kChunk] = from_f<B>(D.h[q * dpl + k] - P.w_move[q] * rm);
+            }
+        } else {
+            if (D.g)
+                for (int q = 0; q < QT; ++q) db[PL::pcm(q) * kChunk] = from_f<B>(D.g[q * dpl + k]);
+            if (D.h)
+                for (int q = 0; q < QT; ++q) db[PL::met(q) * kChunk] = from_f<B>(D.h[q * dpl + k]);
+            if constexpr (kComp<M>)
+                if (D.lo || D.g) db[PL::lo * kChunk] = D.lo ? D.lo[k] : R(0);
         }
     }
 }
@@ -164,7 +187,8 @@ cudaError_t launch_init(const StepParams<typename ModeTraits<M>::R>& P, const In
 }
 
 template <int M>
-cudaError_t launch_convert(const StepParams<float>& P, const DenseState& D, int to_dense, int qt, int flow,
+cudaError_t launch_convert(const StepParams<typename ModeTraits<M>::R>& P,
+                           const DenseState<typename ModeTraits<M>::R>& D, int to_dense, int qt, int flow,
                            cudaStream_t s) {
     const dim3 g = grid_for(P.nx, P.ny), b(kBlockX, kBlockY);
     return dispatch<M>(qt, flow, [&]<int MM, int Q, bool F>() {
@@ -216,7 +240,8 @@ int batch_blocks_per_sm(int qt, int flow, int ph) {
     template int batch_blocks_per_sm<M>(int, int, int);                                                   \
     template const void* step_kernel<M>(int, int, int);
 
-#define LBMK_INSTANTIATE_CONVERT(M) \
-    template cudaError_t launch_convert<M>(const StepParams<float>&, const DenseState&, int, int, int, cudaStream_t);
+#define LBMK_INSTANTIATE_CONVERT(M)                                                                           \
+    template cudaError_t launch_convert<M>(const StepParams<ModeTraits<M>::R>&, const DenseState<ModeTraits<M>::R>&, \
+                                           int, int, int, cudaStream_t);
 
 }  // namespace lbmk
