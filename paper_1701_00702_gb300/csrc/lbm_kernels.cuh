@@ -62,6 +62,9 @@ template <> struct ModeTraits<MODE_F16> { using R = float; using B = __half; };
 template <> struct ModeTraits<MODE_BF16> { using R = float; using B = __nv_bfloat16; };
 
 template <int M> constexpr bool kSplit = (M == MODE_F16 || M == MODE_BF16);
+// FP16 stores the flow deviations times 2^10 (|f_i - w_i| < 1 while |u| < 0.3
+// keeps them in the normal range); the other modes store them as they are.
+template <int M> constexpr int kFlowScale = (M == MODE_F16) ? 1024 : 1;
 template <int M> constexpr bool kComp = (M == MODE_F32);
 
 __device__ __forceinline__ float to_f(__half v) { return __half2float(v); }
@@ -161,20 +164,21 @@ __device__ __forceinline__ FF ff_add(FF a, float b) {
     return fast_two_sum(s.hi, __fadd_rn(s.lo, a.lo));
 }
 
-__device__ __forceinline__ FF ff_add(FF a, FF b) {
-    const FF s = two_sum(a.hi, b.hi);
-    return fast_two_sum(s.hi, __fadd_rn(__fadd_rn(s.lo, a.lo), b.lo));
-}
 
-__device__ __forceinline__ FF ff_neg(FF a) { return {-a.hi, -a.lo}; }
-
-// Sum of the moving populations v[1..Q-1] as a float-float pair.
+// a.hi + a.lo + sign * (v[1] + ... + v[Q-1]) as a float-float pair: each term
+// enters through TwoSum, the rounding errors gather in one float, and the pair
+// is normalised once at the end (a compensated sum; its error is of the order
+// of (Q - 1) u^2 |sum|, u = 2^-24).
 template <int Q>
-__device__ __forceinline__ FF ff_sum_movers(const float* v) {
-    FF acc = {v[1], 0.0f};
+__device__ __forceinline__ FF ff_accumulate(FF a, const float* v, float sign) {
+    float s = a.hi, c = a.lo;
 #pragma unroll
-    for (int i = 2; i < Q; ++i) acc = ff_add(acc, v[i]);
-    return acc;
+    for (int i = 1; i < Q; ++i) {
+        const FF t = two_sum(s, sign * v[i]);
+        s = t.hi;
+        c = __fadd_rn(c, t.lo);
+    }
+    return fast_two_sum(s, c);
 }
 
 // ---------------------------------------------------------------------------
@@ -199,12 +203,15 @@ __device__ __forceinline__ void m_from_f9(const R* f, R* m) {
     m[8] = f[5] - f[6] + f[7] - f[8];
 }
 
-template <typename R>
+// f = M^-1 m, every f scaled by SC (a power of two: the 16-bit flow storage
+// scale, folded into the row norms).
+template <typename R, int SC = 1>
 __device__ __forceinline__ void f_from_m9(const R* m, R* f) {
-    const R A = m[0] * R(1.0 / 9.0), B = m[1] * R(1.0 / 36.0), C = m[2] * R(1.0 / 36.0);
-    const R DX = m[3] * R(1.0 / 6.0), QX = m[4] * R(1.0 / 12.0);
-    const R DY = m[5] * R(1.0 / 6.0), QY = m[6] * R(1.0 / 12.0);
-    const R P = m[7] * R(0.25), S = m[8] * R(0.25);
+    constexpr double s = SC;
+    const R A = m[0] * R(s / 9.0), B = m[1] * R(s / 36.0), C = m[2] * R(s / 36.0);
+    const R DX = m[3] * R(s / 6.0), QX = m[4] * R(s / 12.0);
+    const R DY = m[5] * R(s / 6.0), QY = m[6] * R(s / 12.0);
+    const R P = m[7] * R(s * 0.25), S = m[8] * R(s * 0.25);
     f[0] = A - R(4) * B + R(4) * C;
     const R b1 = A - B - R(2) * C;
     f[1] = b1 + DX - R(2) * QX + P;
@@ -439,7 +446,7 @@ __device__ __forceinline__ void pull_moments(const StepParams<typename ModeTrait
     if constexpr (kComp<M>) {
         // H = (g_0 hi + g_0 lo) + sum of movers, without rounding loss
         const float lo = ldb<M>(sb[0] + PL::lo * kChunk);
-        const FF H = ff_add(FF{g[0], lo}, ff_sum_movers<QT>(g));
+        const FF H = ff_accumulate<QT>(FF{g[0], lo}, g, 1.0f);
         n.ng[0] = H.hi;
         n.Hlo = H.lo;
     }
@@ -593,7 +600,7 @@ __device__ __forceinline__ void store_thermal(const StepParams<typename ModeTrai
         if (!remainder) {
             stb<M>(db + rest_plane * kChunk, v[0]);
         } else if constexpr (kComp<M>) {
-            const FF r = ff_add(FF{n0hi, n0lo}, ff_neg(ff_sum_movers<QT>(v)));
+            const FF r = ff_accumulate<QT>(FF{n0hi, n0lo}, v, -1.0f);
             stb<M>(db + rest_plane * kChunk, r.hi);
             stb<M>(db + lo_plane * kChunk, r.lo);
         } else {
@@ -633,12 +640,9 @@ __device__ __forceinline__ void step_node(const StepParams<typename ModeTraits<M
         // sign of the odd moments (j, q) and keeps the even ones (deviation form too)
         n.mp[3] = -n.mp[3]; n.mp[4] = -n.mp[4]; n.mp[5] = -n.mp[5]; n.mp[6] = -n.mp[6];
         R f[9];
-        f_from_m9(n.mp, f);
+        f_from_m9<R, kFlowScale<M>>(n.mp, f);
 #pragma unroll
-        for (int k = 0; k < 9; ++k) {
-            if constexpr (M == MODE_F16) f[k] *= R(1024.0);
-            stb<M>(db + k * kChunk, f[k]);
-        }
+        for (int k = 0; k < 9; ++k) stb<M>(db + k * kChunk, f[k]);
       } else {
         // Eq. 3 at the node's velocity (u = u_b = 0 on walls)
         const R um = fast_sqrt(n.ux * n.ux + n.uy * n.uy);
@@ -662,15 +666,18 @@ __device__ __forceinline__ void step_node(const StepParams<typename ModeTraits<M
         const R S[9] = {R(0), rho * R(6) * uF * ip, -rho * R(6) * uF * ip, rho * Fx, -rho * Fx,
                         rho * Fy, -rho * Fy, rho * R(2) * (n.ux * Fx - n.uy * Fy) * ip,
                         rho * (n.ux * Fy + n.uy * Fx) * ip};
+        // Eq. 14: the rates of Sec. III C are constants (s_rho = s_j = 1, s_e = s_eps =
+        // 1.1, s_q = 1.2); only s_v = s[7] = s[8] depends on the run
+        constexpr double sk[7] = {1.0, 1.1, 1.1, 1.0, 1.2, 1.0, 1.2};
 #pragma unroll
-        for (int k = 0; k < 9; ++k) m[k] = m[k] - P.s[k] * (m[k] - me[k]) + (R(1) - R(0.5) * P.s[k]) * S[k];
+        for (int k = 0; k < 7; ++k) m[k] = m[k] - R(sk[k]) * (m[k] - me[k]) + R(1.0 - 0.5 * sk[k]) * S[k];
+        const R sv = P.s[7], hv = R(1) - R(0.5) * sv;
+        m[7] = m[7] - sv * (m[7] - me[7]) + hv * S[7];
+        m[8] = m[8] - sv * (m[8] - me[8]) + hv * S[8];
         R f[9];
-        f_from_m9(m, f);
+        f_from_m9<R, kFlowScale<M>>(m, f);
 #pragma unroll
-        for (int k = 0; k < 9; ++k) {
-            if constexpr (M == MODE_F16) f[k] *= R(1024.0);
-            stb<M>(db + k * kChunk, f[k]);
-        }
+        for (int k = 0; k < 9; ++k) stb<M>(db + k * kChunk, f[k]);
       }
     }
 
