@@ -179,7 +179,9 @@ int lbm_create_ex(const lbm_params* p, void* cuda_stream, lbm_alloc_fn alloc,
 /* Enqueues nsteps >= 0 time steps (Sec. III: stream, walls, enthalpy, blend,
  * velocity, three collisions).  Asynchronous: returns the sticky status known
  * on the host (LBM_ERR_UNSTABLE after any synchronising call saw the device
- * flag).  Large nsteps are replayed from a captured CUDA graph. */
+ * flag).  Large nsteps are replayed from a captured CUDA graph.  The step
+ * kernel runs one node per thread in blocks of 64 x 2 threads on grids of up
+ * to 100,000 nodes and 128 x 1 on larger ones. */
 int lbm_step(lbm_handle* h, int64_t nsteps);
 
 /* Macroscopic fields at the current time level.  dst[i] receives field i of
@@ -253,14 +255,15 @@ const char* lbm_strerror(int code);
  * persistent blocks striding over the list.  Map 3 launches lbm_step's own
  * kernel once per run and step, each run a chain of kernel nodes in one
  * graph and the chains independent, so small runs overlap large ones; each
- * run's kernel takes a block shape of 128 x 2, 64 x 4, 32 x 8 or 256 x 1
- * threads.  With autotune = 1 the call times, on freshly created copies of
+ * run's kernel takes one of the block shapes 128 x 2, 64 x 4, 32 x 8, 256 x 1
+ * (256 threads), 128 x 1, 64 x 2, 32 x 4 (128) or 64 x 1, 32 x 2 (64).  With autotune = 1 the call times, on freshly created copies of
  * the runs (the runs themselves do not move, but the copies hold as much
  * device memory again while tuning), map 3 with the block shape chosen per
  * size class (grid width <= 64, <= 128, <= 256, wider; one class at a time,
  * keeping the fastest shape) and every combination of tile-width cap (64,
  * 128, 256) and map 0-2, and keeps the fastest; otherwise it takes width cap
- * 128, map 0, every block 128 x 2.  Under
+ * 128, map 0, and for map 3 lbm_step's own block shapes (64 x 2 up to 100,000
+ * nodes, 128 x 1 above).  Under
  * map 3 a batched step equals lbm_step on each run bit for bit.  Maps 0-2
  * inline the same per-node code into another kernel, where the compiler may
  * fuse a few multiply-adds differently: their states can differ from
@@ -287,9 +290,9 @@ int lbm_batch_step(lbm_batch* b, int64_t nsteps);
 int lbm_batch_configure(lbm_batch* b, int32_t width_cap, int32_t mapping);
 int lbm_batch_info(const lbm_batch* b, int32_t* n_tiles, int32_t* width_cap, int32_t* mapping, int32_t* grid,
                    double* tuned_us_per_step);
-/* Block shape of run `run` under map 3: one of 128 x 2, 64 x 4, 32 x 8,
- * 256 x 1 (LBM_ERR_ARG otherwise).  The shape changes no result.  set
- * synchronises the batch's stream. */
+/* Block shape of run `run` under map 3: one of the shapes listed above
+ * (LBM_ERR_ARG otherwise).  The shape changes no result.  set synchronises
+ * the batch's stream. */
 int lbm_batch_set_block(lbm_batch* b, int32_t run, int32_t block_x, int32_t block_y);
 int lbm_batch_get_block(const lbm_batch* b, int32_t run, int32_t* block_x, int32_t* block_y);
 int lbm_batch_destroy(lbm_batch* b);

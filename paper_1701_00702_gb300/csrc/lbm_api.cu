@@ -850,8 +850,9 @@ struct lbm_batch {
 namespace {
 
 // Block shapes of the single-run kernel under map 3 (threads in x, in y).
-constexpr int kNumShapes = 4;
-constexpr int kShapes[kNumShapes][2] = {{128, 2}, {64, 4}, {32, 8}, {256, 1}};
+constexpr int kNumShapes = 9;
+constexpr int kShapes[kNumShapes][2] = {{128, 2}, {64, 4}, {32, 8}, {256, 1}, {128, 1},
+                                        {64, 2},  {32, 4}, {64, 1},  {32, 2}};
 constexpr int kNumClasses = 4;
 
 // Size class of a run for the shape tuner: by grid width, <= 64, <= 128, <= 256, wider.
@@ -1175,7 +1176,11 @@ int lbm_batch_create(lbm_handle* const* runs, int32_t n_runs, int32_t autotune, 
     b->ctx = runs[0]->ctx;
     b->parity = 0;
     for (int r = 0; r < n_runs; ++r) b->flip.push_back(runs[r]->cur);
-    b->shape.assign(n_runs, 0);
+    // the single-run kernel's own shape rule until tuned (64 x 2 small, 128 x 1 large)
+    for (int r = 0; r < n_runs; ++r) {
+        const dim3 sb = lbmk::step_block(runs[r]->p.nx, runs[r]->p.ny);
+        b->shape.push_back(sb.x == 64 ? 5 : 4);
+    }
     b->params_stride = b->precision == LBM_F64 ? sizeof(lbmk::StepParams<double>) : sizeof(lbmk::StepParams<float>);
     for (lbm_handle* h : b->runs)
         if (cudaStreamSynchronize(h->stream) != cudaSuccess) {
@@ -1228,8 +1233,10 @@ int lbm_batch_create(lbm_handle* const* runs, int32_t n_runs, int32_t autotune, 
                     for (size_t r = 0; r < b->runs.size(); ++r)
                         if (width_class(b->runs[r]) == c) members.push_back((int)r);
                     if (members.empty()) continue;
-                    int chosen = 0;
-                    for (int sh = 1; sh < kNumShapes; ++sh) {
+                    std::vector<int> start;   // the class's shapes before this pass
+                    for (int r : members) start.push_back(b->shape[r]);
+                    int chosen = -1;
+                    for (int sh = 0; sh < kNumShapes; ++sh) {
                         for (int r : members) b->shape[r] = sh;
                         const double us = time_batch(b, 16);
                         if (us < t3) {
@@ -1237,7 +1244,7 @@ int lbm_batch_create(lbm_handle* const* runs, int32_t n_runs, int32_t autotune, 
                             chosen = sh;
                         }
                     }
-                    for (int r : members) b->shape[r] = chosen;
+                    for (size_t i = 0; i < members.size(); ++i) b->shape[members[i]] = chosen >= 0 ? chosen : start[i];
                 }
                 if (t3 < best) {
                     best = t3;

@@ -144,9 +144,17 @@ inline cudaError_t dispatch_step(int qt, int flow, int ph, Fn&& fn) {
     });
 }
 
+// Block shape of the single-run step kernel by grid size (measured on GB300:
+// small grids finish sooner when their nodes spread over more, smaller blocks,
+// 64 x 2 at 256^2; one-row blocks do best from ~100k nodes up).
+inline dim3 step_block(int nx, int ny) {
+    return (long long)nx * ny <= 100000 ? dim3(64, 2) : dim3(128, 1);
+}
+
 template <int M>
 cudaError_t launch_step(const StepParams<typename ModeTraits<M>::R>& P, int qt, int flow, cudaStream_t s) {
-    const dim3 g = grid_for(P.nx, P.ny), b(kBlockX, kBlockY);
+    const dim3 b = step_block(P.nx, P.ny);
+    const dim3 g((unsigned)((P.nx + b.x - 1) / b.x), (unsigned)((P.ny + b.y - 1) / b.y), 1u);
     return dispatch_step<M>(qt, flow, P.phase_k, [&]<int MM, int Q, bool F, bool PH>() {
         fused_step<MM, Q, F, PH><<<g, b, 0, s>>>(P);
         return cudaGetLastError();

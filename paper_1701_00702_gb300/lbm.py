@@ -409,7 +409,7 @@ class Batch:
         return self
 
     def set_block(self, run: int, block_x: int, block_y: int) -> "Batch":
-        """Block shape of one run under map 3 (128x2, 64x4, 32x8 or 256x1)."""
+        """Block shape of one run under map 3 (128x2, 64x4, 32x8, 256x1, 128x1, 64x2, 32x4, 64x1, 32x2)."""
         _check(lib().lbm_batch_set_block(self._b, int(run), int(block_x), int(block_y)), "lbm_batch_set_block")
         return self
 
