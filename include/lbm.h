@@ -106,7 +106,7 @@ typedef struct lbm_params {
     double  cond_ratio;        /* λ = k_m / k_f */
     double  Nu_i;              /* interstitial number H_v = h_v d_p² / k_f */
     double  J;                 /* ν_e / ν_f (paper: 1) */
-    double  F_phi;             /* Forchheimer coefficient (paper: 0.068) */
+    double  F_phi;             /* Forchheimer coefficient (paper: 0.068); < 0: Eq. 4's 1.75/sqrt(150 φ^3) */
     double  sigma_hat;         /* (ρc_p)_m / (ρc_p)_f (paper: 1) */
     double  dp_over_L;         /* pore size d_p / L (paper: 0.0135) */
     double  k_f;               /* PCM conductivity in lattice units (= α_f) */
@@ -144,6 +144,7 @@ typedef struct lbm_derived {
     double H_wall[4];          /* enthalpy of each Dirichlet wall, inverse of Eq. 38 */
     double k_s, c_ps;          /* solid PCM conductivity and specific heat (Eq. 9) */
     double zeta_a_solid;       /* ζ_α of a fully solid node (Eq. A19 with k_s); = zeta_a of liquid when k_s = k_l */
+    double F_phi;              /* the Forchheimer coefficient in use (Eq. 4 when lbm_params.F_phi < 0) */
 } lbm_derived;
 
 typedef struct lbm_handle lbm_handle;

@@ -158,6 +158,8 @@ def lattice_config(p: dict) -> dict:
         eta = [eta_a] * qt + [0.0] * (9 - qt)
         role = [1] * qt + [0] * (9 - qt)
     F_phi = float(p["F_phi"])
+    if F_phi < 0.0:                                      # Eq. 4 (Ergun): 1.75 / sqrt(150 phi^3)
+        F_phi = 1.75 / math.sqrt(150.0 * phi ** 3)
     return dict(
         nx=int(p["nx"]), ny=int(p["ny"]), qt=qt, flow=int(p["flow"]),
         periodic_x=int(p["periodic_x"]), periodic_y=int(p["periodic_y"]),

@@ -63,7 +63,7 @@ int derive_impl(const lbm_params* pp, lbm_derived* out) {
         const double fv[] = {p.Ra, p.Pr, p.Da, p.J, p.F_phi};
         for (double v : fv)
             if (!finite(v)) return LBM_ERR_ARG;
-        if (!(p.Pr > 0.0) || !(p.Da > 0.0) || !(p.J > 0.0) || !(p.F_phi >= 0.0) || !(p.Ra >= 0.0)) return LBM_ERR_ARG;
+        if (!(p.Pr > 0.0) || !(p.Da > 0.0) || !(p.J > 0.0) || !(p.Ra >= 0.0)) return LBM_ERR_ARG;
     }
 
     // Eq. 54 with delta_x = delta_t = c = 1, rho_l = 1, c_pl = c_pm = 1; c_ps and
@@ -91,6 +91,7 @@ int derive_impl(const lbm_params* pp, lbm_derived* out) {
     d.csT2 = p.thermal_q == 9 ? cs2 : 0.5 * p.varpi;
     d.c_ps = p.cps_over_cpl * c_pl;
     d.k_s = p.ks_over_kl * p.k_f;
+    d.F_phi = p.F_phi >= 0.0 ? p.F_phi : 1.75 / std::sqrt(150.0 * phi * phi * phi);   // Eq. 4 (Ergun)
     d.H_fs = d.c_ps * p.T_solidus;
     d.H_fl = c_pl * p.T_liquidus + d.L_a;
     d.exchange_rate = d.h_v * (1.0 / (phi * rho_l) + 1.0 / ((1.0 - phi) * d.rho_m));
@@ -121,7 +122,7 @@ int derive_impl(const lbm_params* pp, lbm_derived* out) {
         }
     if (p.flow) {
         d.l0 = 0.5 * (1.0 + phi * 0.5 * d.nu_f / d.K);  // Eq. 25
-        d.l1 = phi * 0.5 * p.F_phi / std::sqrt(d.K);
+        d.l1 = phi * 0.5 * d.F_phi / std::sqrt(d.K);
     }
     for (int s = 0; s < 4; ++s) d.H_wall[s] = enthalpy_of_T(p, d.L_a, p.wall_T[s]);
 
@@ -265,7 +266,7 @@ lbmk::StepParams<R> make_params(const lbm_handle* h, int from) {
     P.inv_phi = (R)(1.0 / phi);
     if (p.flow) {
         P.drag_lin = (R)(phi * d.nu_f / d.K);
-        P.drag_forch = (R)(phi * p.F_phi / std::sqrt(d.K));
+        P.drag_forch = (R)(phi * d.F_phi / std::sqrt(d.K));
         P.gbeta = (R)d.gbeta;
         P.T0 = (R)p.T_ref0;
         P.l0 = (R)d.l0;

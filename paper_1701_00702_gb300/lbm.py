@@ -57,7 +57,7 @@ class LbmDerived(ctypes.Structure):
         "H_fs", "H_fl", "l0", "l1", "exchange_rate")] + [
         ("s", ctypes.c_double * 9), ("zeta", ctypes.c_double * 9), ("eta", ctypes.c_double * 9),
         ("H_wall", ctypes.c_double * 4), ("k_s", ctypes.c_double), ("c_ps", ctypes.c_double),
-        ("zeta_a_solid", ctypes.c_double)]
+        ("zeta_a_solid", ctypes.c_double), ("F_phi", ctypes.c_double)]
 
 
 class RequestResult(ctypes.Structure):

@@ -46,6 +46,7 @@ def test_library_exports_every_declared_entry_point(lbm):
     lambda: dict(inputs.cavity(128, thermal_q=9), zeta_e=0.6),
     lambda: dict(inputs.cavity(128), zeta_e=1.8, solid_scheme=1),
     lambda: dict(inputs.cavity(128), ks_over_kl=0.5, cps_over_cpl=1.4, wall_T=[1.0, 0.1, 0.0, 0.0]),
+    lambda: dict(inputs.cavity(128), F_phi=-1.0),
     lambda: inputs.conduction_1d(thermal_q=9, ks_over_kl=2.0, cps_over_cpl=1.5, T_init=-0.3,
                                  wall_T=[1.0, -0.3, 0.0, 0.0]),
 ])
@@ -55,7 +56,7 @@ def test_parameter_map_matches_oracle(lbm, oracle_mod, make):
     lc = oracle_mod.lattice_config(p)
     keys = ["k_m", "rho_m", "L_a", "h_v", "alpha_fref", "alpha_mref", "c_fref", "c_mref", "d_p"]
     if p["flow"]:
-        keys += ["nu_f", "nu_e", "gbeta", "K"]
+        keys += ["nu_f", "nu_e", "gbeta", "K", "F_phi"]
     for k in keys:
         assert math.isclose(d[k], lc[k], rel_tol=1e-15, abs_tol=0.0), k
     q = lc["qt"]

@@ -299,7 +299,8 @@ VARIANTS = {"bgk": dict(thermal_collision=1), "bounce_back": dict(solid_scheme=1
             "bounce_back_bgk": dict(solid_scheme=1, thermal_collision=1),
             "eq9": dict(ks_over_kl=0.5, cps_over_cpl=1.4),
             "eq9_bgk": dict(ks_over_kl=2.0, cps_over_cpl=0.8, thermal_collision=1),
-            "eq9_zeta_e": dict(ks_over_kl=0.5, zeta_e=0.6)}
+            "eq9_zeta_e": dict(ks_over_kl=0.5, zeta_e=0.6),
+            "ergun_F_phi": dict(F_phi=-1.0)}
 
 
 @pytest.mark.parametrize("variant", sorted(VARIANTS))
