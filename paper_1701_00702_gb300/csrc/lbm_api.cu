@@ -260,6 +260,8 @@ lbmk::StepParams<R> make_params(const lbm_handle* h, int from) {
         P.tg_liquid = (R)(1.0 / (1.0 - om * d.c_fref));
         P.tg_mushy = (R)((p.T_liquidus - p.T_solidus) / (g0fl - g0fs));
         P.kappa_m = (R)(d.c_mref / (1.0 - om * d.c_mref));
+        P.om_cf = (R)(om * d.c_fref);
+        P.rest_m = (R)(1.0 - om * d.c_mref);
     }
     const double phi = p.porosity;
     P.phi = (R)phi;

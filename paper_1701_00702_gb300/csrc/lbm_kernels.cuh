@@ -126,6 +126,8 @@ struct StepParams {
     R g0_fs, g0_fl;      // PCM rest population at solidus / liquidus equilibrium
     R tg_solid, tg_mushy, tg_liquid;   // dT/dg_0 on the three branches
     R kappa_m;           // c_m,ref / (c_pm - omega c_m,ref): mover reference per unit of h_0 / w'_i
+    R om_cf;             // omega c_f,ref (omega = sum of the w'_i): g_0 = H - om_cf T(H) at equilibrium
+    R rest_m;            // 1 - omega c_m,ref / c_pm: h_0 = rest_m c_pm T_m at equilibrium
     // flow (Eqs. 3, 7, 16, 25)
     R phi, inv_phi, drag_lin, drag_forch, gbeta, T0, l0, l0sq, l1;
     R s[9];
@@ -573,27 +575,38 @@ __device__ __forceinline__ void store_thermal(const StepParams<typename ModeTrai
     nm[0] = n0hi;
     inv<R, QT>(nm, v);
     if constexpr (kSplit<M>) {
-        // reference from the provisional rest population, 16-bit deviations,
-        // then the rest population that closes the balance with the movers as
-        // encoded here.  Readers rebuild the reference from the stored rest
-        // population, which differs from the provisional one by the movers'
-        // 16-bit roundings, so the balance as read holds to those roundings
-        // times the slope of the reference (about a sixth of one rounding)
+        // 16-bit deviations from the reference of the provisional rest population,
+        // then the rest population readers will see the balance with.  Readers
+        // rebuild the reference from the stored rest population g_0; with
+        // Y = n_0 - sum of the stored deviations the balance needs
+        // g_0 + omega ref(g_0) = Y, and since g_0 = H - omega c_ref T(H) is the
+        // equilibrium rest population of an enthalpy H (Eqs. 38, 40, B3; Eqs. 49,
+        // B5 for the metal), the solution is that of H = Y: g_0 = Y - omega
+        // c_ref T(Y), whose reference is c_ref T(Y).  The stored populations as
+        // read then carry n_0 to FP32 rounding.
         using B = typename ModeTraits<M>::B;
         float sm = v[1];
 #pragma unroll
         for (int k = 2; k < QT; ++k) sm += v[k];
         const float g0a = n0hi - sm;
         const float ref = is_pcm ? pcm_ref(P, g0a) : P.kappa_m * g0a;
-        float st = 0.0f;
+        float sd = 0.0f;
 #pragma unroll
         for (int k = 1; k < QT; ++k) {
-            const float r = P.w_move[k] * ref;
-            const B b = from_f<B>(v[k] - r);
+            const B b = from_f<B>(v[k] - P.w_move[k] * ref);
             db[(mover_plane1 + k - 1) * kChunk] = b;
-            st += to_f(b) + r;
+            sd += to_f(b);
         }
-        dw[rest_plane * kChunk] = n0hi - st;
+        const float Y = n0hi - sd;
+        float rest;
+        if (is_pcm) {
+            float T, fl;
+            enthalpy_state(P, Y, T, fl);
+            rest = Y - P.om_cf * T;
+        } else {
+            rest = Y * P.rest_m;
+        }
+        dw[rest_plane * kChunk] = rest;
     } else {
 #pragma unroll
         for (int k = 1; k < QT; ++k) stb<M>(db + (mover_plane1 + k - 1) * kChunk, v[k]);

@@ -115,7 +115,9 @@ def test_periodic_box_conservation(lbm, prec):
     d0 = s.diag()
     s.step(500)
     d1 = s.diag()
-    assert abs(d1["enthalpy"] / d0["enthalpy"] - 1) < 1e-5      # rest populations close the balance in FP32
+    # the stored rest population closes the balance with the movers as readers
+    # decode them, so enthalpy is kept to FP32 rounding (measured 3e-8 / 1.4e-8)
+    assert abs(d1["enthalpy"] / d0["enthalpy"] - 1) < 1e-6
     assert abs(d1["mass"] / d0["mass"] - 1) < 1e-3
     s.close()
 
