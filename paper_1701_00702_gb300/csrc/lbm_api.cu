@@ -315,6 +315,7 @@ lbmk::StepParams<R> make_params(const lbm_handle* h, int from) {
         }
     }
     P.a_m = (R)(d.h_v / ((1.0 - phi) * d.rho_m));
+    P.x_pm = (R)(-(1.0 - phi) * d.rho_m / (phi * 1.0));
     return P;
 }
 

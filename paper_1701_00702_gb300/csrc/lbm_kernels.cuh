@@ -136,6 +136,7 @@ struct StepParams {
     R c_pl, c_fref, c_mref, c_pm, inv_c_pm, varpi;
     R zeta[9], eta[9];
     R a_f, a_m;          // h_v/(phi rho_l), h_v/((1 - phi) rho_m)
+    R x_pm;              // -a_f/a_m = -(1 - phi) rho_m/(phi rho_l): PCM source per unit of metal source
     // Eq. 9 variant: PCM rates from the node's liquid fraction
     int phase_k;         // 1: k_s != k_l, rates per node
     R kl_c, ks_c;        // k_l, k_s over (rho_l c_fref c_sT^2)
@@ -558,9 +559,10 @@ __device__ __forceinline__ void node_state(const StepParams<typename ModeTraits<
 // Post-collision thermal populations from their moments.  n0 is the
 // conserved moment after the source (hi, lo).  The rest population is the
 // remainder n0 - sum of the moving populations as they are stored, so the
-// stored populations carry exactly the enthalpy (internal energy) that the
-// collision produced: to float-float accuracy with FP32 storage, to one FP32
-// rounding with 16-bit movers, to FP64 rounding with FP64 storage.
+// stored populations carry the enthalpy (internal energy) that the collision
+// produced: the FP32 PCM rest population to float-float accuracy, the FP32
+// metal one to one rounding, the 16-bit forms to FP32 rounding as readers
+// decode them, FP64 to FP64 rounding.
 // db and dw point at the node's element in bulk plane 0 and wide plane 0 of the
 // next copy; rest_plane is a wide plane in the 16-bit modes, a bulk plane
 // otherwise.
@@ -569,7 +571,7 @@ __device__ __forceinline__ void store_thermal(const StepParams<typename ModeTrai
                                               typename ModeTraits<M>::R* nm, typename ModeTraits<M>::R n0hi,
                                               typename ModeTraits<M>::R n0lo, typename ModeTraits<M>::B* db,
                                               float* dw, int rest_plane, int mover_plane1, int lo_plane,
-                                              bool remainder, bool is_pcm) {
+                                              bool is_pcm) {
     using R = typename ModeTraits<M>::R;
     R v[QT];
     nm[0] = n0hi;
@@ -610,13 +612,16 @@ __device__ __forceinline__ void store_thermal(const StepParams<typename ModeTrai
     } else {
 #pragma unroll
         for (int k = 1; k < QT; ++k) stb<M>(db + (mover_plane1 + k - 1) * kChunk, v[k]);
-        if (!remainder) {
-            stb<M>(db + rest_plane * kChunk, v[0]);
-        } else if constexpr (kComp<M>) {
-            const FF r = ff_accumulate<QT>(FF{n0hi, n0lo}, v, -1.0f);
-            stb<M>(db + rest_plane * kChunk, r.hi);
-            stb<M>(db + lo_plane * kChunk, r.lo);
-        } else {
+        bool pair = false;   // the FP32 PCM rest population is a float-float pair
+        if constexpr (kComp<M>) {
+            if (is_pcm) {
+                const FF r = ff_accumulate<QT>(FF{n0hi, n0lo}, v, -1.0f);
+                stb<M>(db + rest_plane * kChunk, r.hi);
+                stb<M>(db + lo_plane * kChunk, r.lo);
+                pair = true;
+            }
+        }
+        if (!pair) {
             R sm = v[1];
 #pragma unroll
             for (int k = 2; k < QT; ++k) sm += v[k];
@@ -698,8 +703,16 @@ __device__ __forceinline__ void step_node(const StepParams<typename ModeTraits<M
     const R dTn = n.Tm - n.Tf;
     const R dTp = P.dT[o];
     const R Sx = R(1.5) * dTn - R(0.5) * dTp;
-    const R S_pcm = P.a_f * Sx;
     const R S_met = -P.a_m * Sx;
+    // metal n_0 after its source (n_0 is conserved by the collision, Eq. 43).  The
+    // PCM takes the opposite of what the metal's n_0 actually changed by, scaled
+    // by the heat capacities (S_PCM = -(a_f/a_m) S_metal, Eqs. 36, 47), so an
+    // exchange that the metal's rounding drops moves no energy into the PCM
+    R hm_base;
+    if constexpr (kSplit<M>) hm_base = n.nh[0];
+    else hm_base = n.nh[0] - P.eta[0] * (n.nh[0] - P.c_pm * n.Tm);
+    const R hm = hm_base + S_met;
+    const R S_pcm = (hm - hm_base) * P.x_pm;
 
     {
         R ne[QT];
@@ -728,7 +741,7 @@ __device__ __forceinline__ void step_node(const StepParams<typename ModeTraits<M
             hi = n.ng[0] + S_pcm;
             lo = R(0);
         }
-        store_thermal<M, QT>(P, n.ng, hi, lo, db, dw, kSplit<M> ? 0 : PL::pcm(0), PL::pcm(1), PL::lo, true, true);
+        store_thermal<M, QT>(P, n.ng, hi, lo, db, dw, kSplit<M> ? 0 : PL::pcm(0), PL::pcm(1), PL::lo, true);
     }
     {
         R ne[QT];
@@ -740,11 +753,7 @@ __device__ __forceinline__ void step_node(const StepParams<typename ModeTraits<M
         } else {
             n.nh[3] += P.varpi * S_met;
         }
-        R hi;
-        if constexpr (kSplit<M>) hi = n.nh[0] + S_met;
-        else hi = n.nh[0] - P.eta[0] * (n.nh[0] - ne[0]) + S_met;
-        store_thermal<M, QT>(P, n.nh, hi, R(0), db, dw, kSplit<M> ? 1 : PL::met(0), PL::met(1), PL::lo,
-                             kSplit<M>, false);
+        store_thermal<M, QT>(P, n.nh, hm, R(0), db, dw, kSplit<M> ? 1 : PL::met(0), PL::met(1), PL::lo, false);
     }
     P.dT[o] = dTn;
 
