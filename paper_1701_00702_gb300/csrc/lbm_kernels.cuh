@@ -23,11 +23,18 @@
 //   * the PCM enthalpy is bookkept exactly: with FP32 storage the rest
 //     population g_0 is kept as an unevaluated float-float sum (hi in the
 //     g_0 plane, lo in one extra plane), H = g_0 + sum_{i>=1} g_i is formed
-//     with error-free additions (Knuth's TwoSum, Dekker's Fast2Sum), and the
-//     post-collision rest population is the remainder g_0* = n_0* - sum_{i>=1}
-//     g_i* of the rounded moving populations, so that streaming and collision
-//     conserve the enthalpy to ~2^-48 instead of accumulating FP32 rounding
-//     in the isothermal mushy zone, where nothing damps it.
+//     as a compensated sum of error-free additions (Knuth's TwoSum, Dekker's
+//     Fast2Sum), and the post-collision rest population is the remainder
+//     g_0* = n_0* - sum_{i>=1} g_i* of the stored moving populations, so that
+//     streaming and collision conserve the enthalpy to ~2^-46 instead of
+//     accumulating FP32 rounding in the isothermal mushy zone, where nothing
+//     damps it;
+//   * every other rest population is a remainder as well, and the PCM's
+//     exchange source is the opposite of the change the metal's n_0 actually
+//     took (scaled by the heat capacities), so the exchange moves no energy
+//     that the metal's rounding dropped;
+//   * the state is chunked: [chunk][plane][kChunk] with chunks of kChunk nodes
+//     along x, so one pointer per pulled neighbour reaches all its planes.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -52,7 +59,9 @@ namespace lbmk {
 //             w'_i c_ref T and the rest population is g_0 = H - omega c_ref T
 //             (Eqs. 40, 49, B3, B5), a monotone map of the node's state, so
 //             T (hence the reference) follows from g_0 alone.  The 16-bit
-//             values then carry only the flux and non-equilibrium parts.
+//             values then carry only the flux and non-equilibrium parts, and
+//             the sender stores the rest population that closes the balance
+//             with the movers as readers decode them.
 enum : int { MODE_F64 = 0, MODE_F32 = 1, MODE_F16 = 2, MODE_BF16 = 3 };
 
 template <int M> struct ModeTraits;
