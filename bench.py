@@ -93,7 +93,8 @@ def parse():
     ap.add_argument("--n", type=int, default=256, help="cavity side")
     ap.add_argument("--precision", default="f32", choices=["f64", "f32", "f16", "bf16"],
                     help="storage form of the headline run")
-    ap.add_argument("--lb-steps", type=int, default=2000, help="LB time steps per benchmark step")
+    ap.add_argument("--lb-steps", type=int, default=20000,
+                    help="LB time steps per benchmark step (a tenth of the 200k-step solve)")
     ap.add_argument("--roofline-n", type=int, default=2048)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
@@ -162,10 +163,16 @@ class ClockSampler:
         try:
             fd, self.path = tempfile.mkstemp(suffix=".csv")
             os.close(fd)
-            cmd = ["nvidia-smi", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits", "-lms", "200"]
+            cmd = ["nvidia-smi", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits", "-lms", "50"]
             if self.bus_id:
                 cmd += ["-i", self.bus_id]
             self.proc = subprocess.Popen(cmd, stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+            # the timed region starts only once the sampler is running
+            t0 = time.perf_counter()
+            while time.perf_counter() - t0 < 2.0 and self.proc.poll() is None:
+                if Path(self.path).stat().st_size > 0:
+                    break
+                time.sleep(0.01)
         except Exception:
             self.proc = None
 
