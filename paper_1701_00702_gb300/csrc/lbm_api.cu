@@ -256,10 +256,14 @@ lbmk::StepParams<R> make_params(const lbm_handle* h, int from) {
         const double g0fs = d.H_fs - om * d.c_fref * p.T_solidus, g0fl = d.H_fl - om * d.c_fref * p.T_liquidus;
         P.g0_fs = (R)g0fs;
         P.g0_fl = (R)g0fl;
-        P.tg_solid = (R)(1.0 / (d.c_ps - om * d.c_fref));
-        P.tg_liquid = (R)(1.0 / (1.0 - om * d.c_fref));
-        P.tg_mushy = (R)((p.T_liquidus - p.T_solidus) / (g0fl - g0fs));
-        P.kappa_m = (R)(d.c_mref / (1.0 - om * d.c_mref));
+        P.cr_solid = (R)(d.c_fref / (d.c_ps - om * d.c_fref));
+        P.cr_liquid = (R)(d.c_fref / (1.0 - om * d.c_fref));
+        P.cr_mushy = (R)(d.c_fref * (p.T_liquidus - p.T_solidus) / (g0fl - g0fs));
+        P.cr_fs = (R)(d.c_fref * p.T_solidus);
+        P.cr_fl = (R)(d.c_fref * p.T_liquidus);
+        const double kappa = d.c_mref / (1.0 - om * d.c_mref);
+        P.kappa_m = (R)kappa;
+        for (int k = 0; k < 9; ++k) P.wk_move[k] = (R)((Q == 9 ? w9[k] : 0.25 * p.varpi) * kappa);
         P.om_cf = (R)(om * d.c_fref);
         P.rest_m = (R)(1.0 - om * d.c_mref);
     }

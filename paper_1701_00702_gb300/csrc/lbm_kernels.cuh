@@ -133,7 +133,9 @@ struct StepParams {
     // 16-bit modes: references of the moving thermal populations
     R w_move[9];         // w'_i: the equilibrium weight of mover i (D2Q9 w_i, D2Q5 varpi/4)
     R g0_fs, g0_fl;      // PCM rest population at solidus / liquidus equilibrium
-    R tg_solid, tg_mushy, tg_liquid;   // dT/dg_0 on the three branches
+    R cr_solid, cr_mushy, cr_liquid;   // c_f,ref dT/dg_0 on the three branches
+    R cr_fs, cr_fl;      // c_f,ref T_fs, c_f,ref T_fl
+    R wk_move[9];        // w'_i kappa_m: metal mover reference per unit of h_0
     R kappa_m;           // c_m,ref / (c_pm - omega c_m,ref): mover reference per unit of h_0 / w'_i
     R om_cf;             // omega c_f,ref (omega = sum of the w'_i): g_0 = H - om_cf T(H) at equilibrium
     R rest_m;            // 1 - omega c_m,ref / c_pm: h_0 = rest_m c_pm T_m at equilibrium
@@ -338,10 +340,10 @@ __device__ __forceinline__ void enthalpy_state(const StepParams<R>& P, R H, R& T
 // inverse of g_0 = H - omega c_f,ref T(H) with T(H) from Eq. 38 (16-bit modes).
 template <typename R>
 __device__ __forceinline__ R pcm_ref(const StepParams<R>& P, R g0) {
-    const R Ts = g0 * P.tg_solid;
-    const R Tm = P.T_fs + (g0 - P.g0_fs) * P.tg_mushy;
-    const R Tl = P.T_fl + (g0 - P.g0_fl) * P.tg_liquid;
-    return P.c_fref * (g0 <= P.g0_fs ? Ts : (g0 < P.g0_fl ? Tm : Tl));
+    const R Ts = g0 * P.cr_solid;
+    const R Tm = P.cr_fs + (g0 - P.g0_fs) * P.cr_mushy;
+    const R Tl = P.cr_fl + (g0 - P.g0_fl) * P.cr_liquid;
+    return g0 <= P.g0_fs ? Ts : (g0 < P.g0_fl ? Tm : Tl);
 }
 
 template <typename R>
@@ -442,7 +444,7 @@ __device__ __forceinline__ void pull_moments(const StepParams<typename ModeTrait
 #pragma unroll
         for (int q = 1; q < QT; ++q) {   // deviation + reference of the sending node
             g[q] = ldb<M>(sb[q] + PL::pcm(q) * kChunk) + P.w_move[q] * pcm_ref(P, __ldg(sw[q]));
-            h[q] = ldb<M>(sb[q] + PL::met(q) * kChunk) + P.w_move[q] * P.kappa_m * __ldg(sw[q] + kChunk);
+            h[q] = ldb<M>(sb[q] + PL::met(q) * kChunk) + P.wk_move[q] * __ldg(sw[q] + kChunk);
         }
     } else {
 #pragma unroll
