@@ -312,6 +312,27 @@ def bench_serving(args, lbm, inputs, stream, plain_mlups: float, seed: int = 170
             "peak_admitted_gb": st["peak_used_bytes"] / 1e9})
     return out
 
+def bench_accuracy(args, lbm, inputs, stream, steps: int = 4000) -> dict:
+    """Error of each storage form against FP64 on the headline cavity: melt
+    fraction and hot-wall Nusselt number after `steps` steps.  The reference is
+    the FP64 GPU path, which the parity tests hold to 1e-10 of the FP64 oracle."""
+    res = {}
+    for fprec in (0, 1, 2, 3):
+        s = lbm.Solver(inputs.cavity(args.n, precision=fprec), stream=stream)
+        s.step(steps)
+        d = s.diag()
+        s.close()
+        res[fprec] = d
+    ref = res[0]
+    out = {"workload": f"{args.n}x{args.n} cavity, {steps} steps", "reference": "FP64 (GPU path)",
+           "melt_frac": ref["melt_frac"], "nu_hot": ref["nu_hot"], "forms": []}
+    for fprec in (1, 2, 3):
+        out["forms"].append({"precision": PREC_NAMES[fprec],
+                             "melt_frac_rel_err": abs(res[fprec]["melt_frac"] / ref["melt_frac"] - 1.0),
+                             "nu_hot_rel_err": abs(res[fprec]["nu_hot"] / ref["nu_hot"] - 1.0)})
+    return out
+
+
 def bench_batched(args, lbm, inputs, torch, stream, steps_per_solve: int = 10_000, chunk: int = 64, reps: int = 3):
     """64 cavities, sides uniform in [64, 512], porosity, Da, Ra, Ste drawn as in
     the batched workload; every form advances all runs by the same steps."""
@@ -505,6 +526,8 @@ def main():
         if not args.no_serving:
             serving = bench_serving(args, lbm, inputs, stream, roof["mlups"] if roof else 30000.0)
 
+        accuracy = None if args.roofline_n <= 0 else bench_accuracy(args, lbm, inputs, stream)
+
         # every storage form of the same step, on the L2-resident and the HBM-bound cavity
         forms = []
         if args.roofline_n > 0:
@@ -533,6 +556,7 @@ def main():
                         "gbs_algorithmic": bpu * cells / (launch_ms_small / 1e3) / 1e9,
                         "note": "256x256 state (10 MB) is L2-resident; launch-to-launch time inside CUDA graphs"},
         "forms": forms if args.roofline_n > 0 else None,
+        "accuracy": accuracy,
         "batched": batched,
         "serving": serving,
         "cpu_baseline": cpu,
