@@ -155,3 +155,51 @@ def test_conduction_melting_vs_fp64_oracle(lbm, oracle_mod, prec):
     assert abs(d["melt_frac"] / do["melt_frac"] - 1) < TOL[prec]
     assert abs(d["nu_hot"] / do["nu_hot"] - 1) < TOL[prec]
     s.close()
+
+
+@pytest.mark.parametrize("prec,rtol", [(F16, 2 * 2.0 ** -11), (BF16, 2 * 2.0 ** -8)])
+def test_full_size_sampled_parity_2048(lbm, oracle_mod, prec, rtol):
+    """The 16-bit forms on the 2048 x 2048 cavity in the benchmark's launch
+    configuration: one step from a random state (as the solver holds it after
+    encoding) against the oracle at sampled nodes, all edges and corners plus
+    random interior nodes."""
+    n = 2048
+    p = inputs.cavity(n, precision=prec)
+    lc = oracle_mod.lattice_config(p)
+    F, G, Hm, dT = inputs.random_state(n, n, 5, seed=2049, H_range=(lc["T_fs"] - 0.3, lc["T_fl"] + lc["L_a"] + 0.3))
+    s = lbm.Solver(p)
+    s.set_state(on_grid(F - W9, prec, 1024.0), G.astype(np.float32), Hm.astype(np.float32), dT.astype(np.float32))
+    del F, G, Hm
+    f0, g0, h0, d0 = s.get_state()                        # the oracle starts from what the solver holds
+    s.step(1)
+    f1, g1, h1, d1 = s.get_state()
+    o = oracle_mod.Oracle(p)
+    o.set_state(f0.astype(np.float64) + W9, g0.astype(np.float64), h0.astype(np.float64), d0.astype(np.float64))
+    rng = np.random.default_rng(11)
+    edge = np.arange(n)
+    xs = np.concatenate([edge, edge, np.zeros(n, int), np.full(n, n - 1), rng.integers(0, n, 20000)])
+    ys = np.concatenate([np.zeros(n, int), np.full(n, n - 1), edge, edge, rng.integers(0, n, 20000)])
+    fo, go, ho, do = o.step_nodes(xs, ys)
+    fo = fo - W9[:, 0, 0][None, :]
+    for a, b, name in ((f1[:, ys, xs].T, fo, "f - w"), (g1[:, ys, xs].T, go, "g"), (h1[:, ys, xs].T, ho, "h")):
+        err = np.abs(a.astype(np.float64) - b).max() / max(np.abs(b).max(), 1e-3)
+        assert err < rtol * 4, (name, err)
+    assert np.abs(d1[ys, xs] - do).max() < 1e-5
+    s.close()
+
+
+@pytest.mark.parametrize("prec", [F16, BF16])
+def test_config2_size_against_fp32(lbm, prec):
+    """The 1024 x 1024 cavity (the mixed-precision workload's size), 4,000 steps:
+    melt fraction and hot-wall Nusselt number of the 16-bit form within the
+    mixed-form tolerance of the FP32 path on the same GPU (which the parity
+    tests hold to 1e-5 of the FP64 oracle)."""
+    d = {}
+    for q in (1, prec):
+        s = lbm.Solver(inputs.cavity(1024, precision=q))
+        s.step(4000)
+        assert s.status() == 0
+        d[q] = s.diag()
+        s.close()
+    assert abs(d[prec]["melt_frac"] / d[1]["melt_frac"] - 1) < TOL[prec]
+    assert abs(d[prec]["nu_hot"] / d[1]["nu_hot"] - 1) < TOL[prec]
