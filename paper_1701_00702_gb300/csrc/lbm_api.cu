@@ -291,13 +291,11 @@ lbmk::StepParams<R> make_params(const lbm_handle* h, int from) {
     P.T_fs = (R)p.T_solidus;
     P.T_fl = (R)p.T_liquidus;
     P.inv_c_ps = (R)(1.0 / d.c_ps);
-    P.inv_c_pl = (R)1.0;
-    P.c_pl = (R)1.0;
     P.c_fref = (R)d.c_fref;
     P.c_mref = (R)d.c_mref;
-    P.c_pm = (R)1.0;
-    P.inv_c_pm = (R)1.0;
     P.varpi = (R)p.varpi;
+    P.vcf = (R)(p.varpi * d.c_fref);
+    P.vcm = (R)(p.varpi * d.c_mref);
     P.a_f = (R)(d.h_v / (phi * 1.0));
     // Eq. 9 variant: per-node zeta_alpha = 1/(1/2 + k_f(f_l)/(rho_l c_fref c_sT^2)) (Eq. A19);
     // rate k of the PCM lattice is zr_a[k] + zr_b[k] zeta_alpha (fixed, zeta_alpha, or 2 - zeta_alpha)

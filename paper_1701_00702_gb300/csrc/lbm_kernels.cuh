@@ -143,8 +143,10 @@ struct StepParams {
     R phi, inv_phi, drag_lin, drag_forch, gbeta, T0, l0, l0sq, l1;
     R s[9];
     // thermal (Eqs. 38-39, 34, 45, App. B)
-    R H_fs, H_fl, inv_dH, mush_slope, T_fs, T_fl, inv_c_ps, inv_c_pl;
-    R c_pl, c_fref, c_mref, c_pm, inv_c_pm, varpi;
+    // (c_pl = c_pm = 1 in the lattice units of Eq. 54, so they appear nowhere below)
+    R H_fs, H_fl, inv_dH, mush_slope, T_fs, T_fl, inv_c_ps;
+    R c_fref, c_mref, varpi;
+    R vcf, vcm;          // varpi c_f,ref and varpi c_m,ref (D2Q5 equilibria, Eqs. B2, B4)
     R zeta[9], eta[9];
     R a_f, a_m;          // h_v/(phi rho_l), h_v/((1 - phi) rho_m)
     R x_pm;              // -a_f/a_m = -(1 - phi) rho_m/(phi rho_l): PCM source per unit of metal source
@@ -293,7 +295,8 @@ __device__ __forceinline__ void meq_flow_dev(const StepParams<R>& P, R rho, R dr
 // Eq. 34 (D2Q9) / Eq. B2 (D2Q5)
 template <typename R, int Q>
 __device__ __forceinline__ void neq_pcm(const StepParams<R>& P, R H, R T, R ux, R uy, R* ne) {
-    const R jx = P.c_pl * T * ux * P.inv_phi, jy = P.c_pl * T * uy * P.inv_phi;
+    const R t = T * P.inv_phi;   // c_pl T / phi
+    const R jx = t * ux, jy = t * uy;
     if constexpr (Q == 9) {
         ne[0] = H;
         ne[1] = R(-4) * H + R(2) * P.c_fref * T;
@@ -301,7 +304,7 @@ __device__ __forceinline__ void neq_pcm(const StepParams<R>& P, R H, R T, R ux, 
         ne[3] = jx; ne[4] = -jx; ne[5] = jy; ne[6] = -jy;
         ne[7] = R(0); ne[8] = R(0);
     } else {
-        ne[0] = H; ne[1] = jx; ne[2] = jy; ne[3] = P.varpi * P.c_fref * T; ne[4] = R(0);
+        ne[0] = H; ne[1] = jx; ne[2] = jy; ne[3] = P.vcf * T; ne[4] = R(0);
     }
 }
 
@@ -309,14 +312,14 @@ __device__ __forceinline__ void neq_pcm(const StepParams<R>& P, R H, R T, R ux, 
 template <typename R, int Q>
 __device__ __forceinline__ void neq_metal(const StepParams<R>& P, R Tm, R* ne) {
     if constexpr (Q == 9) {
-        const R e = P.c_pm * Tm;
+        const R e = Tm;   // c_pm T_m
         ne[0] = e;
         ne[1] = R(-4) * e + R(2) * P.c_mref * Tm;
         ne[2] = R(4) * e - R(3) * P.c_mref * Tm;
 #pragma unroll
         for (int k = 3; k < 9; ++k) ne[k] = R(0);
     } else {
-        ne[0] = P.c_pm * Tm; ne[1] = R(0); ne[2] = R(0); ne[3] = P.varpi * P.c_mref * Tm; ne[4] = R(0);
+        ne[0] = Tm; ne[1] = R(0); ne[2] = R(0); ne[3] = P.vcm * Tm; ne[4] = R(0);   // ne[0] = c_pm T_m
     }
 }
 
@@ -331,7 +334,7 @@ __device__ __forceinline__ void enthalpy_state(const StepParams<R>& P, R H, R& T
         T = P.T_fs + d * P.mush_slope;
         fl = d * P.inv_dH;
     } else {
-        T = P.T_fl + (H - P.H_fl) * P.inv_c_pl;
+        T = P.T_fl + (H - P.H_fl);   // 1/c_pl = 1
         fl = R(1);
     }
 }
@@ -404,6 +407,16 @@ __device__ __forceinline__ auto wide_at(C* base, const StepParams<R>& P, int x, 
            (x & (kChunk - 1));
 }
 
+// Byte offset of node x's element in bulk plane 0 (WIDE: wide plane 0) from
+// the start of its row of chunks; a row of chunks is cpr * Chunk::bytes long
+// (below 2^31 bytes for every admitted grid).
+template <int M, int QT, bool FLOW, bool WIDE = false>
+__device__ __forceinline__ int col_off(int x) {
+    using CH = Chunk<M, QT, FLOW>;
+    constexpr int es = WIDE ? (int)sizeof(float) : (int)sizeof(typename ModeTraits<M>::B);
+    return (x >> kChunkShift) * CH::bytes + (WIDE ? CH::wide_off : 0) + (x & (kChunk - 1)) * es;
+}
+
 // Pull streaming around node (xs, ys): the population along e_i comes from
 // xs - e_i.  The index wrap is also correct for interior nodes of a walled
 // direction, which never reach the edge.
@@ -418,13 +431,18 @@ __device__ __forceinline__ void pull_moments(const StepParams<typename ModeTrait
     const int xp = xs == P.nx - 1 ? 0 : xs + 1;
     const int ym = ys == 0 ? P.ny - 1 : ys - 1;
     const int yp = ys == P.ny - 1 ? 0 : ys + 1;
-    const int xc[3] = {xm, xs, xp}, yr[3] = {ym, ys, yp};
     // source column and row (x - e_x, y - e_y) of direction q, D2Q9 order of Eq. 11
     constexpr int ci[9] = {1, 0, 1, 2, 1, 0, 2, 2, 0};
     constexpr int ri[9] = {1, 1, 0, 1, 2, 0, 0, 2, 2};
+    // one 64-bit row pointer per source row, one 32-bit offset per source column
+    const int rb = P.cpr * Chunk<M, QT, FLOW>::bytes;
+    const int c0 = col_off<M, QT, FLOW>(xs);
+    const char* own = P.src + ((long long)ys * rb + c0);
+    const char* row[3] = {own + (long long)(ym - ys) * rb, own, own + (long long)(yp - ys) * rb};
+    const int dc[3] = {col_off<M, QT, FLOW>(xm) - c0, 0, col_off<M, QT, FLOW>(xp) - c0};
     const B* sb[ND];   // the source node's element in bulk plane 0
 #pragma unroll
-    for (int q = 0; q < ND; ++q) sb[q] = bulk_at<M, QT, FLOW>(P.src, P, xc[ci[q]], yr[ri[q]]);
+    for (int q = 0; q < ND; ++q) sb[q] = reinterpret_cast<const B*>(row[ri[q]] + dc[ci[q]]);
     if constexpr (FLOW) {
         R f[9];
 #pragma unroll
@@ -438,7 +456,10 @@ __device__ __forceinline__ void pull_moments(const StepParams<typename ModeTrait
     if constexpr (kSplit<M>) {
         const float* sw[QT];   // the source node's element in wide plane 0 (PCM rest; metal rest follows)
 #pragma unroll
-        for (int q = 0; q < QT; ++q) sw[q] = wide_at<M, QT, FLOW>(P.src, P, xc[ci[q]], yr[ri[q]]);
+        for (int q = 0; q < QT; ++q) {
+            const int dw = col_off<M, QT, FLOW, true>(ci[q] == 0 ? xm : (ci[q] == 1 ? xs : xp)) - c0;
+            sw[q] = reinterpret_cast<const float*>(row[ri[q]] + dw);
+        }
         g[0] = __ldg(sw[0]);
         h[0] = __ldg(sw[0] + kChunk);
 #pragma unroll
@@ -473,7 +494,7 @@ __device__ __forceinline__ void macro(const StepParams<typename ModeTraits<M>::R
     using R = typename ModeTraits<M>::R;
     n.H = n.ng[0];
     enthalpy_state(P, n.H, n.Tf, n.fl);
-    n.Tm = n.nh[0] * P.inv_c_pm;
+    n.Tm = n.nh[0];   // h_0 moment = c_pm T_m, c_pm = 1
     if constexpr (FLOW) {
         n.drho = n.mp[0];
         n.rho = R(1) + n.drho;
@@ -598,10 +619,7 @@ __device__ __forceinline__ void store_thermal(const StepParams<typename ModeTrai
         // c_ref T(Y), whose reference is c_ref T(Y).  The stored populations as
         // read then carry n_0 to FP32 rounding.
         using B = typename ModeTraits<M>::B;
-        float sm = v[1];
-#pragma unroll
-        for (int k = 2; k < QT; ++k) sm += v[k];
-        const float g0a = n0hi - sm;
+        const float g0a = v[0];   // provisional rest population (only picks the reference)
         const float ref = is_pcm ? pcm_ref(P, g0a) : P.kappa_m * g0a;
         float sd = 0.0f;
 #pragma unroll
@@ -659,9 +677,11 @@ __device__ __forceinline__ void step_node(const StepParams<typename ModeTraits<M
     node_state<M, QT, FLOW>(P, x, y, n, wall);
 
     const int o = y * P.pitch + x;                                  // exchange history
-    typename ModeTraits<M>::B* db = bulk_at<M, QT, FLOW>(P.dst, P, x, y);   // this node in the next copy
+    // this node in the next copy
+    const long long ro = (long long)y * (P.cpr * Chunk<M, QT, FLOW>::bytes);
+    typename ModeTraits<M>::B* db = reinterpret_cast<typename ModeTraits<M>::B*>(P.dst + (ro + col_off<M, QT, FLOW>(x)));
     float* dw = nullptr;
-    if constexpr (kSplit<M>) dw = wide_at<M, QT, FLOW>(P.dst, P, x, y);
+    if constexpr (kSplit<M>) dw = reinterpret_cast<float*>(P.dst + (ro + col_off<M, QT, FLOW, true>(x)));
 
     if constexpr (FLOW) {
       if (P.solid_scheme && n.fl <= R(0.5)) {
@@ -696,10 +716,14 @@ __device__ __forceinline__ void step_node(const StepParams<typename ModeTraits<M
                         rho * Fy, -rho * Fy, rho * R(2) * (n.ux * Fx - n.uy * Fy) * ip,
                         rho * (n.ux * Fy + n.uy * Fx) * ip};
         // Eq. 14: the rates of Sec. III C are constants (s_rho = s_j = 1, s_e = s_eps =
-        // 1.1, s_q = 1.2); only s_v = s[7] = s[8] depends on the run
+        // 1.1, s_q = 1.2); only s_v = s[7] = s[8] depends on the run.  Where s = 1 the
+        // result is m^eq + S/2 whatever the blend gave (rho: m^eq = delta_rho, S = 0)
         constexpr double sk[7] = {1.0, 1.1, 1.1, 1.0, 1.2, 1.0, 1.2};
+        m[0] = me[0];
 #pragma unroll
-        for (int k = 0; k < 7; ++k) m[k] = m[k] - R(sk[k]) * (m[k] - me[k]) + R(1.0 - 0.5 * sk[k]) * S[k];
+        for (int k = 1; k < 7; ++k)
+            m[k] = sk[k] == 1.0 ? me[k] + R(0.5) * S[k]
+                                : m[k] - R(sk[k]) * (m[k] - me[k]) + R(1.0 - 0.5 * sk[k]) * S[k];
         const R sv = P.s[7], hv = R(1) - R(0.5) * sv;
         m[7] = m[7] - sv * (m[7] - me[7]) + hv * S[7];
         m[8] = m[8] - sv * (m[8] - me[8]) + hv * S[8];
@@ -721,7 +745,7 @@ __device__ __forceinline__ void step_node(const StepParams<typename ModeTraits<M
     // exchange that the metal's rounding drops moves no energy into the PCM
     R hm_base;
     if constexpr (kSplit<M>) hm_base = n.nh[0];
-    else hm_base = n.nh[0] - P.eta[0] * (n.nh[0] - P.c_pm * n.Tm);
+    else hm_base = n.nh[0] - P.eta[0] * (n.nh[0] - n.Tm);
     const R hm = hm_base + S_met;
     const R S_pcm = (hm - hm_base) * P.x_pm;
 
@@ -769,8 +793,9 @@ __device__ __forceinline__ void step_node(const StepParams<typename ModeTraits<M
     P.dT[o] = dTn;
 
     // non-finite or runaway state: raise the sticky flag (no trap)
-    const bool bad = !(fabs(n.H) < R(1e30)) || !(n.rho > R(0) && n.rho < R(1e30)) ||
-                     !(n.ux * n.ux + n.uy * n.uy <= R(0.09)) || !(fabs(n.Tm) < R(1e30));
+    // (a NaN anywhere fails a comparison; the sum overflows if any term is huge)
+    const bool bad = !(fabs(n.H) + fabs(n.Tm) + n.rho < R(1e30)) || !(n.rho > R(0)) ||
+                     !(n.ux * n.ux + n.uy * n.uy <= R(0.09));
     if (bad) atomicOr(P.status, STATUS_UNSTABLE);
 }
 
