@@ -258,9 +258,9 @@ lbmk::StepParams<R> make_params(const lbm_handle* h, int from) {
         P.g0_fl = (R)g0fl;
         P.cr_solid = (R)(d.c_fref / (d.c_ps - om * d.c_fref));
         P.cr_liquid = (R)(d.c_fref / (1.0 - om * d.c_fref));
-        P.cr_mushy = (R)(d.c_fref * (p.T_liquidus - p.T_solidus) / (g0fl - g0fs));
         P.cr_fs = (R)(d.c_fref * p.T_solidus);
-        P.cr_fl = (R)(d.c_fref * p.T_liquidus);
+        P.cr_dsl = (R)(d.c_fref * (p.T_liquidus - p.T_solidus));
+        P.inv_dg0 = (R)(1.0 / (g0fl - g0fs));
         const double kappa = d.c_mref / (1.0 - om * d.c_mref);
         P.kappa_m = (R)kappa;
         for (int k = 0; k < 9; ++k) P.wk_move[k] = (R)((Q == 9 ? w9[k] : 0.25 * p.varpi) * kappa);
@@ -287,7 +287,7 @@ lbmk::StepParams<R> make_params(const lbm_handle* h, int from) {
     P.H_fs = (R)d.H_fs;
     P.H_fl = (R)d.H_fl;
     P.inv_dH = (R)(1.0 / (d.H_fl - d.H_fs));
-    P.mush_slope = (R)((p.T_liquidus - p.T_solidus) / (d.H_fl - d.H_fs));
+    P.dT_sl = (R)(p.T_liquidus - p.T_solidus);
     P.T_fs = (R)p.T_solidus;
     P.T_fl = (R)p.T_liquidus;
     P.inv_c_ps = (R)(1.0 / d.c_ps);

@@ -133,8 +133,9 @@ struct StepParams {
     // 16-bit modes: references of the moving thermal populations
     R w_move[9];         // w'_i: the equilibrium weight of mover i (D2Q9 w_i, D2Q5 varpi/4)
     R g0_fs, g0_fl;      // PCM rest population at solidus / liquidus equilibrium
-    R cr_solid, cr_mushy, cr_liquid;   // c_f,ref dT/dg_0 on the three branches
-    R cr_fs, cr_fl;      // c_f,ref T_fs, c_f,ref T_fl
+    R cr_solid, cr_liquid;   // c_f,ref dT/dg_0 on the solid and liquid branches
+    R cr_fs, cr_dsl;     // c_f,ref T_fs, c_f,ref (T_fl - T_fs)
+    R inv_dg0;           // 1 / (g0_fl - g0_fs)
     R wk_move[9];        // w'_i kappa_m: metal mover reference per unit of h_0
     R kappa_m;           // c_m,ref / (c_pm - omega c_m,ref): mover reference per unit of h_0 / w'_i
     R om_cf;             // omega c_f,ref (omega = sum of the w'_i): g_0 = H - om_cf T(H) at equilibrium
@@ -144,7 +145,7 @@ struct StepParams {
     R s[9];
     // thermal (Eqs. 38-39, 34, 45, App. B)
     // (c_pl = c_pm = 1 in the lattice units of Eq. 54, so they appear nowhere below)
-    R H_fs, H_fl, inv_dH, mush_slope, T_fs, T_fl, inv_c_ps;
+    R H_fs, H_fl, inv_dH, T_fs, T_fl, dT_sl, inv_c_ps;   // dT_sl = T_fl - T_fs
     R c_fref, c_mref, varpi;
     R vcf, vcm;          // varpi c_f,ref and varpi c_m,ref (D2Q5 equilibria, Eqs. B2, B4)
     R zeta[9], eta[9];
@@ -278,18 +279,18 @@ __device__ __forceinline__ void inv(const R* m, R* v) {
 // Eq. 18 (alpha_1 = 1, alpha_2 = -3) minus the rest moments r = (1, -2, 1, 0, ..., 0);
 // rho = 1 + drho.
 template <typename R>
-__device__ __forceinline__ void meq_flow_dev(const StepParams<R>& P, R rho, R drho, R ux, R uy, R* me) {
-    const R ip = P.inv_phi;
-    const R q = R(3) * rho * (ux * ux + uy * uy) * ip;
+__device__ __forceinline__ void meq_flow_dev(R rho, R rip, R drho, R ux, R uy, R* me) {   // rip = rho/phi
+    const R q = R(3) * rip * (ux * ux + uy * uy);
+    const R jx = rho * ux, jy = rho * uy;
     me[0] = drho;
     me[1] = R(-2) * drho + q;
     me[2] = drho - q;
-    me[3] = rho * ux;
-    me[4] = -rho * ux;
-    me[5] = rho * uy;
-    me[6] = -rho * uy;
-    me[7] = rho * (ux * ux - uy * uy) * ip;
-    me[8] = rho * ux * uy * ip;
+    me[3] = jx;
+    me[4] = -jx;
+    me[5] = jy;
+    me[6] = -jy;
+    me[7] = rip * (ux * ux - uy * uy);
+    me[8] = rip * (ux * uy);
 }
 
 // Eq. 34 (D2Q9) / Eq. B2 (D2Q5)
@@ -323,30 +324,30 @@ __device__ __forceinline__ void neq_metal(const StepParams<R>& P, R Tm, R* ne) {
     }
 }
 
-// Eqs. 38-39
+template <typename R>
+__device__ __forceinline__ R sat01(R x) {
+    if constexpr (sizeof(R) == 4) return __saturatef(x);
+    else return fmin(fmax(x, R(0)), R(1));
+}
+
+// Eqs. 38-39 without branches: f_l = clamp((H - H_s)/(H_l - H_s), 0, 1) and
+// T = min(H/c_ps, T_s) + f_l (T_l - T_s) + max(H - H_l, 0)/c_pl, which is
+// H/c_ps below the solidus, T_s + f_l (T_l - T_s) in the mushy zone and
+// T_l + (H - H_l)/c_pl above the liquidus (c_pl = 1).
 template <typename R>
 __device__ __forceinline__ void enthalpy_state(const StepParams<R>& P, R H, R& T, R& fl) {
-    if (H <= P.H_fs) {
-        T = H * P.inv_c_ps;
-        fl = R(0);
-    } else if (H < P.H_fl) {
-        const R d = H - P.H_fs;
-        T = P.T_fs + d * P.mush_slope;
-        fl = d * P.inv_dH;
-    } else {
-        T = P.T_fl + (H - P.H_fl);   // 1/c_pl = 1
-        fl = R(1);
-    }
+    fl = sat01((H - P.H_fs) * P.inv_dH);
+    T = fmin(H * P.inv_c_ps, P.T_fs) + fl * P.dT_sl + fmax(H - P.H_fl, R(0));
 }
 
 // c_f,ref T at equilibrium as a function of the PCM rest population g_0: the
 // inverse of g_0 = H - omega c_f,ref T(H) with T(H) from Eq. 38 (16-bit modes).
 template <typename R>
 __device__ __forceinline__ R pcm_ref(const StepParams<R>& P, R g0) {
-    const R Ts = g0 * P.cr_solid;
-    const R Tm = P.cr_fs + (g0 - P.g0_fs) * P.cr_mushy;
-    const R Tl = P.cr_fl + (g0 - P.g0_fl) * P.cr_liquid;
-    return g0 <= P.g0_fs ? Ts : (g0 < P.g0_fl ? Tm : Tl);
+    // the three branches as in enthalpy_state: solid slope up to g0_fs, a linear
+    // rise of c_f,ref (T_fl - T_fs) across the mushy zone, liquid slope above g0_fl
+    return fmin(g0 * P.cr_solid, P.cr_fs) + sat01((g0 - P.g0_fs) * P.inv_dg0) * P.cr_dsl +
+           fmax(g0 - P.g0_fl, R(0)) * P.cr_liquid;
 }
 
 template <typename R>
@@ -371,7 +372,7 @@ struct NodeState {
     R mp[FLOW ? 9 : 1];  // moments of f+ minus r (after the wall rule)
     R ng[QT], nh[QT];    // moments of g and h (after the wall rule); ng[0] = H, nh[0] = c_pm T_m (high parts)
     R Hlo, Elo;          // low parts of H and c_pm T_m (error-free bookkeeping; 0 where unused)
-    R H, Tf, fl, Tm, rho, drho, ux, uy, Gy;
+    R H, Tf, fl, Tm, rho, drho, ux, uy, um, Gy;   // um = |u|
 };
 
 template <int M>
@@ -502,6 +503,7 @@ __device__ __forceinline__ void macro(const StepParams<typename ModeTraits<M>::R
         if (wall || (P.solid_scheme && n.fl <= R(0.5))) {
             n.ux = R(0);
             n.uy = R(0);
+            n.um = R(0);
         } else {
             // Eq. 24 with sum_i e_i f_i = f_l sum_i e_i f+_i (the equilibrium at rest carries no
             // momentum); without the blend (bounce-back variant) sum_i e_i f_i = sum_i e_i f+_i
@@ -513,12 +515,14 @@ __device__ __forceinline__ void macro(const StepParams<typename ModeTraits<M>::R
             const R den = fast_rcp(P.l0 + fast_sqrt(P.l0sq + P.l1 * vm));   // Eq. 23
             n.ux = vx * den;
             n.uy = vy * den;
+            n.um = vm * den;
         }
     } else {
         n.drho = R(0);
         n.rho = R(1);
         n.ux = R(0);
         n.uy = R(0);
+        n.um = R(0);
         n.Gy = R(0);
     }
 }
@@ -694,8 +698,7 @@ __device__ __forceinline__ void step_node(const StepParams<typename ModeTraits<M
         for (int k = 0; k < 9; ++k) stb<M>(db + k * kChunk, f[k]);
       } else {
         // Eq. 3 at the node's velocity (u = u_b = 0 on walls)
-        const R um = fast_sqrt(n.ux * n.ux + n.uy * n.uy);
-        const R drag = P.drag_lin + P.drag_forch * um;
+        const R drag = P.drag_lin + P.drag_forch * n.um;
         const R Fx = -drag * n.ux;
         const R Fy = -drag * n.uy + P.phi * n.Gy;
         // blended moments (Eq. 20 in moment space, deviation form); no blend in the
@@ -708,13 +711,13 @@ __device__ __forceinline__ void step_node(const StepParams<typename ModeTraits<M
         m[0] += sol;
         m[1] -= R(2) * sol;
         m[2] += sol;
+        const R rho = n.rho, rip = rho * P.inv_phi;
         R me[9];
-        meq_flow_dev(P, n.rho, n.drho, n.ux, n.uy, me);
-        const R ip = P.inv_phi, rho = n.rho;
+        meq_flow_dev(rho, rip, n.drho, n.ux, n.uy, me);
         const R uF = n.ux * Fx + n.uy * Fy;
-        const R S[9] = {R(0), rho * R(6) * uF * ip, -rho * R(6) * uF * ip, rho * Fx, -rho * Fx,
-                        rho * Fy, -rho * Fy, rho * R(2) * (n.ux * Fx - n.uy * Fy) * ip,
-                        rho * (n.ux * Fy + n.uy * Fx) * ip};
+        const R s1 = R(6) * rip * uF, sx = rho * Fx, sy = rho * Fy;
+        const R S[9] = {R(0), s1, -s1, sx, -sx, sy, -sy, R(2) * rip * (n.ux * Fx - n.uy * Fy),
+                        rip * (n.ux * Fy + n.uy * Fx)};
         // Eq. 14: the rates of Sec. III C are constants (s_rho = s_j = 1, s_e = s_eps =
         // 1.1, s_q = 1.2); only s_v = s[7] = s[8] depends on the run.  Where s = 1 the
         // result is m^eq + S/2 whatever the blend gave (rho: m^eq = delta_rho, S = 0)
