@@ -264,6 +264,10 @@ lbmk::StepParams<R> make_params(const lbm_handle* h, int from) {
         const double kappa = d.c_mref / (1.0 - om * d.c_mref);
         P.kappa_m = (R)kappa;
         for (int k = 0; k < 9; ++k) P.wk_move[k] = (R)((Q == 9 ? w9[k] : 0.25 * p.varpi) * kappa);
+        for (int k = 0; k < 9; ++k) {
+            P.wmv[k] = {P.w_move[k], P.wk_move[k]};
+            P.nwmv[k] = {-P.w_move[k], -P.wk_move[k]};
+        }
         P.om_cf = (R)(om * d.c_fref);
         P.rest_m = (R)(1.0 - om * d.c_mref);
     }
@@ -283,6 +287,7 @@ lbmk::StepParams<R> make_params(const lbm_handle* h, int from) {
         P.s[k] = (R)d.s[k];
         P.zeta[k] = (R)d.zeta[k];
         P.eta[k] = (R)d.eta[k];
+        P.nrate[k] = {-(R)d.zeta[k], -(R)d.eta[k]};
     }
     P.H_fs = (R)d.H_fs;
     P.H_fl = (R)d.H_fl;

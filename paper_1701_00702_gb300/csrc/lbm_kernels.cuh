@@ -116,6 +116,52 @@ struct Chunk {
     static constexpr int bytes = wide_off + PL::wide * kChunk * (int)sizeof(float);
 };
 
+// A pair of values that go through the same arithmetic: the PCM and metal
+// lattices' populations and moments (x: PCM, y: metal).  With FP32 arithmetic
+// a pair operation is one packed instruction (the .f32x2 add, multiply and
+// fused multiply-add of sm_100 and later), which halves the issue slots of
+// that arithmetic; FP64 keeps two scalar operations.  Each lane is rounded as
+// the scalar operation would be.
+template <typename R>
+struct alignas(2 * sizeof(R)) V2 {
+    R x, y;
+};
+
+template <typename R>
+__device__ __forceinline__ V2<R> add2(V2<R> a, V2<R> b) {
+    if constexpr (sizeof(R) == 4) {
+        const float2 r = __fadd2_rn(make_float2(a.x, a.y), make_float2(b.x, b.y));
+        return {r.x, r.y};
+    } else {
+        return {a.x + b.x, a.y + b.y};
+    }
+}
+
+template <typename R>
+__device__ __forceinline__ V2<R> mul2(V2<R> a, V2<R> b) {
+    if constexpr (sizeof(R) == 4) {
+        const float2 r = __fmul2_rn(make_float2(a.x, a.y), make_float2(b.x, b.y));
+        return {r.x, r.y};
+    } else {
+        return {a.x * b.x, a.y * b.y};
+    }
+}
+
+template <typename R>
+__device__ __forceinline__ V2<R> fma2(V2<R> a, V2<R> b, V2<R> c) {   // a b + c, one rounding per lane
+    if constexpr (sizeof(R) == 4) {
+        const float2 r = __ffma2_rn(make_float2(a.x, a.y), make_float2(b.x, b.y), make_float2(c.x, c.y));
+        return {r.x, r.y};
+    } else {
+        return {fma(a.x, b.x, c.x), fma(a.y, b.y, c.y)};
+    }
+}
+
+template <typename R>
+__device__ __forceinline__ V2<R> sub2(V2<R> a, V2<R> b) {   // a - b, one rounding per lane
+    return fma2(b, V2<R>{R(-1), R(-1)}, a);
+}
+
 // Per-run constants, passed by value (__grid_constant__).
 template <typename R>
 struct StepParams {
@@ -149,6 +195,9 @@ struct StepParams {
     R c_fref, c_mref, varpi;
     R vcf, vcm;          // varpi c_f,ref and varpi c_m,ref (D2Q5 equilibria, Eqs. B2, B4)
     R zeta[9], eta[9];
+    V2<R> nrate[9];      // (-zeta_k, -eta_k): PCM and metal relaxation rates, negated
+    V2<R> nwmv[9];       // (-w'_k, -w'_k kappa_m): 16-bit mover references per unit of (ref, h_0)
+    V2<R> wmv[9];        // (w'_k, w'_k kappa_m)
     R a_f, a_m;          // h_v/(phi rho_l), h_v/((1 - phi) rho_m)
     R x_pm;              // -a_f/a_m = -(1 - phi) rho_m/(phi rho_l): PCM source per unit of metal source
     // Eq. 9 variant: PCM rates from the node's liquid fraction
@@ -262,6 +311,59 @@ __device__ __forceinline__ void f_from_m5(const R* n, R* g) {
     g[4] = R(-0.5) * n[2] + q;
 }
 
+// Eq. B1 and its inverse on (PCM, metal) pairs, same rounding order as above
+// except n_0 = g_0 + ((g_1 + g_3) + (g_2 + g_4)).
+template <typename R>
+__device__ __forceinline__ void m_from_f5(const V2<R>* g, V2<R>* n) {
+    const V2<R> a = add2(g[1], g[3]), b = add2(g[2], g[4]);
+    n[1] = sub2(g[1], g[3]);
+    n[2] = sub2(g[2], g[4]);
+    n[3] = add2(a, b);
+    n[4] = sub2(a, b);
+    n[0] = add2(g[0], n[3]);
+}
+
+template <typename R>
+__device__ __forceinline__ void f_from_m5(const V2<R>* n, V2<R>* g) {
+    const V2<R> qu = {R(0.25), R(0.25)}, h = {R(0.5), R(0.5)}, mh = {R(-0.5), R(-0.5)};
+    const V2<R> p = mul2(add2(n[3], n[4]), qu), q = mul2(sub2(n[3], n[4]), qu);
+    g[0] = sub2(n[0], n[3]);
+    g[1] = fma2(h, n[1], p);
+    g[3] = fma2(mh, n[1], p);
+    g[2] = fma2(h, n[2], q);
+    g[4] = fma2(mh, n[2], q);
+}
+
+template <typename R, int Q>
+__device__ __forceinline__ void fwd2(const V2<R>* v, V2<R>* m) {
+    if constexpr (Q == 5) {
+        m_from_f5(v, m);
+    } else {
+        R a[9], b[9], ma[9], mb[9];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) { a[k] = v[k].x; b[k] = v[k].y; }
+        m_from_f9(a, ma);
+        m_from_f9(b, mb);
+#pragma unroll
+        for (int k = 0; k < 9; ++k) m[k] = {ma[k], mb[k]};
+    }
+}
+
+template <typename R, int Q>
+__device__ __forceinline__ void inv2(const V2<R>* m, V2<R>* v) {
+    if constexpr (Q == 5) {
+        f_from_m5(m, v);
+    } else {
+        R a[9], b[9], va[9], vb[9];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) { a[k] = m[k].x; b[k] = m[k].y; }
+        f_from_m9(a, va);
+        f_from_m9(b, vb);
+#pragma unroll
+        for (int k = 0; k < 9; ++k) v[k] = {va[k], vb[k]};
+    }
+}
+
 template <typename R, int Q>
 __device__ __forceinline__ void fwd(const R* v, R* m) {
     if constexpr (Q == 9) m_from_f9(v, m); else m_from_f5(v, m);
@@ -370,7 +472,7 @@ template <int M, int QT, bool FLOW>
 struct NodeState {
     using R = typename ModeTraits<M>::R;
     R mp[FLOW ? 9 : 1];  // moments of f+ minus r (after the wall rule)
-    R ng[QT], nh[QT];    // moments of g and h (after the wall rule); ng[0] = H, nh[0] = c_pm T_m (high parts)
+    V2<R> th[QT];        // moments of (g, h) (after the wall rule); th[0] = (H, c_pm T_m) (high parts)
     R Hlo, Elo;          // low parts of H and c_pm T_m (error-free bookkeeping; 0 where unused)
     R H, Tf, fl, Tm, rho, drho, ux, uy, um, Gy;   // um = |u|
 };
@@ -453,7 +555,7 @@ __device__ __forceinline__ void pull_moments(const StepParams<typename ModeTrait
         }
         m_from_f9(f, n.mp);
     }
-    R g[QT], h[QT];
+    V2<R> t[QT];   // (g_q, h_q)
     if constexpr (kSplit<M>) {
         const float* sw[QT];   // the source node's element in wide plane 0 (PCM rest; metal rest follows)
 #pragma unroll
@@ -461,29 +563,28 @@ __device__ __forceinline__ void pull_moments(const StepParams<typename ModeTrait
             const int dw = col_off<M, QT, FLOW, true>(ci[q] == 0 ? xm : (ci[q] == 1 ? xs : xp)) - c0;
             sw[q] = reinterpret_cast<const float*>(row[ri[q]] + dw);
         }
-        g[0] = __ldg(sw[0]);
-        h[0] = __ldg(sw[0] + kChunk);
+        t[0] = {__ldg(sw[0]), __ldg(sw[0] + kChunk)};
 #pragma unroll
         for (int q = 1; q < QT; ++q) {   // deviation + reference of the sending node
-            g[q] = ldb<M>(sb[q] + PL::pcm(q) * kChunk) + P.w_move[q] * pcm_ref(P, __ldg(sw[q]));
-            h[q] = ldb<M>(sb[q] + PL::met(q) * kChunk) + P.wk_move[q] * __ldg(sw[q] + kChunk);
+            const V2<R> dev = {ldb<M>(sb[q] + PL::pcm(q) * kChunk), ldb<M>(sb[q] + PL::met(q) * kChunk)};
+            const V2<R> ref = {pcm_ref(P, __ldg(sw[q])), __ldg(sw[q] + kChunk)};
+            t[q] = fma2(P.wmv[q], ref, dev);
         }
     } else {
 #pragma unroll
-        for (int q = 0; q < QT; ++q) {
-            g[q] = ldb<M>(sb[q] + PL::pcm(q) * kChunk);
-            h[q] = ldb<M>(sb[q] + PL::met(q) * kChunk);
-        }
+        for (int q = 0; q < QT; ++q) t[q] = {ldb<M>(sb[q] + PL::pcm(q) * kChunk), ldb<M>(sb[q] + PL::met(q) * kChunk)};
     }
-    fwd<R, QT>(g, n.ng);
-    fwd<R, QT>(h, n.nh);
+    fwd2<R, QT>(t, n.th);
     n.Hlo = R(0);
     n.Elo = R(0);
     if constexpr (kComp<M>) {
         // H = (g_0 hi + g_0 lo) + sum of movers, without rounding loss
         const float lo = ldb<M>(sb[0] + PL::lo * kChunk);
+        float g[QT];
+#pragma unroll
+        for (int q = 0; q < QT; ++q) g[q] = t[q].x;
         const FF H = ff_accumulate<QT>(FF{g[0], lo}, g, 1.0f);
-        n.ng[0] = H.hi;
+        n.th[0].x = H.hi;
         n.Hlo = H.lo;
     }
 }
@@ -493,9 +594,9 @@ template <int M, int QT, bool FLOW>
 __device__ __forceinline__ void macro(const StepParams<typename ModeTraits<M>::R>& P, NodeState<M, QT, FLOW>& n,
                                       bool wall) {
     using R = typename ModeTraits<M>::R;
-    n.H = n.ng[0];
+    n.H = n.th[0].x;
     enthalpy_state(P, n.H, n.Tf, n.fl);
-    n.Tm = n.nh[0];   // h_0 moment = c_pm T_m, c_pm = 1
+    n.Tm = n.th[0].y;   // h_0 moment = c_pm T_m, c_pm = 1
     if constexpr (FLOW) {
         n.drho = n.mp[0];
         n.rho = R(1) + n.drho;
@@ -571,47 +672,46 @@ __device__ __forceinline__ void node_state(const StepParams<typename ModeTraits<
     neq_pcm<R, QT>(P, Hb, Tb, R(0), R(0), a);
     neq_pcm<R, QT>(P, n.H, n.Tf, n.ux, n.uy, b);
 #pragma unroll
-    for (int k = 1; k < QT; ++k) n.ng[k] += a[k] - b[k];
+    for (int k = 1; k < QT; ++k) n.th[k].x += a[k] - b[k];
     if (dirichlet) {   // n_0 = H_b exactly (adiabatic: n_0 = H(x_f), unchanged)
-        n.ng[0] = P.wall_H[side];
+        n.th[0].x = P.wall_H[side];
         n.Hlo = P.wall_H_lo[side];
     }
     neq_metal<R, QT>(P, Tmb, a);
     neq_metal<R, QT>(P, n.Tm, b);
     if constexpr (kSplit<M>) {
 #pragma unroll
-        for (int k = 1; k < QT; ++k) n.nh[k] += a[k] - b[k];
+        for (int k = 1; k < QT; ++k) n.th[k].y += a[k] - b[k];
         if (dirichlet) {   // c_pm T_m = c_pm T_b exactly (c_pm = 1)
-            n.nh[0] = P.wall_T[side];
+            n.th[0].y = P.wall_T[side];
             n.Elo = P.wall_T_lo[side];
         }
     } else {
 #pragma unroll
-        for (int k = 0; k < QT; ++k) n.nh[k] += a[k] - b[k];
+        for (int k = 0; k < QT; ++k) n.th[k].y += a[k] - b[k];
     }
     macro<M, QT, FLOW>(P, n, true);
 }
 
-// Post-collision thermal populations from their moments.  n0 is the
-// conserved moment after the source (hi, lo).  The rest population is the
-// remainder n0 - sum of the moving populations as they are stored, so the
-// stored populations carry the enthalpy (internal energy) that the collision
-// produced: the FP32 PCM rest population to float-float accuracy, the FP32
-// metal one to one rounding, the 16-bit forms to FP32 rounding as readers
-// decode them, FP64 to FP64 rounding.
-// db and dw point at the node's element in bulk plane 0 and wide plane 0 of the
-// next copy; rest_plane is a wide plane in the 16-bit modes, a bulk plane
-// otherwise.
-template <int M, int QT>
+// Post-collision thermal populations of both lattices from their moments
+// (x: PCM, y: metal).  n0g (hi, lo) and n0h are the conserved moments after the
+// sources.  Each rest population is the remainder n_0 - sum of the moving
+// populations as they are stored, so the stored populations carry the enthalpy
+// (internal energy) that the collision produced: the FP32 PCM rest population
+// to float-float accuracy, the FP32 metal one to one rounding, the 16-bit forms
+// to FP32 rounding as readers decode them, FP64 to FP64 rounding.  db and dw
+// point at the node's element in bulk plane 0 and wide plane 0 of the next copy.
+template <int M, int QT, bool FLOW>
 __device__ __forceinline__ void store_thermal(const StepParams<typename ModeTraits<M>::R>& P,
-                                              typename ModeTraits<M>::R* nm, typename ModeTraits<M>::R n0hi,
-                                              typename ModeTraits<M>::R n0lo, typename ModeTraits<M>::B* db,
-                                              float* dw, int rest_plane, int mover_plane1, int lo_plane,
-                                              bool is_pcm) {
+                                              V2<typename ModeTraits<M>::R>* nm, typename ModeTraits<M>::R n0ghi,
+                                              typename ModeTraits<M>::R n0glo, typename ModeTraits<M>::R n0h,
+                                              typename ModeTraits<M>::B* db, float* dw) {
     using R = typename ModeTraits<M>::R;
-    R v[QT];
-    nm[0] = n0hi;
-    inv<R, QT>(nm, v);
+    using B = typename ModeTraits<M>::B;
+    using PL = Planes<M, QT, FLOW>;
+    V2<R> v[QT];
+    nm[0] = {n0ghi, n0h};
+    inv2<R, QT>(nm, v);
     if constexpr (kSplit<M>) {
         // 16-bit deviations from the reference of the provisional rest population,
         // then the rest population readers will see the balance with.  Readers
@@ -622,44 +722,43 @@ __device__ __forceinline__ void store_thermal(const StepParams<typename ModeTrai
         // B5 for the metal), the solution is that of H = Y: g_0 = Y - omega
         // c_ref T(Y), whose reference is c_ref T(Y).  The stored populations as
         // read then carry n_0 to FP32 rounding.
-        using B = typename ModeTraits<M>::B;
-        const float g0a = v[0];   // provisional rest population (only picks the reference)
-        const float ref = is_pcm ? pcm_ref(P, g0a) : P.kappa_m * g0a;
-        float sd = 0.0f;
+        const V2<float> ref = {pcm_ref(P, v[0].x), v[0].y};   // v[0]: provisional rest populations
+        V2<float> sd;
 #pragma unroll
         for (int k = 1; k < QT; ++k) {
-            const B b = from_f<B>(v[k] - P.w_move[k] * ref);
-            db[(mover_plane1 + k - 1) * kChunk] = b;
-            sd += to_f(b);
+            const V2<float> e = fma2(P.nwmv[k], ref, v[k]);
+            const B bg = from_f<B>(e.x), bh = from_f<B>(e.y);
+            db[PL::pcm(k) * kChunk] = bg;
+            db[PL::met(k) * kChunk] = bh;
+            const V2<float> d = {to_f(bg), to_f(bh)};
+            sd = k == 1 ? d : add2(sd, d);
         }
-        const float Y = n0hi - sd;
-        float rest;
-        if (is_pcm) {
-            float T, fl;
-            enthalpy_state(P, Y, T, fl);
-            rest = Y - P.om_cf * T;
-        } else {
-            rest = Y * P.rest_m;
-        }
-        dw[rest_plane * kChunk] = rest;
+        const V2<float> Y = sub2(V2<float>{n0ghi, n0h}, sd);
+        float T, fl;
+        enthalpy_state(P, Y.x, T, fl);
+        dw[0] = Y.x - P.om_cf * T;
+        dw[kChunk] = Y.y * P.rest_m;
     } else {
 #pragma unroll
-        for (int k = 1; k < QT; ++k) stb<M>(db + (mover_plane1 + k - 1) * kChunk, v[k]);
-        bool pair = false;   // the FP32 PCM rest population is a float-float pair
-        if constexpr (kComp<M>) {
-            if (is_pcm) {
-                const FF r = ff_accumulate<QT>(FF{n0hi, n0lo}, v, -1.0f);
-                stb<M>(db + rest_plane * kChunk, r.hi);
-                stb<M>(db + lo_plane * kChunk, r.lo);
-                pair = true;
-            }
+        for (int k = 1; k < QT; ++k) {
+            stb<M>(db + PL::pcm(k) * kChunk, v[k].x);
+            stb<M>(db + PL::met(k) * kChunk, v[k].y);
         }
-        if (!pair) {
-            R sm = v[1];
+        V2<R> sm = v[1];
 #pragma unroll
-            for (int k = 2; k < QT; ++k) sm += v[k];
-            stb<M>(db + rest_plane * kChunk, n0hi - sm);
+        for (int k = 2; k < QT; ++k) sm = add2(sm, v[k]);
+        const V2<R> rest = sub2(V2<R>{n0ghi, n0h}, sm);
+        if constexpr (kComp<M>) {   // the FP32 PCM rest population is a float-float pair
+            float vg[QT];
+#pragma unroll
+            for (int k = 0; k < QT; ++k) vg[k] = v[k].x;
+            const FF r = ff_accumulate<QT>(FF{n0ghi, n0glo}, vg, -1.0f);
+            stb<M>(db + PL::pcm(0) * kChunk, r.hi);
+            stb<M>(db + PL::lo * kChunk, r.lo);
+        } else {
+            stb<M>(db + PL::pcm(0) * kChunk, rest.x);
         }
+        stb<M>(db + PL::met(0) * kChunk, rest.y);
     }
 }
 
@@ -747,51 +846,49 @@ __device__ __forceinline__ void step_node(const StepParams<typename ModeTraits<M
     // by the heat capacities (S_PCM = -(a_f/a_m) S_metal, Eqs. 36, 47), so an
     // exchange that the metal's rounding drops moves no energy into the PCM
     R hm_base;
-    if constexpr (kSplit<M>) hm_base = n.nh[0];
-    else hm_base = n.nh[0] - P.eta[0] * (n.nh[0] - n.Tm);
+    if constexpr (kSplit<M>) hm_base = n.th[0].y;
+    else hm_base = n.th[0].y - P.eta[0] * (n.th[0].y - n.Tm);
     const R hm = hm_base + S_met;
     const R S_pcm = (hm - hm_base) * P.x_pm;
 
     {
-        R ne[QT];
-        neq_pcm<R, QT>(P, n.H, n.Tf, n.ux, n.uy, ne);
+        // PCM (Eq. 32) and metal (Eq. 43) collisions side by side
+        R neg[QT], nem[QT];
+        neq_pcm<R, QT>(P, n.H, n.Tf, n.ux, n.uy, neg);
+        neq_metal<R, QT>(P, n.Tm, nem);
+        V2<R> nr[QT];
+#pragma unroll
+        for (int k = 1; k < QT; ++k) nr[k] = P.nrate[k];
         if (PH && P.phase_k) {
             // Eq. 9 at the node's liquid fraction -> zeta_alpha (Eq. A19) -> zeta_e (Eq. 53)
             const R za = fast_rcp(R(0.5) + P.ks_c + n.fl * (P.kl_c - P.ks_c));
 #pragma unroll
-            for (int k = 1; k < QT; ++k) n.ng[k] -= (P.zr_a[k] + P.zr_b[k] * za) * (n.ng[k] - ne[k]);
-        } else {
+            for (int k = 1; k < QT; ++k) nr[k].x = -(P.zr_a[k] + P.zr_b[k] * za);
+        }
 #pragma unroll
-            for (int k = 1; k < QT; ++k) n.ng[k] -= P.zeta[k] * (n.ng[k] - ne[k]);
+        for (int k = 1; k < QT; ++k) {
+            // both equilibria vanish for k = 4 (D2Q5) and k = 7, 8 (D2Q9)
+            const bool zero = QT == 5 ? k == 4 : k >= 7;
+            const V2<R> d = zero ? n.th[k] : sub2(n.th[k], V2<R>{neg[k], nem[k]});
+            n.th[k] = fma2(nr[k], d, n.th[k]);
         }
         if constexpr (QT == 9) {
-            n.ng[1] -= R(2) * S_pcm; n.ng[2] += S_pcm;
+            n.th[1] = fma2(V2<R>{R(-2), R(-2)}, V2<R>{S_pcm, S_met}, n.th[1]);
+            n.th[2] = add2(n.th[2], V2<R>{S_pcm, S_met});
         } else {
-            n.ng[3] += P.varpi * S_pcm;
+            n.th[3] = fma2(V2<R>{P.varpi, P.varpi}, V2<R>{S_pcm, S_met}, n.th[3]);
         }
         // n_0* = H + S_PCM (n_0 is conserved up to the source, Eq. 32)
         R hi, lo;
         if constexpr (kComp<M>) {
-            const FF n0 = ff_add(FF{n.ng[0], n.Hlo}, S_pcm);
+            const FF n0 = ff_add(FF{n.th[0].x, n.Hlo}, S_pcm);
             hi = n0.hi;
             lo = n0.lo;
         } else {
-            hi = n.ng[0] + S_pcm;
+            hi = n.th[0].x + S_pcm;
             lo = R(0);
         }
-        store_thermal<M, QT>(P, n.ng, hi, lo, db, dw, kSplit<M> ? 0 : PL::pcm(0), PL::pcm(1), PL::lo, true);
-    }
-    {
-        R ne[QT];
-        neq_metal<R, QT>(P, n.Tm, ne);
-#pragma unroll
-        for (int k = 1; k < QT; ++k) n.nh[k] -= P.eta[k] * (n.nh[k] - ne[k]);
-        if constexpr (QT == 9) {
-            n.nh[1] -= R(2) * S_met; n.nh[2] += S_met;
-        } else {
-            n.nh[3] += P.varpi * S_met;
-        }
-        store_thermal<M, QT>(P, n.nh, hm, R(0), db, dw, kSplit<M> ? 1 : PL::met(0), PL::met(1), PL::lo, false);
+        store_thermal<M, QT, FLOW>(P, n.th, hi, lo, hm, db, dw);
     }
     P.dT[o] = dTn;
 
