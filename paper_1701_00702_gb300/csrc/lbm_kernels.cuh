@@ -311,6 +311,46 @@ __device__ __forceinline__ void f_from_m5(const R* n, R* g) {
     g[4] = R(-0.5) * n[2] + q;
 }
 
+// Eq. 13 on the population pairs (f1, f2), (f3, f4), (f5, f6), (f7, f8) (the
+// D2Q9 order of Eq. 11): m_0 and the moment pairs (e, eps), (j_x, j_y),
+// (q_x, q_y), (p_xx, p_xy).
+template <typename R>
+__device__ __forceinline__ void m_from_f9p(R f0, const V2<R>* F, R& m0, V2<R>* m) {
+    const V2<R> A = add2(F[0], F[1]);   // (f1 + f3, f2 + f4)
+    const V2<R> D = sub2(F[0], F[1]);   // (f1 - f3, f2 - f4)
+    const V2<R> B = add2(F[2], F[3]);   // (f5 + f7, f6 + f8)
+    const V2<R> E = sub2(F[2], F[3]);   // (f5 - f7, f6 - f8)
+    const R s14 = A.x + A.y, s58 = B.x + B.y;
+    const V2<R> a = {E.x - E.y, E.x + E.y};   // (f5 - f6 - f7 + f8, f5 + f6 - f7 - f8)
+    m0 = f0 + s14 + s58;
+    m[0] = {R(-4) * f0 - s14 + R(2) * s58, R(4) * f0 - R(2) * s14 + s58};
+    m[1] = add2(D, a);
+    m[2] = fma2(V2<R>{R(-2), R(-2)}, D, a);
+    m[3] = {A.x - A.y, B.x - B.y};
+}
+
+// f = M^-1 m on the same pairs, every f scaled by SC (as f_from_m9).
+template <typename R, int SC = 1>
+__device__ __forceinline__ void f_from_m9p(R m0, const V2<R>* m, R& f0, V2<R>* F) {
+    constexpr double s = SC;
+    const R A = m0 * R(s / 9.0);
+    const V2<R> BC = mul2(m[0], V2<R>{R(s / 36.0), R(s / 36.0)});   // (B, C)
+    const V2<R> D = mul2(m[1], V2<R>{R(s / 6.0), R(s / 6.0)});      // (DX, DY)
+    const V2<R> Q = mul2(m[2], V2<R>{R(s / 12.0), R(s / 12.0)});    // (QX, QY)
+    const V2<R> PS = mul2(m[3], V2<R>{R(s * 0.25), R(s * 0.25)});   // (P, S)
+    f0 = A - R(4) * BC.x + R(4) * BC.y;
+    const R b1 = A - BC.x - R(2) * BC.y;
+    const R b5 = A + R(2) * BC.x + BC.y;
+    const V2<R> T = fma2(V2<R>{R(-2), R(-2)}, Q, D);   // (DX - 2 QX, DY - 2 QY)
+    const V2<R> X = add2(D, Q);                         // (DX + QX, DY + QY)
+    const V2<R> bp = {b1 + PS.x, b1 - PS.x};
+    F[0] = add2(bp, T);                                 // (f1, f2)
+    F[1] = sub2(bp, T);                                 // (f3, f4)
+    const V2<R> G = {b5 + PS.y, b5 - PS.y}, H = {X.x + X.y, X.y - X.x};
+    F[2] = add2(G, H);                                  // (f5, f6)
+    F[3] = sub2(G, H);                                  // (f7, f8)
+}
+
 // Eq. B1 and its inverse on (PCM, metal) pairs, same rounding order as above
 // except n_0 = g_0 + ((g_1 + g_3) + (g_2 + g_4)).
 template <typename R>
@@ -377,23 +417,6 @@ __device__ __forceinline__ void inv(const R* m, R* v) {
 // ---------------------------------------------------------------------------
 // Equilibrium moments
 // ---------------------------------------------------------------------------
-
-// Eq. 18 (alpha_1 = 1, alpha_2 = -3) minus the rest moments r = (1, -2, 1, 0, ..., 0);
-// rho = 1 + drho.
-template <typename R>
-__device__ __forceinline__ void meq_flow_dev(R rho, R rip, R drho, R ux, R uy, R* me) {   // rip = rho/phi
-    const R q = R(3) * rip * (ux * ux + uy * uy);
-    const R jx = rho * ux, jy = rho * uy;
-    me[0] = drho;
-    me[1] = R(-2) * drho + q;
-    me[2] = drho - q;
-    me[3] = jx;
-    me[4] = -jx;
-    me[5] = jy;
-    me[6] = -jy;
-    me[7] = rip * (ux * ux - uy * uy);
-    me[8] = rip * (ux * uy);
-}
 
 // Eq. 34 (D2Q9) / Eq. B2 (D2Q5)
 template <typename R, int Q>
@@ -488,6 +511,18 @@ __device__ __forceinline__ void stb(typename ModeTraits<M>::B* p, R v) {
     *p = from_f<B>(v);
 }
 
+// The nine flow populations of one node (f_0 and the pairs of f_from_m9p).
+template <int M>
+__device__ __forceinline__ void store_flow(typename ModeTraits<M>::B* db, typename ModeTraits<M>::R f0,
+                                           const V2<typename ModeTraits<M>::R>* F) {
+    stb<M>(db, f0);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        stb<M>(db + (2 * j + 1) * kChunk, F[j].x);
+        stb<M>(db + (2 * j + 2) * kChunk, F[j].y);
+    }
+}
+
 // Byte offset, within a state copy, of the chunk holding node (x, y).
 template <int M, int QT, bool FLOW, typename R>
 __device__ __forceinline__ long long chunk_at(const StepParams<R>& P, int x, int y) {
@@ -547,13 +582,23 @@ __device__ __forceinline__ void pull_moments(const StepParams<typename ModeTrait
 #pragma unroll
     for (int q = 0; q < ND; ++q) sb[q] = reinterpret_cast<const B*>(row[ri[q]] + dc[ci[q]]);
     if constexpr (FLOW) {
-        R f[9];
+        R f0 = ldb<M>(sb[0]);
+        V2<R> F[4];
 #pragma unroll
-        for (int q = 0; q < 9; ++q) {
-            f[q] = ldb<M>(sb[q] + q * kChunk);
-            if constexpr (M == MODE_F16) f[q] *= R(1.0 / 1024.0);
+        for (int j = 0; j < 4; ++j)
+            F[j] = {ldb<M>(sb[2 * j + 1] + (2 * j + 1) * kChunk), ldb<M>(sb[2 * j + 2] + (2 * j + 2) * kChunk)};
+        if constexpr (M == MODE_F16) {
+            constexpr R is = R(1.0 / 1024.0);
+            f0 *= is;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) F[j] = mul2(F[j], V2<R>{is, is});
         }
-        m_from_f9(f, n.mp);
+        V2<R> m[4];
+        m_from_f9p(f0, F, n.mp[0], m);
+        n.mp[1] = m[0].x; n.mp[2] = m[0].y;
+        n.mp[3] = m[1].x; n.mp[5] = m[1].y;
+        n.mp[4] = m[2].x; n.mp[6] = m[2].y;
+        n.mp[7] = m[3].x; n.mp[8] = m[3].y;
     }
     V2<R> t[QT];   // (g_q, h_q)
     if constexpr (kSplit<M>) {
@@ -790,49 +835,48 @@ __device__ __forceinline__ void step_node(const StepParams<typename ModeTraits<M
       if (P.solid_scheme && n.fl <= R(0.5)) {
         // bounce-back solid node: f*_i = f+_opp(i); reversing every link flips the
         // sign of the odd moments (j, q) and keeps the even ones (deviation form too)
-        n.mp[3] = -n.mp[3]; n.mp[4] = -n.mp[4]; n.mp[5] = -n.mp[5]; n.mp[6] = -n.mp[6];
-        R f[9];
-        f_from_m9<R, kFlowScale<M>>(n.mp, f);
-#pragma unroll
-        for (int k = 0; k < 9; ++k) stb<M>(db + k * kChunk, f[k]);
+        const V2<R> m[4] = {{n.mp[1], n.mp[2]}, {-n.mp[3], -n.mp[5]}, {-n.mp[4], -n.mp[6]}, {n.mp[7], n.mp[8]}};
+        R f0;
+        V2<R> F[4];
+        f_from_m9p<R, kFlowScale<M>>(n.mp[0], m, f0, F);
+        store_flow<M>(db, f0, F);
       } else {
         // Eq. 3 at the node's velocity (u = u_b = 0 on walls)
         const R drag = P.drag_lin + P.drag_forch * n.um;
-        const R Fx = -drag * n.ux;
-        const R Fy = -drag * n.uy + P.phi * n.Gy;
+        const V2<R> U = {n.ux, n.uy};
+        const V2<R> F = fma2(V2<R>{-drag, -drag}, U, V2<R>{R(0), P.phi * n.Gy});   // (F_x, F_y)
         // blended moments (Eq. 20 in moment space, deviation form); no blend in the
-        // bounce-back variant
-        R m[9];
+        // bounce-back variant.  Pairs (e, eps), (j_x, j_y), (q_x, q_y), (p_xx, p_xy)
         const R fb = P.solid_scheme ? R(1) : n.fl;
         const R sol = (R(1) - fb) * n.drho;
-#pragma unroll
-        for (int k = 0; k < 9; ++k) m[k] = fb * n.mp[k];
-        m[0] += sol;
-        m[1] -= R(2) * sol;
-        m[2] += sol;
-        const R rho = n.rho, rip = rho * P.inv_phi;
-        R me[9];
-        meq_flow_dev(rho, rip, n.drho, n.ux, n.uy, me);
-        const R uF = n.ux * Fx + n.uy * Fy;
-        const R s1 = R(6) * rip * uF, sx = rho * Fx, sy = rho * Fy;
-        const R S[9] = {R(0), s1, -s1, sx, -sx, sy, -sy, R(2) * rip * (n.ux * Fx - n.uy * Fy),
-                        rip * (n.ux * Fy + n.uy * Fx)};
+        const V2<R> FB = {fb, fb};
+        V2<R> m12 = fma2(FB, V2<R>{n.mp[1], n.mp[2]}, V2<R>{R(-2) * sol, sol});
+        V2<R> m46 = mul2(FB, V2<R>{n.mp[4], n.mp[6]});
+        V2<R> m78 = mul2(FB, V2<R>{n.mp[7], n.mp[8]});
+        // equilibria (Eq. 18, deviation form) and forcing moments (Eq. 19); the q
+        // pair's equilibrium and forcing are the negated j pair's
+        const R rho = n.rho, rip = rho * P.inv_phi, drho = n.drho;
+        const R q = R(3) * rip * (n.ux * n.ux + n.uy * n.uy);
+        const V2<R> me12 = {R(-2) * drho + q, drho - q};
+        const V2<R> J = mul2(V2<R>{rho, rho}, U);
+        const V2<R> me78 = mul2(V2<R>{rip, rip}, V2<R>{n.ux * n.ux - n.uy * n.uy, n.ux * n.uy});
+        const R s1 = R(6) * rip * (n.ux * F.x + n.uy * F.y);
+        const V2<R> RF = mul2(V2<R>{rho, rho}, F);
+        const V2<R> S78 = mul2(V2<R>{rip, rip}, V2<R>{R(2) * (n.ux * F.x - n.uy * F.y), n.ux * F.y + n.uy * F.x});
         // Eq. 14: the rates of Sec. III C are constants (s_rho = s_j = 1, s_e = s_eps =
         // 1.1, s_q = 1.2); only s_v = s[7] = s[8] depends on the run.  Where s = 1 the
         // result is m^eq + S/2 whatever the blend gave (rho: m^eq = delta_rho, S = 0)
-        constexpr double sk[7] = {1.0, 1.1, 1.1, 1.0, 1.2, 1.0, 1.2};
-        m[0] = me[0];
-#pragma unroll
-        for (int k = 1; k < 7; ++k)
-            m[k] = sk[k] == 1.0 ? me[k] + R(0.5) * S[k]
-                                : m[k] - R(sk[k]) * (m[k] - me[k]) + R(1.0 - 0.5 * sk[k]) * S[k];
+        m12 = fma2(V2<R>{R(0.45), R(0.45)}, V2<R>{s1, -s1},
+                   fma2(V2<R>{R(-1.1), R(-1.1)}, sub2(m12, me12), m12));
+        const V2<R> m35 = fma2(V2<R>{R(0.5), R(0.5)}, RF, J);
+        m46 = fma2(V2<R>{R(-0.4), R(-0.4)}, RF, fma2(V2<R>{R(-1.2), R(-1.2)}, add2(m46, J), m46));
         const R sv = P.s[7], hv = R(1) - R(0.5) * sv;
-        m[7] = m[7] - sv * (m[7] - me[7]) + hv * S[7];
-        m[8] = m[8] - sv * (m[8] - me[8]) + hv * S[8];
-        R f[9];
-        f_from_m9<R, kFlowScale<M>>(m, f);
-#pragma unroll
-        for (int k = 0; k < 9; ++k) stb<M>(db + k * kChunk, f[k]);
+        m78 = fma2(V2<R>{hv, hv}, S78, fma2(V2<R>{-sv, -sv}, sub2(m78, me78), m78));
+        const V2<R> m[4] = {m12, m35, m46, m78};
+        R f0;
+        V2<R> Fo[4];
+        f_from_m9p<R, kFlowScale<M>>(drho, m, f0, Fo);
+        store_flow<M>(db, f0, Fo);
       }
     }
 
