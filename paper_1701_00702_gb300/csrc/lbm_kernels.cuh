@@ -613,7 +613,7 @@ __device__ __forceinline__ void pull_moments(const StepParams<typename ModeTrait
         for (int q = 1; q < QT; ++q) {   // deviation + reference of the sending node
             const V2<R> dev = {ldb<M>(sb[q] + PL::pcm(q) * kChunk), ldb<M>(sb[q] + PL::met(q) * kChunk)};
             const V2<R> ref = {pcm_ref(P, __ldg(sw[q])), __ldg(sw[q] + kChunk)};
-            t[q] = fma2(P.wmv[q], ref, dev);
+            t[q] = fma2(P.wmv[QT == 5 ? 1 : q], ref, dev);   // D2Q5: one weight varpi/4 for all movers (App. B)
         }
     } else {
 #pragma unroll
@@ -771,7 +771,7 @@ __device__ __forceinline__ void store_thermal(const StepParams<typename ModeTrai
         V2<float> sd;
 #pragma unroll
         for (int k = 1; k < QT; ++k) {
-            const V2<float> e = fma2(P.nwmv[k], ref, v[k]);
+            const V2<float> e = fma2(P.nwmv[QT == 5 ? 1 : k], ref, v[k]);
             const B bg = from_f<B>(e.x), bh = from_f<B>(e.y);
             db[PL::pcm(k) * kChunk] = bg;
             db[PL::met(k) * kChunk] = bh;
@@ -902,7 +902,7 @@ __device__ __forceinline__ void step_node(const StepParams<typename ModeTraits<M
         neq_metal<R, QT>(P, n.Tm, nem);
         V2<R> nr[QT];
 #pragma unroll
-        for (int k = 1; k < QT; ++k) nr[k] = P.nrate[k];
+        for (int k = 1; k < QT; ++k) nr[k] = P.nrate[QT == 5 && k == 2 ? 1 : k];   // D2Q5: j_x, j_y share a rate (App. B)
         if (PH && P.phase_k) {
             // Eq. 9 at the node's liquid fraction -> zeta_alpha (Eq. A19) -> zeta_e (Eq. 53)
             const R za = fast_rcp(R(0.5) + P.ks_c + n.fl * (P.kl_c - P.ks_c));
