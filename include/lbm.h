@@ -182,8 +182,24 @@ int lbm_create_ex(const lbm_params* p, void* cuda_stream, lbm_alloc_fn alloc,
  * on the host (LBM_ERR_UNSTABLE after any synchronising call saw the device
  * flag).  Large nsteps are replayed from a captured CUDA graph.  The step
  * kernel runs one node per thread in blocks of 64 x 2 threads on grids of up
- * to 100,000 nodes and 128 x 1 on larger ones. */
+ * to 100,000 nodes and 128 x 1 on larger ones, or node pairs (see
+ * lbm_set_step_form). */
 int lbm_step(lbm_handle* h, int64_t nsteps);
+
+/* Step form of a run (the paper has no counterpart: an implementation
+ * choice).  LBM_STEP_FORM_SINGLE: one node per thread.  LBM_STEP_FORM_PAIRS:
+ * two neighbouring nodes per thread, each FP32 operation one packed
+ * instruction for both; taken only by runs in the default configuration (flow,
+ * D2Q5 thermal lattices, volumetric blend, FP32/FP16/BF16 storage), the others
+ * keep one node per thread.  LBM_STEP_FORM_AUTO (the default): node pairs for
+ * FP16/BF16 runs of at least 2048 x 2048 nodes.  Both forms compute the same
+ * step to within a few roundings of the FP32 arithmetic.  Applies to later
+ * lbm_step calls and to batches created afterwards; synchronises the run's
+ * stream when it drops a captured graph.  LBM_ERR_ARG for another value. */
+#define LBM_STEP_FORM_AUTO 0
+#define LBM_STEP_FORM_SINGLE 1
+#define LBM_STEP_FORM_PAIRS 2
+int lbm_set_step_form(lbm_handle* h, int32_t form);
 
 /* Macroscopic fields at the current time level.  dst[i] receives field i of
  * LBM_FIELD_* when bit i of mask is set (nx*ny elements of the run's type,

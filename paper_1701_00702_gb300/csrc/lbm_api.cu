@@ -197,6 +197,7 @@ struct lbm_handle {
     int cur = 0;
     int64_t steps = 0;
     int sticky = LBM_OK;
+    int form = 0;   // step form (LBM_STEP_FORM_*)
     cudaGraphExec_t graph = nullptr;
 };
 
@@ -340,12 +341,12 @@ int cuda_fail(lbm_handle* h) {
 }
 
 cudaError_t enqueue_one(lbm_handle* h, int from, cudaStream_t s) {
-    const int q = h->p.thermal_q, fl = h->p.flow;
+    const int q = h->p.thermal_q, fl = h->p.flow, fm = h->form;
     switch (h->p.precision) {
-        case LBM_F64: return lbmk::launch_step<lbmk::MODE_F64>(make_params<double>(h, from), q, fl, s);
-        case LBM_F32: return lbmk::launch_step<lbmk::MODE_F32>(make_params<float>(h, from), q, fl, s);
-        case LBM_F16: return lbmk::launch_step<lbmk::MODE_F16>(make_params<float>(h, from), q, fl, s);
-        default: return lbmk::launch_step<lbmk::MODE_BF16>(make_params<float>(h, from), q, fl, s);
+        case LBM_F64: return lbmk::launch_step<lbmk::MODE_F64>(make_params<double>(h, from), q, fl, fm, s);
+        case LBM_F32: return lbmk::launch_step<lbmk::MODE_F32>(make_params<float>(h, from), q, fl, fm, s);
+        case LBM_F16: return lbmk::launch_step<lbmk::MODE_F16>(make_params<float>(h, from), q, fl, fm, s);
+        default: return lbmk::launch_step<lbmk::MODE_BF16>(make_params<float>(h, from), q, fl, fm, s);
     }
 }
 
@@ -546,6 +547,17 @@ int lbm_step(lbm_handle* h, int64_t nsteps) {
         --n;
     }
     return h->sticky;
+}
+
+int lbm_set_step_form(lbm_handle* h, int32_t form) {
+    if (!h || form < LBM_STEP_FORM_AUTO || form > LBM_STEP_FORM_PAIRS) return LBM_ERR_ARG;
+    if (form != h->form && h->graph) {   // the captured steps used the old form
+        if (cudaStreamSynchronize(h->stream) != cudaSuccess) return cuda_fail(h);
+        cudaGraphExecDestroy(h->graph);
+        h->graph = nullptr;
+    }
+    h->form = form;
+    return LBM_OK;
 }
 
 int lbm_fields(lbm_handle* h, int32_t mask, void* const* dst, int32_t dst_on_device) {
@@ -1009,15 +1021,6 @@ void free_batch(lbm_batch* b) {
     delete b;
 }
 
-const void* step_kernel_of(int precision, int qt, int flow, int ph) {
-    switch (precision) {
-        case LBM_F64: return lbmk::step_kernel<lbmk::MODE_F64>(qt, flow, ph);
-        case LBM_F32: return lbmk::step_kernel<lbmk::MODE_F32>(qt, flow, ph);
-        case LBM_F16: return lbmk::step_kernel<lbmk::MODE_F16>(qt, flow, ph);
-        default: return lbmk::step_kernel<lbmk::MODE_BF16>(qt, flow, ph);
-    }
-}
-
 // Map 3: a graph of `steps` steps with one chain of kernel nodes per run; a
 // run's step k reads the copy flip ^ (k mod 2), starting from batch parity 0.
 int build_chain_graph(lbm_batch* b, int steps, cudaGraphExec_t* out) {
@@ -1026,7 +1029,6 @@ int build_chain_graph(lbm_batch* b, int steps, cudaGraphExec_t* out) {
     cudaError_t e = cudaSuccess;
     for (size_t r = 0; r < b->runs.size() && e == cudaSuccess; ++r) {
         lbm_handle* h = b->runs[r];
-        const void* fn = step_kernel_of(b->precision, b->qt, b->flow, phase_k_of(h));
         cudaGraphNode_t prev = nullptr;
         for (int k = 0; k < steps && e == cudaSuccess; ++k) {
             const int from = b->flip[r] ^ (k & 1);
@@ -1040,11 +1042,18 @@ int build_chain_graph(lbm_batch* b, int steps, cudaGraphExec_t* out) {
                 Pf = make_params<float>(h, from);
                 args[0] = &Pf;
             }
-            const int bx = kShapes[b->shape[r]][0], by = kShapes[b->shape[r]][1];
+            const dim3 blk((unsigned)kShapes[b->shape[r]][0], (unsigned)kShapes[b->shape[r]][1], 1u);
+            lbmk::StepLaunch L;
+            switch (b->precision) {   // the kernel and grid lbm_step would launch for this run
+                case LBM_F64: L = lbmk::step_launch<lbmk::MODE_F64>(Pd, b->qt, b->flow, h->form, blk); break;
+                case LBM_F32: L = lbmk::step_launch<lbmk::MODE_F32>(Pf, b->qt, b->flow, h->form, blk); break;
+                case LBM_F16: L = lbmk::step_launch<lbmk::MODE_F16>(Pf, b->qt, b->flow, h->form, blk); break;
+                default: L = lbmk::step_launch<lbmk::MODE_BF16>(Pf, b->qt, b->flow, h->form, blk); break;
+            }
             cudaKernelNodeParams kp = {};
-            kp.func = const_cast<void*>(fn);
-            kp.gridDim = dim3((unsigned)((h->p.nx + bx - 1) / bx), (unsigned)((h->p.ny + by - 1) / by), 1u);
-            kp.blockDim = dim3((unsigned)bx, (unsigned)by, 1u);
+            kp.func = const_cast<void*>(L.fn);
+            kp.gridDim = L.grid;
+            kp.blockDim = L.block;
             kp.sharedMemBytes = 0;
             kp.kernelParams = args;
             kp.extra = nullptr;

@@ -960,6 +960,401 @@ __global__ void __launch_bounds__(256, (kMinBlocks<M, QT, FLOW>)) fused_step(con
     step_node<M, QT, FLOW, PH>(P, x, y);
 }
 
+// ---------------------------------------------------------------------------
+// Two nodes per thread
+// ---------------------------------------------------------------------------
+// Large grids of the default configuration (flow, D2Q5 thermal lattices,
+// volumetric blend, FP32/FP16/BF16 storage) advance node pairs (x0, x0 + 1),
+// x0 even, one pair per thread.  Every FP32 operation of the step is one
+// packed instruction for both nodes (lane x: node x0, lane y: node x0 + 1),
+// the parameter loads and the index arithmetic serve both nodes, and the pair
+// is read and written with one access per plane wherever both elements are
+// adjacent (x0 even keeps them inside one chunk, aligned).  The arithmetic is
+// that of step_node, operation for operation, except where noted; a pair with
+// a wall node (or without a second node) goes through step_node instead.
+
+using W = V2<float>;
+
+__device__ __forceinline__ W wb(float s) { return {s, s}; }
+__device__ __forceinline__ W wmin(W a, float b) { return {fminf(a.x, b), fminf(a.y, b)}; }
+__device__ __forceinline__ W wmax0(W a) { return {fmaxf(a.x, 0.0f), fmaxf(a.y, 0.0f)}; }
+__device__ __forceinline__ W wsat(W a) { return {__saturatef(a.x), __saturatef(a.y)}; }
+__device__ __forceinline__ W wrcp(W a) { return {__fdividef(1.0f, a.x), __fdividef(1.0f, a.y)}; }
+__device__ __forceinline__ W wsqrt(W a) { return {fast_sqrt(a.x), fast_sqrt(a.y)}; }
+
+// two adjacent elements of a plane (16-bit: one 32-bit access; FP32: 64-bit)
+template <int M>
+__device__ __forceinline__ W ldw(const char* p) {
+    if constexpr (M == MODE_F16) {
+        const float2 f = __half22float2(__ldg(reinterpret_cast<const __half2*>(p)));
+        return {f.x, f.y};
+    } else if constexpr (M == MODE_BF16) {
+        const float2 f = __bfloat1622float2(__ldg(reinterpret_cast<const __nv_bfloat162*>(p)));
+        return {f.x, f.y};
+    } else {
+        const float2 f = __ldg(reinterpret_cast<const float2*>(p));
+        return {f.x, f.y};
+    }
+}
+
+// stores v; returns the stored values as a reader decodes them
+template <int M>
+__device__ __forceinline__ W stw(char* p, W v) {
+    if constexpr (M == MODE_F16) {
+        const __half2 h = __floats2half2_rn(v.x, v.y);
+        *reinterpret_cast<__half2*>(p) = h;
+        const float2 f = __half22float2(h);
+        return {f.x, f.y};
+    } else if constexpr (M == MODE_BF16) {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(v.x, v.y);
+        *reinterpret_cast<__nv_bfloat162*>(p) = h;
+        const float2 f = __bfloat1622float2(h);
+        return {f.x, f.y};
+    } else {
+        *reinterpret_cast<float2*>(p) = make_float2(v.x, v.y);
+        return v;
+    }
+}
+
+__device__ __forceinline__ W ldwf(const char* p) {   // two adjacent FP32 elements
+    const float2 f = __ldg(reinterpret_cast<const float2*>(p));
+    return {f.x, f.y};
+}
+
+__device__ __forceinline__ void stwf(char* p, W v) { *reinterpret_cast<float2*>(p) = make_float2(v.x, v.y); }
+
+struct FW {
+    W hi, lo;
+};
+
+__device__ __forceinline__ FW two_sum(W a, W b) {   // Knuth, lane by lane
+    const W s = add2(a, b);
+    const W bb = sub2(s, a);
+    return {s, add2(sub2(a, sub2(s, bb)), sub2(b, bb))};
+}
+
+__device__ __forceinline__ FW fast_two_sum(W a, W b) {   // Dekker, |a| >= |b|
+    const W s = add2(a, b);
+    return {s, sub2(b, sub2(s, a))};
+}
+
+// as ff_accumulate<5>
+__device__ __forceinline__ FW fw_accumulate(FW a, const W* v, float sign) {
+    W s = a.hi, c = a.lo;
+#pragma unroll
+    for (int i = 1; i < 5; ++i) {
+        const FW t = two_sum(s, sign == 1.0f ? v[i] : mul2(wb(sign), v[i]));
+        s = t.hi;
+        c = add2(c, t.lo);
+    }
+    return fast_two_sum(s, c);
+}
+
+__device__ __forceinline__ void enthalpy_state(const StepParams<float>& P, W H, W& T, W& fl) {
+    fl = wsat(mul2(sub2(H, wb(P.H_fs)), wb(P.inv_dH)));
+    T = add2(fma2(fl, wb(P.dT_sl), wmin(mul2(H, wb(P.inv_c_ps)), P.T_fs)), wmax0(sub2(H, wb(P.H_fl))));
+}
+
+__device__ __forceinline__ W pcm_ref(const StepParams<float>& P, W g0) {
+    const W a = fma2(wsat(mul2(sub2(g0, wb(P.g0_fs)), wb(P.inv_dg0))), wb(P.cr_dsl), wmin(mul2(g0, wb(P.cr_solid)), P.cr_fs));
+    return fma2(wmax0(sub2(g0, wb(P.g0_fl))), wb(P.cr_liquid), a);
+}
+
+// D2Q5 moments of one lattice (Eq. B1) and back
+__device__ __forceinline__ void m_from_f5w(const W* g, W* n) {
+    const W a = add2(g[1], g[3]), b = add2(g[2], g[4]);
+    n[1] = sub2(g[1], g[3]);
+    n[2] = sub2(g[2], g[4]);
+    n[3] = add2(a, b);
+    n[4] = sub2(a, b);
+    n[0] = add2(g[0], n[3]);
+}
+
+__device__ __forceinline__ void f_from_m5w(const W* n, W* g) {
+    const W p = mul2(add2(n[3], n[4]), wb(0.25f)), q = mul2(sub2(n[3], n[4]), wb(0.25f));
+    g[0] = sub2(n[0], n[3]);
+    g[1] = fma2(wb(0.5f), n[1], p);
+    g[3] = fma2(wb(-0.5f), n[1], p);
+    g[2] = fma2(wb(0.5f), n[2], q);
+    g[4] = fma2(wb(-0.5f), n[2], q);
+}
+
+template <int M, bool PH>
+__device__ __forceinline__ void step_pair(const StepParams<float>& P, int x0, int y) {
+    using B = typename ModeTraits<M>::B;
+    using PL = Planes<M, 5, true>;
+    using CH = Chunk<M, 5, true>;
+    constexpr int es = (int)sizeof(B);
+    constexpr int pb = kChunk * es;   // bytes from one bulk plane to the next
+    // neighbour columns of the pair (periodic wrap; no walls reach here)
+    const int xm = x0 == 0 ? P.nx - 1 : x0 - 1;   // west of x0
+    const int xp = x0 + 2 == P.nx ? 0 : x0 + 2;   // east of x0 + 1
+    const int ym = y == 0 ? P.ny - 1 : y - 1;
+    const int yp = y == P.ny - 1 ? 0 : y + 1;
+    const int rb = P.cpr * CH::bytes;
+    const char* row[3] = {P.src + (long long)ym * rb, P.src + (long long)y * rb, P.src + (long long)yp * rb};
+    const int c0 = col_off<M, 5, true>(x0), cm = col_off<M, 5, true>(xm), cp = col_off<M, 5, true>(xp);
+    // plane q in row r: the pair (x0, x0+1), its west neighbours (x0-1, x0), its east ones (x0+1, x0+2)
+    auto own = [&](int r, int q) { return ldw<M>(row[r] + c0 + q * pb); };
+    auto west = [&](int r, int q) {
+        return W{ldb<M>(reinterpret_cast<const B*>(row[r] + cm + q * pb)),
+                 ldb<M>(reinterpret_cast<const B*>(row[r] + c0 + q * pb))};
+    };
+    auto east = [&](int r, int q) {
+        return W{ldb<M>(reinterpret_cast<const B*>(row[r] + c0 + q * pb) + 1),
+                 ldb<M>(reinterpret_cast<const B*>(row[r] + cp + q * pb))};
+    };
+
+    // ---- pull (Eq. 15) and flow moments (Eq. 13) ----
+    W f[9] = {own(1, 0), west(1, 1), own(0, 2), east(1, 3), own(2, 4), west(0, 5), east(0, 6), east(2, 7), west(2, 8)};
+    if constexpr (M == MODE_F16) {
+#pragma unroll
+        for (int q = 0; q < 9; ++q) f[q] = mul2(f[q], wb(1.0f / 1024.0f));
+    }
+    W m[9];
+    {
+        const W A13 = add2(f[1], f[3]), A24 = add2(f[2], f[4]), dx = sub2(f[1], f[3]), dy = sub2(f[2], f[4]);
+        const W B57 = add2(f[5], f[7]), B68 = add2(f[6], f[8]), E57 = sub2(f[5], f[7]), E68 = sub2(f[6], f[8]);
+        const W s14 = add2(A13, A24), s58 = add2(B57, B68);
+        const W ax = sub2(E57, E68), ay = add2(E57, E68);
+        m[0] = add2(add2(f[0], s14), s58);
+        m[1] = fma2(wb(2.0f), s58, fma2(wb(-1.0f), s14, mul2(wb(-4.0f), f[0])));
+        m[2] = fma2(wb(-2.0f), s14, fma2(wb(4.0f), f[0], s58));
+        m[3] = add2(dx, ax);
+        m[5] = add2(dy, ay);
+        m[4] = fma2(wb(-2.0f), dx, ax);
+        m[6] = fma2(wb(-2.0f), dy, ay);
+        m[7] = sub2(A13, A24);
+        m[8] = sub2(B57, B68);
+    }
+
+    // ---- thermal pull: PCM g, metal h (Eqs. 33, 44; App. B) ----
+    W g[5], h[5];
+    W Hlo = wb(0.0f);
+    if constexpr (kSplit<M>) {
+        constexpr int wo = CH::wide_off;
+        const int w0 = c0 + wo + (x0 & (kChunk - 1)) * 2;               // wide element of x0
+        const int wm = cm + wo + (xm & (kChunk - 1)) * 2, wp = cp + wo + (xp & (kChunk - 1)) * 2;
+        constexpr int wpl = kChunk * 4;                                  // PCM rest -> metal rest plane
+        const W g0o = ldwf(row[1] + w0), h0o = ldwf(row[1] + w0 + wpl);
+        // senders' rest populations for movers 1..4 (from x - e_q)
+        const W sg[5] = {g0o, W{__ldg(reinterpret_cast<const float*>(row[1] + wm)), g0o.x}, ldwf(row[0] + w0),
+                         W{g0o.y, __ldg(reinterpret_cast<const float*>(row[1] + wp))}, ldwf(row[2] + w0)};
+        const W sh[5] = {h0o, W{__ldg(reinterpret_cast<const float*>(row[1] + wm + wpl)), h0o.x},
+                         ldwf(row[0] + w0 + wpl), W{h0o.y, __ldg(reinterpret_cast<const float*>(row[1] + wp + wpl))},
+                         ldwf(row[2] + w0 + wpl)};
+        const W dg[5] = {wb(0.0f), west(1, PL::pcm(1)), own(0, PL::pcm(2)), east(1, PL::pcm(3)), own(2, PL::pcm(4))};
+        const W dh[5] = {wb(0.0f), west(1, PL::met(1)), own(0, PL::met(2)), east(1, PL::met(3)), own(2, PL::met(4))};
+        const float wg = P.wmv[1].x, wk = P.wmv[1].y;   // D2Q5: one weight for all movers (App. B)
+        g[0] = g0o;
+        h[0] = h0o;
+#pragma unroll
+        for (int q = 1; q < 5; ++q) {
+            g[q] = fma2(wb(wg), pcm_ref(P, sg[q]), dg[q]);
+            h[q] = fma2(wb(wk), sh[q], dh[q]);
+        }
+    } else {
+        g[0] = own(1, PL::pcm(0));
+        h[0] = own(1, PL::met(0));
+        g[1] = west(1, PL::pcm(1)); g[2] = own(0, PL::pcm(2)); g[3] = east(1, PL::pcm(3)); g[4] = own(2, PL::pcm(4));
+        h[1] = west(1, PL::met(1)); h[2] = own(0, PL::met(2)); h[3] = east(1, PL::met(3)); h[4] = own(2, PL::met(4));
+    }
+    W ng[5], nh[5];
+    m_from_f5w(g, ng);
+    m_from_f5w(h, nh);
+    if constexpr (kComp<M>) {   // H = (g_0 hi + g_0 lo) + sum of movers, without rounding loss
+        const FW H = fw_accumulate(FW{g[0], own(1, PL::lo)}, g, 1.0f);
+        ng[0] = H.hi;
+        Hlo = H.lo;
+    }
+
+    // ---- macroscopic state (Eqs. 21, 23-25, 37-39, 7) ----
+    const W H = ng[0];
+    W Tf, fl;
+    enthalpy_state(P, H, Tf, fl);
+    const W Tm = nh[0];
+    const W drho = m[0];
+    const W rho = add2(wb(1.0f), drho);
+    const W Gy = mul2(mul2(wb(P.gbeta), sub2(Tf, wb(P.T0))), fl);
+    W ux, uy, um;
+    {
+        const W ir = wrcp(rho);
+        const W vx = mul2(mul2(fl, m[3]), ir);
+        const W vy = fma2(wb(0.5f * P.phi), Gy, mul2(mul2(fl, m[5]), ir));
+        const W vm = wsqrt(fma2(vy, vy, mul2(vx, vx)));
+        W r = wsqrt(fma2(wb(P.l1), vm, wb(P.l0sq)));
+        const W den = wrcp(add2(wb(P.l0), r));   // Eq. 23
+        ux = mul2(vx, den);
+        uy = mul2(vy, den);
+        um = mul2(vm, den);
+    }
+
+    // ---- flow collision (Eqs. 3, 14, 18-20) ----
+    char* dst = P.dst + (long long)y * rb;
+    {
+        const W nd = fma2(wb(-P.drag_forch), um, wb(-P.drag_lin));   // -(drag)
+        const W Fx = mul2(nd, ux), Fy = fma2(nd, uy, mul2(wb(P.phi), Gy));
+        const W sol = mul2(sub2(wb(1.0f), fl), drho);
+        W b1 = fma2(fl, m[1], mul2(wb(-2.0f), sol)), b2 = fma2(fl, m[2], sol);
+        W b4 = mul2(fl, m[4]), b6 = mul2(fl, m[6]), b7 = mul2(fl, m[7]), b8 = mul2(fl, m[8]);
+        const W rip = mul2(rho, wb(P.inv_phi));
+        const W uxx = mul2(ux, ux), uyy = mul2(uy, uy), uxy = mul2(ux, uy);
+        const W q = mul2(mul2(wb(3.0f), rip), add2(uxx, uyy));
+        const W me1 = fma2(wb(-2.0f), drho, q), me2 = sub2(drho, q);
+        const W Jx = mul2(rho, ux), Jy = mul2(rho, uy);
+        const W me7 = mul2(rip, sub2(uxx, uyy)), me8 = mul2(rip, uxy);
+        const W s1 = mul2(mul2(wb(6.0f), rip), fma2(uy, Fy, mul2(ux, Fx)));
+        const W RFx = mul2(rho, Fx), RFy = mul2(rho, Fy);
+        const W S7 = mul2(rip, mul2(wb(2.0f), sub2(mul2(ux, Fx), mul2(uy, Fy))));
+        const W S8 = mul2(rip, fma2(uy, Fx, mul2(ux, Fy)));
+        b1 = fma2(wb(0.45f), s1, fma2(wb(-1.1f), sub2(b1, me1), b1));
+        b2 = fma2(wb(-0.45f), s1, fma2(wb(-1.1f), sub2(b2, me2), b2));
+        const W b3 = fma2(wb(0.5f), RFx, Jx), b5 = fma2(wb(0.5f), RFy, Jy);
+        b4 = fma2(wb(-0.4f), RFx, fma2(wb(-1.2f), add2(b4, Jx), b4));
+        b6 = fma2(wb(-0.4f), RFy, fma2(wb(-1.2f), add2(b6, Jy), b6));
+        const float sv = P.s[7], hv = 1.0f - 0.5f * sv;
+        b7 = fma2(wb(hv), S7, fma2(wb(-sv), sub2(b7, me7), b7));
+        b8 = fma2(wb(hv), S8, fma2(wb(-sv), sub2(b8, me8), b8));
+        // f = M^-1 m* (as f_from_m9p), scaled by the storage scale
+        constexpr float sc = (float)kFlowScale<M>;
+        const W A = mul2(drho, wb(sc / 9.0f)), Bm = mul2(b1, wb(sc / 36.0f)), C = mul2(b2, wb(sc / 36.0f));
+        const W DX = mul2(b3, wb(sc / 6.0f)), QX = mul2(b4, wb(sc / 12.0f));
+        const W DY = mul2(b5, wb(sc / 6.0f)), QY = mul2(b6, wb(sc / 12.0f));
+        const W Pm = mul2(b7, wb(sc * 0.25f)), Sm = mul2(b8, wb(sc * 0.25f));
+        const W f0 = fma2(wb(4.0f), C, fma2(wb(-4.0f), Bm, A));
+        const W bb1 = fma2(wb(-2.0f), C, sub2(A, Bm));
+        const W bb5 = add2(fma2(wb(2.0f), Bm, A), C);
+        const W Tx = fma2(wb(-2.0f), QX, DX), Ty = fma2(wb(-2.0f), QY, DY);
+        const W X = add2(DX, QX), Y = add2(DY, QY);
+        const W bp = add2(bb1, Pm), bm = sub2(bb1, Pm);
+        const W G5 = add2(bb5, Sm), G6 = sub2(bb5, Sm), H5 = add2(X, Y), H6 = sub2(Y, X);
+        const W fo[9] = {f0, add2(bp, Tx), add2(bm, Ty), sub2(bp, Tx), sub2(bm, Ty),
+                         add2(G5, H5), add2(G6, H6), sub2(G5, H5), sub2(G6, H6)};
+#pragma unroll
+        for (int k = 0; k < 9; ++k) stw<M>(dst + c0 + k * pb, fo[k]);
+    }
+
+    // ---- exchange sources (Eqs. 36, 47, Remark III) ----
+    float* dTp_ptr = P.dT + (long long)y * P.pitch + x0;
+    const W dTn = sub2(Tm, Tf);
+    const W dTp = ldwf(reinterpret_cast<const char*>(dTp_ptr));
+    const W Sx = fma2(wb(1.5f), dTn, mul2(wb(-0.5f), dTp));
+    const W S_met = mul2(wb(-P.a_m), Sx);
+    W hm_base;
+    if constexpr (kSplit<M>) hm_base = nh[0];
+    else hm_base = fma2(wb(-P.eta[0]), sub2(nh[0], Tm), nh[0]);
+    const W hm = add2(hm_base, S_met);
+    const W S_pcm = mul2(sub2(hm, hm_base), wb(P.x_pm));
+
+    // ---- PCM (Eq. 32) and metal (Eq. 43) collisions ----
+    {
+        const W t = mul2(Tf, wb(P.inv_phi));
+        const W ne1 = mul2(t, ux), ne2 = mul2(t, uy), ne3 = mul2(wb(P.vcf), Tf);
+        W nz[5];
+        if (PH && P.phase_k) {   // Eq. 9 -> zeta_alpha (Eq. A19) -> zeta_e (Eq. 53)
+            const W za = wrcp(add2(wb(0.5f + P.ks_c), mul2(fl, wb(P.kl_c - P.ks_c))));
+#pragma unroll
+            for (int k = 1; k < 5; ++k) nz[k] = mul2(wb(-1.0f), fma2(wb(P.zr_b[k]), za, wb(P.zr_a[k])));
+        } else {
+            nz[1] = nz[2] = wb(P.nrate[1].x);
+            nz[3] = wb(P.nrate[3].x);
+            nz[4] = wb(P.nrate[4].x);
+        }
+        ng[1] = fma2(nz[1], sub2(ng[1], ne1), ng[1]);
+        ng[2] = fma2(nz[2], sub2(ng[2], ne2), ng[2]);
+        ng[3] = fma2(nz[3], sub2(ng[3], ne3), ng[3]);
+        ng[4] = fma2(nz[4], ng[4], ng[4]);
+        const float ne_j = P.nrate[1].y;
+        nh[1] = fma2(wb(ne_j), nh[1], nh[1]);
+        nh[2] = fma2(wb(ne_j), nh[2], nh[2]);
+        nh[3] = fma2(wb(P.nrate[3].y), sub2(nh[3], mul2(wb(P.vcm), Tm)), nh[3]);
+        nh[4] = fma2(wb(P.nrate[4].y), nh[4], nh[4]);
+        ng[3] = fma2(wb(P.varpi), S_pcm, ng[3]);
+        nh[3] = fma2(wb(P.varpi), S_met, nh[3]);
+    }
+    // n_0* = H + S_PCM (Eq. 32), metal n_0* = hm
+    W n0hi, n0lo = wb(0.0f);
+    if constexpr (kComp<M>) {
+        const FW s = two_sum(ng[0], S_pcm);
+        const FW n0 = fast_two_sum(s.hi, add2(s.lo, Hlo));
+        n0hi = n0.hi;
+        n0lo = n0.lo;
+    } else {
+        n0hi = add2(ng[0], S_pcm);
+    }
+
+    // ---- thermal store: movers, then the rest populations as remainders ----
+    W vg[5], vh[5];
+    ng[0] = n0hi;
+    nh[0] = hm;
+    f_from_m5w(ng, vg);
+    f_from_m5w(nh, vh);
+    if constexpr (kSplit<M>) {
+        // as store_thermal: deviations from the provisional rest population's
+        // reference, then the rest population that closes the balance
+        const W ref = pcm_ref(P, vg[0]);
+        const float nwg = P.nwmv[1].x, nwk = P.nwmv[1].y;
+        W sdg, sdh;
+#pragma unroll
+        for (int k = 1; k < 5; ++k) {
+            const W dgk = stw<M>(dst + c0 + PL::pcm(k) * pb, fma2(wb(nwg), ref, vg[k]));
+            const W dhk = stw<M>(dst + c0 + PL::met(k) * pb, fma2(wb(nwk), vh[0], vh[k]));
+            sdg = k == 1 ? dgk : add2(sdg, dgk);
+            sdh = k == 1 ? dhk : add2(sdh, dhk);
+        }
+        const W Yg = sub2(n0hi, sdg), Yh = sub2(hm, sdh);
+        W T, f_;
+        enthalpy_state(P, Yg, T, f_);
+        const int w0 = c0 + CH::wide_off + (x0 & (kChunk - 1)) * 2;
+        stwf(dst + w0, fma2(wb(-P.om_cf), T, Yg));
+        stwf(dst + w0 + kChunk * 4, mul2(Yh, wb(P.rest_m)));
+    } else {
+#pragma unroll
+        for (int k = 1; k < 5; ++k) {
+            stw<M>(dst + c0 + PL::pcm(k) * pb, vg[k]);
+            stw<M>(dst + c0 + PL::met(k) * pb, vh[k]);
+        }
+        const W smh = add2(add2(add2(vh[1], vh[2]), vh[3]), vh[4]);
+        stw<M>(dst + c0 + PL::met(0) * pb, sub2(hm, smh));
+        if constexpr (kComp<M>) {   // the PCM rest population as a float-float pair
+            const FW r = fw_accumulate(FW{n0hi, n0lo}, vg, -1.0f);
+            stw<M>(dst + c0 + PL::pcm(0) * pb, r.hi);
+            stw<M>(dst + c0 + PL::lo * pb, r.lo);
+        } else {
+            const W smg = add2(add2(add2(vg[1], vg[2]), vg[3]), vg[4]);
+            stw<M>(dst + c0 + PL::pcm(0) * pb, sub2(n0hi, smg));
+        }
+    }
+    stwf(reinterpret_cast<char*>(dTp_ptr), dTn);
+
+    // non-finite or runaway state: raise the sticky flag (no trap)
+    const W a = add2(add2(W{fabsf(H.x), fabsf(H.y)}, W{fabsf(Tm.x), fabsf(Tm.y)}), rho);
+    const W u2 = fma2(uy, uy, mul2(ux, ux));
+    const bool bad = !(a.x < 1e30f) || !(a.y < 1e30f) || !(rho.x > 0.0f) || !(rho.y > 0.0f) ||
+                     !(u2.x <= 0.09f) || !(u2.y <= 0.09f);
+    if (bad) atomicOr(P.status, STATUS_UNSTABLE);
+}
+
+// Node pairs of the default configuration: a block of 64 x 2 threads covers
+// 128 x 2 nodes.  A pair with a wall node or without a second node (or a run
+// of the bounce-back variant) takes step_node.  Seven blocks per SM cap the
+// registers at 72 (measured best: 80 registers leave too few warps to hide
+// the memory latency, 64 spill).
+template <int M, bool PH>
+__global__ void __launch_bounds__(128, 7) fused_step_pair(const __grid_constant__ StepParams<float> P) {
+    const int x0 = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x0 >= P.nx || y >= P.ny) return;
+    const bool single = P.solid_scheme || x0 + 1 >= P.nx || (!P.per_x && (x0 == 0 || x0 + 1 == P.nx - 1)) ||
+                        (!P.per_y && (y == 0 || y == P.ny - 1));
+    if (single) {
+        step_node<M, 5, true, PH>(P, x0, y);
+        if (x0 + 1 < P.nx) step_node<M, 5, true, PH>(P, x0 + 1, y);
+        return;
+    }
+    step_pair<M, PH>(P, x0, y);
+}
+
 // Many runs in one launch.  A tile is w x (256 / w) nodes of one run (w a
 // power of two, 32..256); thread t of a block takes node (x0 + t mod w,
 // y0 + t div w).  Each run has two parameter blocks in global memory, one per

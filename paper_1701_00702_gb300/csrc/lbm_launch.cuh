@@ -151,14 +151,54 @@ inline dim3 step_block(int nx, int ny) {
     return (long long)nx * ny <= 100000 ? dim3(64, 2) : dim3(128, 1);
 }
 
+// Step forms: one node per thread (fused_step) or node pairs
+// (fused_step_pair, the default configuration only: flow, D2Q5, volumetric
+// blend, FP32 arithmetic).  Automatic: node pairs for the 16-bit forms from
+// 2048 x 2048 nodes up (measured on GB300: 2048^2 FP16 69.6 against 73.4 us
+// per step; at 1024^2, and in FP32, where the step is bound by HBM, one node
+// per thread is faster).
+enum : int { FORM_AUTO = 0, FORM_SINGLE = 1, FORM_PAIRS = 2 };
+constexpr long long kPairMinNodes = 1ll << 22;
+
 template <int M>
-cudaError_t launch_step(const StepParams<typename ModeTraits<M>::R>& P, int qt, int flow, cudaStream_t s) {
-    const dim3 b = step_block(P.nx, P.ny);
-    const dim3 g((unsigned)((P.nx + b.x - 1) / b.x), (unsigned)((P.ny + b.y - 1) / b.y), 1u);
-    return dispatch_step<M>(qt, flow, P.phase_k, [&]<int MM, int Q, bool F, bool PH>() {
-        fused_step<MM, Q, F, PH><<<g, b, 0, s>>>(P);
-        return cudaGetLastError();
+inline bool use_pairs(const StepParams<typename ModeTraits<M>::R>& P, int qt, int flow, int form) {
+    const bool can = M != MODE_F64 && qt == 5 && flow && !P.solid_scheme;
+    if (form == FORM_PAIRS) return can;
+    if (form == FORM_SINGLE) return false;
+    return can && kSplit<M> && (long long)P.nx * P.ny >= kPairMinNodes;
+}
+
+// The step kernel of a run, with its grid: one node per thread in blocks of
+// b threads, or node pairs in blocks of 64 x 2.
+struct StepLaunch {
+    const void* fn;
+    dim3 grid, block;
+};
+
+template <int M>
+StepLaunch step_launch(const StepParams<typename ModeTraits<M>::R>& P, int qt, int flow, int form, dim3 b) {
+    StepLaunch L{nullptr, dim3(), b};
+    if constexpr (M != MODE_F64) {
+        if (use_pairs<M>(P, qt, flow, form)) {
+            L.fn = P.phase_k ? (const void*)fused_step_pair<M, true> : (const void*)fused_step_pair<M, false>;
+            L.block = dim3(64, 2);
+            L.grid = dim3((unsigned)(((P.nx + 1) / 2 + 63) / 64), (unsigned)((P.ny + 1) / 2), 1u);
+            return L;
+        }
+    }
+    dispatch_step<M>(qt, flow, P.phase_k, [&]<int MM, int Q, bool F, bool PH>() {
+        L.fn = (const void*)fused_step<MM, Q, F, PH>;
+        return cudaSuccess;
     });
+    L.grid = dim3((unsigned)((P.nx + b.x - 1) / b.x), (unsigned)((P.ny + b.y - 1) / b.y), 1u);
+    return L;
+}
+
+template <int M>
+cudaError_t launch_step(const StepParams<typename ModeTraits<M>::R>& P, int qt, int flow, int form, cudaStream_t s) {
+    const StepLaunch L = step_launch<M>(P, qt, flow, form, step_block(P.nx, P.ny));
+    void* args[1] = {const_cast<StepParams<typename ModeTraits<M>::R>*>(&P)};
+    return cudaLaunchKernel(L.fn, L.grid, L.block, args, 0, s);
 }
 
 template <int M>
@@ -215,17 +255,6 @@ cudaError_t launch_batch(const StepParams<typename ModeTraits<M>::R>* runs, cons
     });
 }
 
-// The single-run kernel as a function pointer, for kernel nodes built
-// directly into a graph (one chain of steps per run).
-template <int M>
-const void* step_kernel(int qt, int flow, int ph) {
-    const void* fn = nullptr;
-    dispatch_step<M>(qt, flow, ph, [&]<int MM, int Q, bool F, bool PH>() {
-        fn = (const void*)fused_step<MM, Q, F, PH>;
-        return cudaSuccess;
-    });
-    return fn;
-}
 
 template <int M>
 int batch_blocks_per_sm(int qt, int flow, int ph) {
@@ -237,7 +266,7 @@ int batch_blocks_per_sm(int qt, int flow, int ph) {
 }
 
 #define LBMK_INSTANTIATE(M)                                                                                   \
-    template cudaError_t launch_step<M>(const StepParams<ModeTraits<M>::R>&, int, int, cudaStream_t);        \
+    template cudaError_t launch_step<M>(const StepParams<ModeTraits<M>::R>&, int, int, int, cudaStream_t);   \
     template cudaError_t launch_fields<M>(const StepParams<ModeTraits<M>::R>&, const FieldOut<ModeTraits<M>::R>&, \
                                           int, int, cudaStream_t);                                            \
     template cudaError_t launch_diag<M>(const StepParams<ModeTraits<M>::R>&, const DiagConst&, double*, double*, \
@@ -246,7 +275,7 @@ int batch_blocks_per_sm(int qt, int flow, int ph) {
     template cudaError_t launch_batch<M>(const StepParams<ModeTraits<M>::R>*, const Tile*, int, int, int, int, int, \
                                          int, int, cudaStream_t);                                               \
     template int batch_blocks_per_sm<M>(int, int, int);                                                   \
-    template const void* step_kernel<M>(int, int, int);
+    template StepLaunch step_launch<M>(const StepParams<ModeTraits<M>::R>&, int, int, int, dim3);
 
 #define LBMK_INSTANTIATE_CONVERT(M)                                                                           \
     template cudaError_t launch_convert<M>(const StepParams<ModeTraits<M>::R>&, const DenseState<ModeTraits<M>::R>&, \

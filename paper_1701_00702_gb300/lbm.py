@@ -97,6 +97,8 @@ def lib() -> ctypes.CDLL:
         L.lbm_create_ex.restype = ctypes.c_int
         L.lbm_step.argtypes = [vp, i64]
         L.lbm_step.restype = ctypes.c_int
+        L.lbm_set_step_form.argtypes = [vp, i32]
+        L.lbm_set_step_form.restype = ctypes.c_int
         L.lbm_fields.argtypes = [vp, i32, ctypes.POINTER(vp), i32]
         L.lbm_fields.restype = ctypes.c_int
         L.lbm_diag.argtypes = [vp] + [ctypes.POINTER(ctypes.c_double)] * 4
@@ -278,6 +280,11 @@ class Solver:
     # -- stepping -----------------------------------------------------------
     def step(self, n: int) -> "Solver":
         _check(lib().lbm_step(self._h, int(n)), "lbm_step")
+        return self
+
+    def set_step_form(self, form: int) -> "Solver":
+        """0: automatic, 1: one node per thread, 2: node pairs (lbm_set_step_form)."""
+        _check(lib().lbm_set_step_form(self._h, int(form)), "lbm_set_step_form")
         return self
 
     @property

@@ -206,3 +206,28 @@ def test_block_shapes_under_map_3_change_no_result(lbm):
     tuned.close()
     for s in runs + solo:
         s.close()
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+def test_node_pair_runs_under_map_3_equal_lbm_step(lbm, prec):
+    """Runs set to the node-pair step form keep it inside a map-3 batch, bit for
+    bit equal to lbm_step; runs left on one node per thread beside them too."""
+    shapes = [(131, 7, 0, 0), (70, 33, 1, 0), (64, 64, 1, 1)]
+    ps = [inputs.cavity(nx, ny=ny, precision=prec, periodic_x=px, periodic_y=py, L_char=100.0, Ra=1e7)
+          for nx, ny, px, py in shapes]
+    runs, solo = [], []
+    for k, p in enumerate(ps):
+        F, G, Hm, dT = inputs.random_state(p["nx"], p["ny"], 5, seed=80 + k, H_range=(-0.2, 1.6), f_base=W9.ravel())
+        for dst in (runs, solo):
+            s = lbm.Solver(p).set_step_form(2 if k != 1 else 1)
+            s.set_state(F - W9, G, Hm, dT)
+            dst.append(s)
+    b = lbm.Batch(runs, autotune=False).configure(128, 3)
+    b.step(70)
+    for s in solo:
+        s.step(70)
+    for r, s in zip(runs, solo):
+        assert _same_state(r, s, True, prec)
+    b.close()
+    for s in runs + solo:
+        s.close()

@@ -203,3 +203,30 @@ def test_config2_size_against_fp32(lbm, prec):
         s.close()
     assert abs(d[prec]["melt_frac"] / d[1]["melt_frac"] - 1) < TOL[prec]
     assert abs(d[prec]["nu_hot"] / d[1]["nu_hot"] - 1) < TOL[prec]
+
+
+@pytest.mark.parametrize("prec,rtol", [(F16, 2 * 2.0 ** -11), (BF16, 2 * 2.0 ** -8)])
+@pytest.mark.parametrize("shape", [(131, 7, 0, 0), (130, 9, 1, 1), (5, 3, 0, 1), (513, 520, 0, 0)])
+def test_node_pair_kernel_one_step(lbm, oracle_mod, prec, rtol, shape):
+    """The two-nodes-per-thread form (LBM_STEP_FORM_PAIRS, automatic for the
+    16-bit forms from 2048^2 nodes) in FP16 and BF16: one step from a random
+    state against the oracle."""
+    nx, ny, px, py = shape
+    p = inputs.cavity(max(nx, ny), ny=ny, precision=prec, periodic_x=px, periodic_y=py, L_char=100.0, Ra=1e7)
+    p["nx"] = nx
+    lc = oracle_mod.lattice_config(p)
+    F, G, Hm, dT = inputs.random_state(nx, ny, 5, seed=nx + ny, H_range=(lc["T_fs"] - 0.3, lc["T_fl"] + lc["L_a"] + 0.3))
+    s = lbm.Solver(p).set_step_form(2)
+    s.set_state(on_grid(F - W9, prec, 1024.0), G.astype(np.float32), Hm.astype(np.float32), dT.astype(np.float32))
+    f0, g0, h0, d0 = s.get_state()
+    o = oracle_mod.Oracle(p)
+    o.set_state(f0.astype(np.float64) + W9, g0.astype(np.float64), h0.astype(np.float64), d0.astype(np.float64))
+    s.step(1)
+    o.run(1)
+    f1, g1, h1, d1 = s.get_state()
+    Fo, Go, Ho, Do = o.state()
+    for a, b, name in ((f1, Fo - W9, "f - w"), (g1, Go, "g"), (h1, Ho, "h")):
+        err = np.abs(a.astype(np.float64) - b).max() / max(np.abs(b).max(), 1e-3)
+        assert err < rtol * 4, (name, err)
+    assert np.abs(d1 - Do).max() < 1e-5
+    s.close()

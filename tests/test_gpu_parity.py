@@ -378,3 +378,46 @@ def test_long_run_conservation_in_a_mushy_box(lbm, prec, tol):
             _, g, _, _, lo = s.get_state(with_lo=True)
             assert abs((g.astype(np.float64).sum() + lo.astype(np.float64).sum()) / pcm0 - 1) < 1e-12
         s.close()
+
+
+PAIR_SHAPES = [
+    # node pairs forced: odd widths end in a single node, walls and periodic sides, blocks
+    # with ragged tails, the smallest periodic pair (nx = 2), grids above 2^18 nodes
+    (131, 7, 0, 0), (130, 9, 1, 1), (257, 4, 1, 0), (5, 3, 0, 1), (2, 2, 1, 1), (4, 5, 1, 0), (513, 520, 0, 0),
+    (515, 511, 1, 1),
+]
+
+
+@pytest.mark.parametrize("shape", PAIR_SHAPES)
+@pytest.mark.parametrize("variant", ["default", "eq9"])
+def test_node_pair_kernel_from_random_state(lbm, oracle_mod, shape, variant):
+    """The two-nodes-per-thread form of the fused step (LBM_STEP_FORM_PAIRS) in
+    FP32 against the oracle, three steps from a random state; the Eq. 9
+    variant compiles the per-node rates into it."""
+    nx, ny, px, py = shape
+    extra = VARIANTS["eq9"] if variant == "eq9" else {}
+    p = inputs.cavity(max(nx, ny), ny=ny, precision=1, periodic_x=px, periodic_y=py, L_char=100.0, Ra=1e7,
+                      **extra)
+    p["nx"] = nx
+    s, o = _random_pair(lbm, oracle_mod, p, seed=nx + 7 * ny)
+    s.set_step_form(2)
+    for n in (1, 2):
+        s.step(n)
+        o.run(n)
+        _compare_states(s, o, 1, 1)
+    s.close()
+
+
+def test_step_forms_agree_over_a_graph_replayed_run(lbm):
+    """Both step forms on the same cavity for 200 steps (graph replays and
+    single launches): states within a few FP32 roundings of each other."""
+    p = inputs.cavity(258, ny=130, precision=1)
+    a, b = lbm.Solver(p).set_step_form(1), lbm.Solver(p).set_step_form(2)
+    a.step(200)
+    b.step(200)
+    for x, y in zip(a.get_state(), b.get_state()):
+        scale = max(np.abs(x).max(), 1e-3)
+        assert np.abs(x.astype(np.float64) - y).max() / scale < 1e-5
+    with pytest.raises(lbm.LbmError):
+        a.set_step_form(3)
+    a.close(); b.close()
