@@ -207,12 +207,15 @@ def test_config2_size_against_fp32(lbm, prec):
 
 @pytest.mark.parametrize("prec,rtol", [(F16, 2 * 2.0 ** -11), (BF16, 2 * 2.0 ** -8)])
 @pytest.mark.parametrize("shape", [(131, 7, 0, 0), (130, 9, 1, 1), (5, 3, 0, 1), (513, 520, 0, 0)])
-def test_node_pair_kernel_one_step(lbm, oracle_mod, prec, rtol, shape):
+@pytest.mark.parametrize("eq9", [0, 1])
+def test_node_pair_kernel_one_step(lbm, oracle_mod, prec, rtol, shape, eq9):
     """The two-nodes-per-thread form (LBM_STEP_FORM_PAIRS, automatic for the
     16-bit forms from 2048^2 nodes) in FP16 and BF16: one step from a random
-    state against the oracle."""
+    state against the oracle, with and without the Eq. 9 per-node rates."""
     nx, ny, px, py = shape
-    p = inputs.cavity(max(nx, ny), ny=ny, precision=prec, periodic_x=px, periodic_y=py, L_char=100.0, Ra=1e7)
+    extra = dict(ks_over_kl=0.5, cps_over_cpl=1.4) if eq9 else {}
+    p = inputs.cavity(max(nx, ny), ny=ny, precision=prec, periodic_x=px, periodic_y=py, L_char=100.0, Ra=1e7,
+                      **extra)
     p["nx"] = nx
     lc = oracle_mod.lattice_config(p)
     F, G, Hm, dT = inputs.random_state(nx, ny, 5, seed=nx + ny, H_range=(lc["T_fs"] - 0.3, lc["T_fl"] + lc["L_a"] + 0.3))
