@@ -180,9 +180,10 @@ int lbm_create_ex(const lbm_params* p, void* cuda_stream, lbm_alloc_fn alloc,
 /* Enqueues nsteps >= 0 time steps (Sec. III: stream, walls, enthalpy, blend,
  * velocity, three collisions).  Asynchronous: returns the sticky status known
  * on the host (LBM_ERR_UNSTABLE after any synchronising call saw the device
- * flag).  Large nsteps are replayed from a captured CUDA graph.  The step
- * kernel runs one node per thread in blocks of 64 x 2 threads on grids of up
- * to 100,000 nodes and 128 x 1 on larger ones, or node pairs (see
+ * flag).  Large nsteps are replayed from a captured CUDA graph.  Each step is
+ * launched as a programmatic dependent of the previous one in the stream.
+ * The step kernel runs one node per thread in blocks of 64 x 2 threads on
+ * grids of up to 100,000 nodes and 128 x 1 on larger ones, or node pairs (see
  * lbm_set_step_form). */
 int lbm_step(lbm_handle* h, int64_t nsteps);
 

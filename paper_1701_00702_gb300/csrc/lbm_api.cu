@@ -1058,7 +1058,17 @@ int build_chain_graph(lbm_batch* b, int steps, cudaGraphExec_t* out) {
             kp.kernelParams = args;
             kp.extra = nullptr;
             cudaGraphNode_t node = nullptr;
-            e = cudaGraphAddKernelNode(&node, g, prev ? &prev : nullptr, prev ? 1 : 0, &kp);
+            e = cudaGraphAddKernelNode(&node, g, nullptr, 0, &kp);
+            if (e == cudaSuccess && prev) {
+                // programmatic edge, as lbm_step's launches: the next step of this
+                // run launches while the previous one drains and waits for it
+                // in-kernel before touching the state
+                cudaGraphEdgeData ed = {};
+                ed.from_port = cudaGraphKernelNodePortProgrammatic;
+                ed.to_port = cudaGraphKernelNodePortDefault;
+                ed.type = cudaGraphDependencyTypeProgrammatic;
+                e = cudaGraphAddDependencies(g, &prev, &node, &ed, 1);
+            }
             prev = node;
         }
     }

@@ -944,11 +944,22 @@ __device__ __forceinline__ void step_node(const StepParams<typename ModeTraits<M
 }
 
 // Blocks of 256 threads each SM must hold, which caps the registers per
-// thread: six for FP32 D2Q5 with flow (bandwidth-bound; 40 registers), five for
-// the 16-bit forms (issue-bound; 48 registers); the others take what their
-// registers allow.
+// thread: five for the FP32 and 16-bit forms of D2Q5 with flow (48 registers;
+// with the packed arithmetic 40 registers and six blocks measured ~1 % slower
+// at 256^2 and 2048^2 in FP32); the others take what their registers allow.
 template <int M, int QT, bool FLOW>
-constexpr int kMinBlocks = (QT == 5 && FLOW) ? (M == MODE_F32 ? 6 : (M == MODE_F64 ? 1 : 5)) : 1;
+constexpr int kMinBlocks = (QT == 5 && FLOW) ? (M == MODE_F64 ? 1 : 5) : 1;
+
+// Programmatic dependent launch (sm_90 and later): the step kernels are
+// launched as programmatic dependents of the previous step, so their launch
+// overlaps its tail.  griddep_wait blocks until the previous grid in the
+// stream has completed and its writes are visible (it returns at once when
+// this grid was not launched as a programmatic dependent); no thread touches
+// the state before it.  The dependents are released when this grid's blocks
+// exit (no early trigger: dependents scheduled while this grid still runs took
+// its SM resources, 256^2 went from 2.75 to 3.52 us per step; released at exit,
+// 2.50).
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
 // One run: one thread per node, 256 threads per block (128 x 2 by default;
 // the batch's map 3 may take other shapes).
@@ -957,6 +968,7 @@ __global__ void __launch_bounds__(256, (kMinBlocks<M, QT, FLOW>)) fused_step(con
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     if (x >= P.nx || y >= P.ny) return;
+    griddep_wait();
     step_node<M, QT, FLOW, PH>(P, x, y);
 }
 
@@ -1345,6 +1357,7 @@ __global__ void __launch_bounds__(128, 7) fused_step_pair(const __grid_constant_
     const int x0 = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     if (x0 >= P.nx || y >= P.ny) return;
+    griddep_wait();
     const bool single = P.solid_scheme || x0 + 1 >= P.nx || (!P.per_x && (x0 == 0 || x0 + 1 == P.nx - 1)) ||
                         (!P.per_y && (y == 0 || y == P.ny - 1));
     if (single) {

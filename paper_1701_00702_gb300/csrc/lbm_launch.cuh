@@ -194,11 +194,23 @@ StepLaunch step_launch(const StepParams<typename ModeTraits<M>::R>& P, int qt, i
     return L;
 }
 
+// Launched as a programmatic dependent of the previous step (the kernels wait
+// for it before touching the state), so the launch overlaps its tail.
 template <int M>
 cudaError_t launch_step(const StepParams<typename ModeTraits<M>::R>& P, int qt, int flow, int form, cudaStream_t s) {
     const StepLaunch L = step_launch<M>(P, qt, flow, form, step_block(P.nx, P.ny));
     void* args[1] = {const_cast<StepParams<typename ModeTraits<M>::R>*>(&P)};
-    return cudaLaunchKernel(L.fn, L.grid, L.block, args, 0, s);
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = L.grid;
+    cfg.blockDim = L.block;
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelExC(&cfg, L.fn, args);
 }
 
 template <int M>
