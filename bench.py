@@ -78,10 +78,19 @@ def measured_traffic(n: int):
     val = re.search(r"traffic_bytes_per_launch: (\d+)", text)
     if not want or not val:
         return None
+    return int(val.group(1)) if kernel_sources_hash() == want.group(1) else None
+
+
+def kernel_sources_hash() -> str:
+    """First 16 hex digits of the sha256 of the step kernels' sources with
+    // comments, trailing blanks and empty lines removed (a comment edit does
+    not invalidate a capture; any code change does)."""
     h = hashlib.sha256()
     for name in ("lbm_kernels.cuh", "lbm_launch.cuh", "lbm_kernels_f32.cu"):
-        h.update((ROOT / "paper_1701_00702_gb300" / "csrc" / name).read_bytes())
-    return int(val.group(1)) if h.hexdigest()[:16] == want.group(1) else None
+        text = (ROOT / "paper_1701_00702_gb300" / "csrc" / name).read_text()
+        code = [ln.split("//", 1)[0].rstrip() for ln in text.splitlines()]
+        h.update("\n".join(ln for ln in code if ln).encode())
+    return h.hexdigest()[:16]
 
 
 def parse():

@@ -1,7 +1,8 @@
 // Device code of the fused three-lattice time step (Liu, He & Li, arXiv
-// 1701.00702, Sec. III).  One thread owns one node; the whole step is one
-// pass over HBM: 9 + 2*Q_T populations and the exchange history are read
-// once (pull streaming, Eqs. 15, 33, 44) and written once.
+// 1701.00702, Sec. III).  One thread owns one node (fused_step) or two
+// neighbouring nodes (fused_step_pair); the whole step is one pass over HBM:
+// 9 + 2*Q_T populations and the exchange history are read once (pull
+// streaming, Eqs. 15, 33, 44) and written once.
 //
 // Everything after the pull works in moment space:
 //   * m+ = M f+, n_g = M g, n_h = M h with the integer matrices of Eq. 13
@@ -34,7 +35,10 @@
 //     took (scaled by the heat capacities), so the exchange moves no energy
 //     that the metal's rounding dropped;
 //   * the state is chunked: [chunk][plane][kChunk] with chunks of kChunk nodes
-//     along x, so one pointer per pulled neighbour reaches all its planes.
+//     along x, so one pointer per pulled neighbour reaches all its planes;
+//   * FP32 arithmetic goes through the packed two-lane instructions of sm_100
+//     and later wherever two values take the same operations (the PCM and
+//     metal lattices, pairs of flow moments, or the two nodes of a pair).
 #pragma once
 
 #include <cuda_bf16.h>
