@@ -286,7 +286,6 @@ lbmk::StepParams<R> make_params(const lbm_handle* h, int from) {
     }
     for (int k = 0; k < 9; ++k) {
         P.s[k] = (R)d.s[k];
-        P.zeta[k] = (R)d.zeta[k];
         P.eta[k] = (R)d.eta[k];
         P.nrate[k] = {-(R)d.zeta[k], -(R)d.eta[k]};
     }
@@ -302,7 +301,6 @@ lbmk::StepParams<R> make_params(const lbm_handle* h, int from) {
     P.varpi = (R)p.varpi;
     P.vcf = (R)(p.varpi * d.c_fref);
     P.vcm = (R)(p.varpi * d.c_mref);
-    P.a_f = (R)(d.h_v / (phi * 1.0));
     // Eq. 9 variant: per-node zeta_alpha = 1/(1/2 + k_f(f_l)/(rho_l c_fref c_sT^2)) (Eq. A19);
     // rate k of the PCM lattice is zr_a[k] + zr_b[k] zeta_alpha (fixed, zeta_alpha, or 2 - zeta_alpha)
     P.phase_k = phase_k_of(h);

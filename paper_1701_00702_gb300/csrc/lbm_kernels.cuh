@@ -198,11 +198,11 @@ struct StepParams {
     R H_fs, H_fl, inv_dH, T_fs, T_fl, dT_sl, inv_c_ps;   // dT_sl = T_fl - T_fs
     R c_fref, c_mref, varpi;
     R vcf, vcm;          // varpi c_f,ref and varpi c_m,ref (D2Q5 equilibria, Eqs. B2, B4)
-    R zeta[9], eta[9];
+    R eta[9];            // metal rates (eta[0] for the FP32 rest population's relaxation)
     V2<R> nrate[9];      // (-zeta_k, -eta_k): PCM and metal relaxation rates, negated
     V2<R> nwmv[9];       // (-w'_k, -w'_k kappa_m): 16-bit mover references per unit of (ref, h_0)
     V2<R> wmv[9];        // (w'_k, w'_k kappa_m)
-    R a_f, a_m;          // h_v/(phi rho_l), h_v/((1 - phi) rho_m)
+    R a_m;               // h_v/((1 - phi) rho_m), Eq. 47
     R x_pm;              // -a_f/a_m = -(1 - phi) rho_m/(phi rho_l): PCM source per unit of metal source
     // Eq. 9 variant: PCM rates from the node's liquid fraction
     int phase_k;         // 1: k_s != k_l, rates per node
@@ -296,25 +296,6 @@ __device__ __forceinline__ void f_from_m9(const R* m, R* f) {
     f[8] = b5 + X - Y - S;
 }
 
-template <typename R>
-__device__ __forceinline__ void m_from_f5(const R* g, R* n) {
-    n[0] = g[0] + g[1] + g[2] + g[3] + g[4];
-    n[1] = g[1] - g[3];
-    n[2] = g[2] - g[4];
-    n[3] = g[1] + g[2] + g[3] + g[4];
-    n[4] = g[1] - g[2] + g[3] - g[4];
-}
-
-template <typename R>
-__device__ __forceinline__ void f_from_m5(const R* n, R* g) {
-    const R p = (n[3] + n[4]) * R(0.25), q = (n[3] - n[4]) * R(0.25);
-    g[0] = n[0] - n[3];
-    g[1] = R(0.5) * n[1] + p;
-    g[3] = R(-0.5) * n[1] + p;
-    g[2] = R(0.5) * n[2] + q;
-    g[4] = R(-0.5) * n[2] + q;
-}
-
 // Eq. 13 on the population pairs (f1, f2), (f3, f4), (f5, f6), (f7, f8) (the
 // D2Q9 order of Eq. 11): m_0 and the moment pairs (e, eps), (j_x, j_y),
 // (q_x, q_y), (p_xx, p_xy).
@@ -355,8 +336,9 @@ __device__ __forceinline__ void f_from_m9p(R m0, const V2<R>* m, R& f0, V2<R>* F
     F[3] = sub2(G, H);                                  // (f7, f8)
 }
 
-// Eq. B1 and its inverse on (PCM, metal) pairs, same rounding order as above
-// except n_0 = g_0 + ((g_1 + g_3) + (g_2 + g_4)).
+// Eq. B1 and its inverse on (PCM, metal) pairs: n = M g for D2Q5 with
+// n_0 = g_0 + ((g_1 + g_3) + (g_2 + g_4)), n_1 = g_1 - g_3, n_2 = g_2 - g_4,
+// n_3 = g_1 + g_2 + g_3 + g_4, n_4 = g_1 - g_2 + g_3 - g_4.
 template <typename R>
 __device__ __forceinline__ void m_from_f5(const V2<R>* g, V2<R>* n) {
     const V2<R> a = add2(g[1], g[3]), b = add2(g[2], g[4]);
@@ -406,16 +388,6 @@ __device__ __forceinline__ void inv2(const V2<R>* m, V2<R>* v) {
 #pragma unroll
         for (int k = 0; k < 9; ++k) v[k] = {va[k], vb[k]};
     }
-}
-
-template <typename R, int Q>
-__device__ __forceinline__ void fwd(const R* v, R* m) {
-    if constexpr (Q == 9) m_from_f9(v, m); else m_from_f5(v, m);
-}
-
-template <typename R, int Q>
-__device__ __forceinline__ void inv(const R* m, R* v) {
-    if constexpr (Q == 9) f_from_m9(m, v); else f_from_m5(m, v);
 }
 
 // ---------------------------------------------------------------------------
