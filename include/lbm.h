@@ -202,6 +202,12 @@ int lbm_step(lbm_handle* h, int64_t nsteps);
 #define LBM_STEP_FORM_PAIRS 2
 int lbm_set_step_form(lbm_handle* h, int32_t form);
 
+/* The form (LBM_STEP_FORM_SINGLE or LBM_STEP_FORM_PAIRS) a run with
+ * parameters p steps in when set to `form`, written to *used.  Host only,
+ * needs no GPU.  Returns lbm_derive's error for invalid p, LBM_ERR_ARG for
+ * another form value or NULL pointers. */
+int lbm_step_form_for(const lbm_params* p, int32_t form, int32_t* used);
+
 /* Macroscopic fields at the current time level.  dst[i] receives field i of
  * LBM_FIELD_* when bit i of mask is set (nx*ny elements of the run's type,
  * [ny][nx]); dst_on_device selects device or host pointers.  Synchronises. */

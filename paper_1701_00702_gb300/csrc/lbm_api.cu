@@ -547,6 +547,16 @@ int lbm_step(lbm_handle* h, int64_t nsteps) {
     return h->sticky;
 }
 
+int lbm_step_form_for(const lbm_params* p, int32_t form, int32_t* used) {
+    if (!p || !used || form < LBM_STEP_FORM_AUTO || form > LBM_STEP_FORM_PAIRS) return LBM_ERR_ARG;
+    const int rc = derive_impl(p, nullptr);
+    if (rc != LBM_OK) return rc;
+    *used = lbmk::pairs_for(p->precision, p->thermal_q, p->flow, p->solid_scheme, (long long)p->nx * p->ny, form)
+                ? LBM_STEP_FORM_PAIRS
+                : LBM_STEP_FORM_SINGLE;
+    return LBM_OK;
+}
+
 int lbm_set_step_form(lbm_handle* h, int32_t form) {
     if (!h || form < LBM_STEP_FORM_AUTO || form > LBM_STEP_FORM_PAIRS) return LBM_ERR_ARG;
     if (form != h->form && h->graph) {   // the captured steps used the old form

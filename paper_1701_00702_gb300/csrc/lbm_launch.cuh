@@ -161,12 +161,17 @@ inline dim3 step_block(int nx, int ny) {
 enum : int { FORM_AUTO = 0, FORM_SINGLE = 1, FORM_PAIRS = 2 };
 constexpr long long kPairMinNodes = 1ll << 22;
 
-template <int M>
-inline bool use_pairs(const StepParams<typename ModeTraits<M>::R>& P, int qt, int flow, int form) {
-    const bool can = M != MODE_F64 && qt == 5 && flow && !P.solid_scheme;
+// The rule (host code; lbm_step_form_for reports it).  mode: MODE_*.
+inline bool pairs_for(int mode, int qt, int flow, int solid_scheme, long long nodes, int form) {
+    const bool can = mode != MODE_F64 && qt == 5 && flow && !solid_scheme;
     if (form == FORM_PAIRS) return can;
     if (form == FORM_SINGLE) return false;
-    return can && kSplit<M> && (long long)P.nx * P.ny >= kPairMinNodes;
+    return can && (mode == MODE_F16 || mode == MODE_BF16) && nodes >= kPairMinNodes;
+}
+
+template <int M>
+inline bool use_pairs(const StepParams<typename ModeTraits<M>::R>& P, int qt, int flow, int form) {
+    return pairs_for(M, qt, flow, P.solid_scheme, (long long)P.nx * P.ny, form);
 }
 
 // The step kernel of a run, with its grid: one node per thread in blocks of

@@ -99,6 +99,8 @@ def lib() -> ctypes.CDLL:
         L.lbm_step.restype = ctypes.c_int
         L.lbm_set_step_form.argtypes = [vp, i32]
         L.lbm_set_step_form.restype = ctypes.c_int
+        L.lbm_step_form_for.argtypes = [pp, i32, ctypes.POINTER(i32)]
+        L.lbm_step_form_for.restype = ctypes.c_int
         L.lbm_fields.argtypes = [vp, i32, ctypes.POINTER(vp), i32]
         L.lbm_fields.restype = ctypes.c_int
         L.lbm_diag.argtypes = [vp] + [ctypes.POINTER(ctypes.c_double)] * 4
@@ -206,6 +208,14 @@ def derive(p: dict) -> dict:
     d = LbmDerived()
     _check(lib().lbm_derive(ctypes.byref(to_struct(p)), ctypes.byref(d)), "lbm_derive")
     return _derived_dict(d)
+
+
+def step_form_for(p: dict, form: int = 0) -> int:
+    """The step form (1: one node per thread, 2: node pairs) a run with
+    parameters p takes when set to `form` (lbm_step_form_for; no GPU needed)."""
+    used = ctypes.c_int32()
+    _check(lib().lbm_step_form_for(ctypes.byref(to_struct(p)), int(form), ctypes.byref(used)), "lbm_step_form_for")
+    return int(used.value)
 
 
 def state_bytes(p: dict) -> int:

@@ -135,3 +135,39 @@ def test_create_without_gpu_fails_cleanly(lbm):
     h = ctypes.c_void_p()
     rc = lbm.lib().lbm_create(ctypes.byref(lbm.to_struct(inputs.cavity(16))), None, ctypes.byref(h))
     assert rc in (-3, -4) and not h.value
+
+
+@pytest.mark.parametrize("params,form,expected", [
+    # automatic: node pairs for FP16/BF16 runs of the default configuration from 2048^2 nodes
+    (dict(n=2048, precision=2), 0, 2),
+    (dict(n=2048, precision=3), 0, 2),
+    (dict(n=2048, ny=4096, precision=2), 0, 2),
+    (dict(n=2048, ny=2047, precision=2), 0, 1),            # one row short of 2^22 nodes
+    (dict(n=1024, precision=2), 0, 1),
+    (dict(n=2048, precision=1), 0, 1),                      # FP32: HBM-bound, one node per thread
+    (dict(n=2048, precision=0), 0, 1),
+    (dict(n=2048, precision=2, thermal_q=9), 0, 1),
+    (dict(n=2048, precision=2, flow=0), 0, 1),
+    (dict(n=2048, precision=2, solid_scheme=1), 0, 1),     # bounce-back variant
+    (dict(n=2048, precision=2, ks_over_kl=0.5), 0, 2),      # Eq. 9 rates: compiled into both forms
+    # forced
+    (dict(n=64, precision=1), 2, 2),
+    (dict(n=3, precision=3, L_char=100.0), 2, 2),
+    (dict(n=64, precision=0), 2, 1),                        # no FP64 node-pair kernel
+    (dict(n=64, precision=1, thermal_q=9), 2, 1),
+    (dict(n=2048, precision=2), 1, 1),
+])
+def test_step_form_rule(lbm, params, form, expected):
+    """lbm_step_form_for reports the kernel form lbm_step takes (the same rule
+    the launcher uses), with no GPU."""
+    params = dict(params)
+    n = params.pop("n")
+    p = inputs.cavity(n, **params)
+    assert lbm.step_form_for(p, form) == expected
+
+
+def test_step_form_query_rejects_bad_input(lbm):
+    with pytest.raises(lbm.LbmError):
+        lbm.step_form_for(inputs.cavity(64), 3)
+    with pytest.raises(lbm.LbmError):
+        lbm.step_form_for(dict(inputs.cavity(64), nx=0), 0)
