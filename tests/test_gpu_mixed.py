@@ -3,7 +3,7 @@ arithmetic) against the FP64 oracle.
 
 Tolerances: one step from a state already on the 16-bit grid agrees to the
 storage rounding of its outputs (2^-11 relative for FP16, 2^-8 for BF16, of
-each array's scale, with a factor 2 margin); long runs are judged on the
+each array's scale, with a factor 2 margin); long runs are assessed on the
 integral quantities the method's stated target names: melt fraction and
 hot-wall Nusselt number within 1e-3 relative of the FP64 oracle for FP16.
 BF16 keeps 8 significant bits and is held to 1e-2 (measured: 1.4e-3 on the

@@ -61,7 +61,7 @@ def _compare_states(s, o, prec, flow):
     tol = 1e-12 if prec == 0 else 5e-6
     pairs = [(g, G, "g"), (h, H, "h"), (dT, D, "dT")] + ([(f, F - W9, "f - w")] if flow else [])
     for a, b, name in pairs:
-        # dT = T_m - T_f is a difference of O(1) temperatures: judge it on that scale
+        # dT = T_m - T_f is a difference of O(1) temperatures: measure it on that scale
         scale = max(np.abs(b).max(), 1.0 if name == "dT" else 1e-3)
         err = np.abs(a.astype(np.float64) - b).max() / scale
         assert err < tol, (name, err)
