@@ -5,8 +5,9 @@ interstitial exchange with its time-derivative correction (Eqs. 36, 47,
 Remark III), the one-phase Stefan problem and its local-thermal-equilibrium
 limit (Eqs. 28, 41, 10), the Brinkman-Forchheimer channel (Eqs. 2-3), a
 decaying shear wave (Eq. 26 and the Darcy term of Eq. 3), adiabatic walls
-(Eq. 52) and a two-step hand calculation of the D2Q5 enthalpy update
-(Eqs. 38, 52, B1-B3)."""
+(Eq. 52), a two-step hand calculation of the D2Q5 enthalpy update
+(Eqs. 38, 52, B1-B3), and the thickness of the cavity's interface region
+(Sec. IV B)."""
 import math
 
 import numpy as np
@@ -554,3 +555,28 @@ def test_eq9_two_step_hand_calculation_d2q5(oracle_mod):
     expect = a * (4.0 - ze - lc["zeta"][4] - 2.0 * za) / 4.0
     assert abs(o.fields()["H_f"][0][2] - expect) < 1e-15
     assert abs(za - lc["zeta_a"]) > 0.1                  # the node's rate is not the liquid one
+
+
+def test_cavity_interface_region_is_about_ten_lattices_thick(oracle_mod):
+    """Sec. IV B cavity at Ra = 1e6 on 150 x 150 (the paper's own set-up) up to
+    Fo = t alpha_f / L^2 = 0.001 (Eq. 54; 45,000 steps): while the PCM melts
+    the phase interface is a region about ten lattices thick (the paper's
+    reading of Fig. 6, Fo <= 0.002), f_l stays in [0, 1], and the flow inside
+    the interface region (f_l < 0.5) is much weaker than in the liquid (the
+    volumetric scheme's damping, Sec. V B).  Measured: 14 lattices with
+    0.01 < f_l < 0.99 in every row, |u_y| 1.1e-6 against |u| 8.2e-5."""
+    p = dict(inputs.paper_cavity_defaults(), precision=0)
+    o = oracle_mod.Oracle(p)
+    steps = int(round(0.001 * p["L_char"] ** 2 / p["k_f"]))
+    assert steps == 45000
+    o.run(steps)
+    f = o.fields()
+    fl = f["f_l"]
+    assert fl.min() >= 0.0 and fl.max() <= 1.0
+    band = ((fl > 0.01) & (fl < 0.99)).sum(axis=1)[5:-5]     # rows away from the adiabatic walls
+    assert 5 <= band.min() and band.max() <= 20, (band.min(), band.max())
+    liquid, weak = fl >= 0.999, (fl > 0.0) & (fl < 0.5)
+    assert liquid.any() and weak.any()
+    u_liquid = np.hypot(f["u_x"], f["u_y"])[liquid].max()
+    assert np.abs(f["u_y"][weak]).max() < 0.1 * u_liquid
+    assert np.all(f["u_x"][fl == 0.0] == 0.0) and np.all(f["u_y"][fl == 0.0] == 0.0)
