@@ -40,16 +40,21 @@ WALL_DIRICHLET = 0
 WALL_ADIABATIC = 1
 
 
-def build(force: bool = False) -> Path:
-    """Compile the C oracle with gcc (IEEE arithmetic, no FMA contraction)."""
-    _BUILD.mkdir(exist_ok=True)
-    if force or not _LIB_PATH.exists() or _LIB_PATH.stat().st_mtime < _SRC.stat().st_mtime:
-        tmp = _LIB_PATH.with_suffix(f".{os.getpid()}.tmp")
+def build(force: bool = False, src: Path | None = None, out: Path | None = None) -> Path:
+    """Compile the C oracle with gcc (IEEE arithmetic, no FMA contraction).
+
+    ``src``/``out`` compile another copy of the source (the pin tests plant
+    mistakes in a copy this way, to show that a pin catches them)."""
+    src = _SRC if src is None else Path(src)
+    out = _LIB_PATH if out is None else Path(out)
+    out.parent.mkdir(parents=True, exist_ok=True)
+    if force or not out.exists() or out.stat().st_mtime < src.stat().st_mtime:
+        tmp = out.with_suffix(f".{os.getpid()}.tmp")
         cmd = ["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-fopenmp",
-               "-ffp-contract=off", "-fno-fast-math", str(_SRC), "-o", str(tmp), "-lm"]
+               "-ffp-contract=off", "-fno-fast-math", str(src), "-o", str(tmp), "-lm"]
         subprocess.run(cmd, check=True)
-        os.replace(tmp, _LIB_PATH)
-    return _LIB_PATH
+        os.replace(tmp, out)
+    return out
 
 
 class OrcCfg(ctypes.Structure):
@@ -73,34 +78,43 @@ class OrcCfg(ctypes.Structure):
 _lib = None
 
 
+def _bind(L):
+    """Declare the argument types of a loaded oracle library."""
+    dp = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
+    cp = ctypes.POINTER(OrcCfg)
+    L.orc_init.argtypes = [cp, ctypes.c_double, dp, dp, dp, dp]
+    L.orc_step.argtypes = [cp, dp, dp, dp, dp, dp, dp, dp]
+    L.orc_fields.argtypes = [cp, dp, dp, dp] + [dp] * 7
+    L.orc_lattice.argtypes = [np.ctypeslib.ndpointer(dtype=np.int32), np.ctypeslib.ndpointer(dtype=np.int32), dp]
+    L.orc_matrices.argtypes = [ctypes.c_int, dp, dp]
+    for name in ("orc_f_eq", "orc_m_eq"):
+        getattr(L, name).argtypes = [cp, ctypes.c_double, ctypes.c_double, ctypes.c_double, dp]
+    L.orc_force_moments.argtypes = [cp] + [ctypes.c_double] * 5 + [dp]
+    for name in ("orc_g_eq", "orc_ng_eq"):
+        getattr(L, name).argtypes = [cp] + [ctypes.c_double] * 4 + [dp]
+    for name in ("orc_h_eq", "orc_nh_eq"):
+        getattr(L, name).argtypes = [cp, ctypes.c_double, dp]
+    for name in ("orc_T_of_H", "orc_fl_of_H", "orc_H_of_T"):
+        getattr(L, name).argtypes = [cp, ctypes.c_double]
+        getattr(L, name).restype = ctypes.c_double
+    L.orc_velocity.argtypes = [cp] + [ctypes.c_double] * 4 + [dp]
+    ip = np.ctypeslib.ndpointer(dtype=np.int32, flags="C_CONTIGUOUS")
+    L.orc_step_nodes.argtypes = [cp, dp, dp, dp, dp, ip, ip, ctypes.c_int, dp, dp, dp, dp]
+    L.orc_set_threads.argtypes = [ctypes.c_int]
+    L.orc_threads.restype = ctypes.c_int
+    return L
+
+
 def lib():
     global _lib
     if _lib is None:
-        L = ctypes.CDLL(str(build()))
-        dp = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
-        cp = ctypes.POINTER(OrcCfg)
-        L.orc_init.argtypes = [cp, ctypes.c_double, dp, dp, dp, dp]
-        L.orc_step.argtypes = [cp, dp, dp, dp, dp, dp, dp, dp]
-        L.orc_fields.argtypes = [cp, dp, dp, dp] + [dp] * 7
-        L.orc_lattice.argtypes = [np.ctypeslib.ndpointer(dtype=np.int32), np.ctypeslib.ndpointer(dtype=np.int32), dp]
-        L.orc_matrices.argtypes = [ctypes.c_int, dp, dp]
-        for name in ("orc_f_eq", "orc_m_eq"):
-            getattr(L, name).argtypes = [cp, ctypes.c_double, ctypes.c_double, ctypes.c_double, dp]
-        L.orc_force_moments.argtypes = [cp] + [ctypes.c_double] * 5 + [dp]
-        for name in ("orc_g_eq", "orc_ng_eq"):
-            getattr(L, name).argtypes = [cp] + [ctypes.c_double] * 4 + [dp]
-        for name in ("orc_h_eq", "orc_nh_eq"):
-            getattr(L, name).argtypes = [cp, ctypes.c_double, dp]
-        for name in ("orc_T_of_H", "orc_fl_of_H", "orc_H_of_T"):
-            getattr(L, name).argtypes = [cp, ctypes.c_double]
-            getattr(L, name).restype = ctypes.c_double
-        L.orc_velocity.argtypes = [cp] + [ctypes.c_double] * 4 + [dp]
-        ip = np.ctypeslib.ndpointer(dtype=np.int32, flags="C_CONTIGUOUS")
-        L.orc_step_nodes.argtypes = [cp, dp, dp, dp, dp, ip, ip, ctypes.c_int, dp, dp, dp, dp]
-        L.orc_set_threads.argtypes = [ctypes.c_int]
-        L.orc_threads.restype = ctypes.c_int
-        _lib = L
+        _lib = _bind(ctypes.CDLL(str(build())))
     return _lib
+
+
+def load(path) -> ctypes.CDLL:
+    """Load another compiled copy of the oracle (see ``build``)."""
+    return _bind(ctypes.CDLL(str(path)))
 
 
 # ---------------------------------------------------------------------------
@@ -192,11 +206,11 @@ def make_cfg(lc: dict) -> OrcCfg:
 class Oracle:
     """One run of the FP64 oracle: state arrays [q][ny][nx] in numpy."""
 
-    def __init__(self, params: dict, threads: int | None = None):
+    def __init__(self, params: dict, threads: int | None = None, library=None):
         self.params = dict(params)
         self.lc = lattice_config(params)
         self.cfg = make_cfg(self.lc)
-        self._L = lib()
+        self._L = lib() if library is None else library
         if threads is not None:
             self._L.orc_set_threads(int(threads))
         nx, ny, qt = self.lc["nx"], self.lc["ny"], self.lc["qt"]

@@ -74,6 +74,21 @@ def conduction_1d(nx: int = 200, ny: int = 4, precision: int = PREC_F64, thermal
     return p
 
 
+def heated_cavity(n: int, Ra: float, k_f: float = 0.05, precision: int = PREC_F64, **over) -> dict:
+    """The differentially heated square cavity of natural convection, reached
+    as a limit of the Sec. IV B set-up: porosity 0.9999, Da = 1e9 and
+    F_phi = 0 (no porous drag), H_v = 0 (the metal lattice decouples),
+    conductivity ratio 1, Pr = 0.71, and a melting point below the cold wall
+    so that the PCM is liquid throughout.  Walls are the nodes x = 0 and
+    x = n - 1, so the cavity width is L = n - 1; the run starts at the mean
+    temperature 0.5, which is also the buoyancy reference."""
+    p = cavity(n, precision=precision, porosity=0.9999, Nu_i=0.0, Da=1e9, F_phi=0.0, Pr=0.71,
+               cond_ratio=1.0, Ra=float(Ra), T_solidus=-1.0, T_liquidus=-1.0, T_init=0.5, T_ref0=0.5,
+               k_f=float(k_f), cfref_over_cpl=0.5, L_char=float(n - 1))
+    p.update(over)
+    return p
+
+
 def periodic_box(nx: int, ny: int, **over) -> dict:
     """Fully periodic box (no walls): the set-up of the conservation checks."""
     p = cavity(max(nx, ny))
