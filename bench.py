@@ -33,7 +33,6 @@ import argparse
 import hashlib
 import json
 import os
-import re
 import statistics
 import subprocess
 import sys
@@ -53,32 +52,50 @@ PREC_NAMES = {0: "f64", 1: "f32", 2: "f16", 3: "bf16"}
 
 
 def bytes_per_update(qt: int, flow: int, precision: int) -> int:
-    """Algorithmic HBM bytes per node update of a storage form: every stored
-    value read and written once.  FP64/FP32: all populations plus the exchange
-    history (FP32 adds the low part of the PCM rest population); FP16/BF16:
-    16-bit flow deviations and moving thermal populations, FP32 thermal rest
-    populations and history."""
+    """Algorithmic HBM bytes per node update: every population the method
+    stores read and written once, plus the exchange history of Remark III.
+    FP64: 8-byte populations and history; FP32: 4-byte; FP16/BF16: 2-byte
+    populations with an FP32 history.  D2Q9 flow + D2Q5 + D2Q5 gives 320, 160
+    and 84 B."""
     fl = 9 if flow else 0
     if precision == 0:
         return (fl + 2 * qt + 1) * 8 * 2
     if precision == 1:
-        return (fl + 2 * qt + 1 + 1) * 4 * 2
-    return ((fl + 2 * (qt - 1)) * 2 + 2 * 4 + 4) * 2
+        return (fl + 2 * qt + 1) * 4 * 2
+    return (fl + 2 * qt) * 2 * 2 + 4 * 2
+
+
+def stored_bytes_per_update(qt: int, flow: int, precision: int) -> int:
+    """Bytes the implementation moves per node update: the algorithmic bytes
+    plus its own extra planes -- FP32 keeps the low part of the float-float
+    PCM rest population (one more FP32 plane), FP16/BF16 keep both thermal
+    rest populations in FP32 (two 16-bit planes become FP32)."""
+    b = bytes_per_update(qt, flow, precision)
+    if precision == 1:
+        return b + 4 * 2
+    if precision in (2, 3):
+        return b + 2 * 2 * 2
+    return b
+
+
+# DRAM traffic of one launch of the roofline kernel (fused_step, FP32, D2Q5,
+# flow, 2048 x 2048 cavity): dram__bytes_read.sum + dram__bytes_write.sum from
+# one ncu capture, taken for the kernel sources whose code hash is given; the
+# bench reports it only while the sources still hash to that value.
+ROOFLINE_TRAFFIC = {
+    "bytes_per_launch": 651068928,
+    "kernel_sources_sha256_16": "0713aeeb754d7d30",
+    "gpu__dram_throughput_pct": 83.5,
+    "captured": "2026-12-03, ncu --set full --clock-control none, one launch after two",
+}
 
 
 def measured_traffic(n: int):
-    """DRAM bytes per launch of the fused step from the committed ncu summary,
-    or None when the kernel sources changed since that capture (or for
-    another grid size)."""
-    prof = ROOT / "profiles" / "fused_step_cavity2048_fp32.md"
-    if n != 2048 or not prof.exists():
+    """ncu DRAM bytes per launch of the roofline kernel, or None for another
+    grid size or once the kernel sources have changed since the capture."""
+    if n != 2048 or kernel_sources_hash() != ROOFLINE_TRAFFIC["kernel_sources_sha256_16"]:
         return None
-    text = prof.read_text()
-    want = re.search(r"kernel_sources_sha256_16: ([0-9a-f]+)", text)
-    val = re.search(r"traffic_bytes_per_launch: (\d+)", text)
-    if not want or not val:
-        return None
-    return int(val.group(1)) if kernel_sources_hash() == want.group(1) else None
+    return ROOFLINE_TRAFFIC["bytes_per_launch"]
 
 
 def kernel_sources_hash() -> str:
@@ -112,7 +129,12 @@ def parse():
     ap.add_argument("--serve-requests", type=int, default=16)
     ap.add_argument("--serve-step-scale", type=float, default=0.1,
                     help="scale of the serving trace's step counts (log-uniform 1e4..5e5 before scaling)")
+    ap.add_argument("--serve-full", action="store_true",
+                    help="serve the stated trace (>= 64 requests, 1e4..5e5 steps) and add a run under a "
+                         "budget that binds (several minutes)")
+    ap.add_argument("--serve-tight-budget-gb", type=float, default=0.5)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-accuracy", action="store_true")
     return ap.parse_args()
 
 
@@ -290,55 +312,95 @@ def run_reference(args):
 
 def bench_serving(args, lbm, inputs, stream, plain_mlups: float, seed: int = 1701):
     """Poisson arrivals of melting runs (grids 128^2, 256^2, 512^2, 1024^2,
-    2048x1024; mixed porosity, Da, Ra, Ste), served by the plain form (FP32,
-    one request at a time in arrival order) and by continuous batching (FP16,
-    150 GB HBM budget), both replaying the same trace on the host clock."""
+    2048x1024; mixed porosity, Da, Ra, Ste; step counts log-uniform over the
+    trace's range) at ~80 % of the plain form's capacity, served by the plain
+    form (FP32, one request at a time in arrival order) and by continuous
+    batching (FP16) under the 150 GB HBM budget and, with --serve-full, under
+    a budget small enough to bind; every form replays the same trace on the
+    host clock."""
     import numpy as np
-    scale = args.serve_step_scale
+    scale = 1.0 if args.serve_full else args.serve_step_scale
+    count = max(64, args.serve_requests) if args.serve_full else args.serve_requests
     lo, hi = int(1e4 * scale), int(5e5 * scale)
     grids = ((128, 128), (256, 256), (512, 512), (1024, 1024), (2048, 1024))
     mean_nodes = float(np.mean([a * b for a, b in grids]))
     mean_steps = (hi - lo) / np.log(hi / lo)
     rate = 0.8 * plain_mlups * 1e6 / (mean_nodes * mean_steps)   # ~80 % of the plain form's capacity
-    base = inputs.serving_arrivals(count=args.serve_requests, rate_per_s=rate, seed=seed, grids=grids,
+    base = inputs.serving_arrivals(count=count, rate_per_s=rate, seed=seed, grids=grids,
                                    steps_lo=lo, steps_hi=hi)
     out = {"requests": len(base), "arrival_rate_per_s": rate, "step_range": [lo, hi],
-           "note": f"step counts of the 1e4..5e5 serving trace scaled by {scale}", "forms": []}
-    for name, batched, prec in (("plain FP32 (one at a time)", False, 1), ("continuous batching FP16", True, 2)):
+           "note": ("the stated trace: 10k..500k steps" if scale == 1.0 else
+                    f"step counts of the 1e4..5e5 serving trace scaled by {scale}"), "forms": []}
+    forms = [("plain FP32 (one at a time)", False, 1, 150.0), ("continuous batching FP16", True, 2, 150.0)]
+    if args.serve_full:
+        forms.append(("continuous batching FP16, tight budget", True, 2, args.serve_tight_budget_gb))
+    for name, batched, prec, budget_gb in forms:
         trace = [dict(r, params=dict(r["params"], precision=prec)) for r in base]
-        srv = lbm.Server(hbm_budget_bytes=150 * 10 ** 9, max_active=64, batched=batched, quantum=256,
+        srv = lbm.Server(hbm_budget_bytes=int(budget_gb * 1e9), max_active=64, batched=batched, quantum=256,
                          precision=prec, stream=stream)
         res = srv.replay(trace)
         st = srv.stats()
         srv.close()
         lat = np.array([r["finish_s"] - r["submit_s"] for r in res])
+        wait = np.array([r["admit_s"] - r["submit_s"] for r in res])
         span = max(r["finish_s"] for r in res) - min(r["submit_s"] for r in res)
         out["forms"].append({
-            "form": name, "ok": all(r["status"] == 0 for r in res),
+            "form": name, "ok": all(r["status"] == 0 for r in res), "hbm_budget_gb": budget_gb,
             "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
+            "p50_queue_s": float(np.percentile(wait, 50)), "max_queue_s": float(wait.max()),
             "runs_per_s": len(res) / span, "aggregate_mlups": st["node_steps"] / span / 1e6,
             "busy_mlups": st["node_steps"] / max(st["busy_s"], 1e-9) / 1e6,
             "peak_admitted_gb": st["peak_used_bytes"] / 1e9})
     return out
 
-def bench_accuracy(args, lbm, inputs, stream, steps: int = 4000) -> dict:
-    """Error of each storage form against FP64 on the headline cavity: melt
-    fraction and hot-wall Nusselt number after `steps` steps.  The reference is
-    the FP64 GPU path, which the parity tests hold to 1e-10 of the FP64 oracle."""
-    res = {}
-    for fprec in (0, 1, 2, 3):
-        s = lbm.Solver(inputs.cavity(args.n, precision=fprec), stream=stream)
-        s.step(steps)
-        d = s.diag()
-        s.close()
-        res[fprec] = d
-    ref = res[0]
-    out = {"workload": f"{args.n}x{args.n} cavity, {steps} steps", "reference": "FP64 (GPU path)",
-           "melt_frac": ref["melt_frac"], "nu_hot": ref["nu_hot"], "forms": []}
-    for fprec in (1, 2, 3):
-        out["forms"].append({"precision": PREC_NAMES[fprec],
-                             "melt_frac_rel_err": abs(res[fprec]["melt_frac"] / ref["melt_frac"] - 1.0),
-                             "nu_hot_rel_err": abs(res[fprec]["nu_hot"] / ref["nu_hot"] - 1.0)})
+
+TRAJECTORY = ROOT / "tests" / "golden" / "cavity256_oracle_trajectory.json"
+
+
+def accuracy_forms():
+    """(name, precision, batched) of every form whose error the bench reports."""
+    return (("f64", 0, False), ("f32", 1, False), ("f16", 2, False), ("bf16", 3, False),
+            ("f16 batched (map 3, with three other cavities)", 2, True))
+
+
+def bench_accuracy(args, lbm, inputs, stream) -> dict | None:
+    """Error of each storage form against the FP64 oracle over the full
+    200,000-step solve of the 256 x 256 cavity (to Fo = 0.00153): melt
+    fraction and hot-wall Nusselt number at every checkpoint of the stored
+    oracle trajectory (tests/golden/cavity256_oracle_trajectory.json, written
+    by a script that runs only the oracle).  The batched form advances the
+    cavity in a map-3 batch beside three other cavities."""
+    if args.n != 256 or not TRAJECTORY.exists():
+        return None
+    ref = json.loads(TRAJECTORY.read_text())
+    rows = ref["rows"]
+    out = {"workload": "256x256 cavity, full 200,000-step solve", "reference": "FP64 oracle (stored trajectory)",
+           "checkpoints": [r["steps"] for r in rows], "Fo": [r["Fo"] for r in rows],
+           "melt_frac": [r["melt_frac"] for r in rows], "nu_hot": [r["nu_hot"] for r in rows], "forms": []}
+    for name, prec, batched in accuracy_forms():
+        s = lbm.Solver(inputs.cavity(256, precision=prec), stream=stream)
+        others, b = [], None
+        if batched:
+            others = [lbm.Solver(dict(q, precision=prec), stream=stream)
+                      for q in inputs.batch_draws(count=3, seed=5, n_lo=64, n_hi=160)]
+            b = lbm.Batch([s] + others, autotune=False, stream=stream).configure(128, 3)
+        em, en = [], []
+        for row in rows:
+            k = row["steps"] - s.steps
+            if b is not None:
+                b.step(k)
+            else:
+                s.step(k)
+            d = s.diag()
+            em.append(abs(d["melt_frac"] / row["melt_frac"] - 1.0))
+            en.append(abs(d["nu_hot"] / row["nu_hot"] - 1.0))
+        ok = s.status() == 0
+        if b is not None:
+            b.close()
+        for r in [s] + others:
+            r.close()
+        out["forms"].append({"form": name, "ok": ok, "melt_frac_rel_err": em, "nu_hot_rel_err": en,
+                             "max_melt_frac_rel_err": max(em), "max_nu_hot_rel_err": max(en)})
     return out
 
 
@@ -517,14 +579,27 @@ def main():
             peaks = json.loads((ROOT / "MEASURED_PEAKS.json").read_text()) if (ROOT / "MEASURED_PEAKS.json").exists() else {}
             peak = float(peaks.get("hbm_gbs", 6800.0))
             nodes = pr["nx"] * pr["ny"]
-            achieved = bpu * nodes / (ms / 1e3) / 1e9
+            b_alg = bytes_per_update(pr["thermal_q"], pr["flow"], 1)
+            b_sto = stored_bytes_per_update(pr["thermal_q"], pr["flow"], 1)
+            achieved = b_alg * nodes / (ms / 1e3) / 1e9
+            traffic = measured_traffic(pr["nx"])
             roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                    "frac": achieved / peak, "traffic": measured_traffic(pr["nx"]),
+                    "frac": achieved / peak, "traffic": traffic,
                     "kernel": "fused_step<float, Q_T=5, flow>",
                     "workload": f"square-cavity melting {pr['nx']}x{pr['ny']} FP32 (state {lbm.state_bytes(pr) / 2**30:.2f} GiB)",
-                    "bytes_per_update": bpu, "units_per_launch": nodes,
+                    "bytes_per_update": b_alg,
+                    "bytes_basis": "algorithmic: 19 FP32 populations and the FP32 exchange history, each read and "
+                                   "written once (D2Q9 flow + D2Q5 PCM + D2Q5 metal)",
+                    "overhead_bytes_per_update": b_sto - b_alg,
+                    "overhead": "the low part of the float-float PCM rest population, read and written once",
+                    "units_per_launch": nodes,
                     "mlups": nodes / (ms / 1e3) / 1e6, "avg_launch_us": ms * 1e3,
-                    "peak_source": "measured" if peaks else "fallback"}
+                    "peak_kind": "measured copy bandwidth (STREAM-style copy, read + write bytes), not the HBM "
+                                 "data-sheet rate",
+                    "peak_source": "measured" if peaks else "fallback",
+                    "traffic_source": (f"ncu dram__bytes_read.sum + dram__bytes_write.sum, {ROOFLINE_TRAFFIC['captured']}"
+                                       if traffic else "no capture of the current kernel sources"),
+                    "ncu_gpu__dram_throughput_pct": ROOFLINE_TRAFFIC["gpu__dram_throughput_pct"] if traffic else None}
 
         # many unequal cavities: plain per-run FP32 vs one launch per step for all runs
         batched = None
@@ -535,7 +610,7 @@ def main():
         if not args.no_serving:
             serving = bench_serving(args, lbm, inputs, stream, roof["mlups"] if roof else 30000.0)
 
-        accuracy = None if args.roofline_n <= 0 else bench_accuracy(args, lbm, inputs, stream)
+        accuracy = None if args.no_accuracy else bench_accuracy(args, lbm, inputs, stream)
 
         # every storage form of the same step, on the L2-resident and the HBM-bound cavity
         forms = []
@@ -548,6 +623,7 @@ def main():
                     gbs = b * n * n / (ms / 1e3) / 1e9
                     forms.append({"precision": PREC_NAMES[fprec], "grid": n, "us_per_step": ms * 1e3,
                                   "mlups": n * n / (ms / 1e3) / 1e6, "bytes_per_update": b,
+                                  "overhead_bytes_per_update": stored_bytes_per_update(5, 1, fprec) - b,
                                   "gbs_algorithmic": gbs, "frac_of_measured_hbm": gbs / peak})
 
     if rank != 0:
@@ -563,6 +639,7 @@ def main():
         "roofline": roof,
         "l2_resident": {"avg_launch_us": launch_ms_small * 1e3,
                         "gbs_algorithmic": bpu * cells / (launch_ms_small / 1e3) / 1e9,
+                        "bytes_per_update": bpu,
                         "note": "256x256 state (10 MB) is L2-resident; launch-to-launch time inside CUDA graphs"},
         "forms": forms if args.roofline_n > 0 else None,
         "accuracy": accuracy,

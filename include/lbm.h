@@ -297,8 +297,13 @@ const char* lbm_strerror(int code);
  *
  * lbm_batch_step enqueues nsteps steps of every run on the batch's stream
  * and advances each run's step count.  Use the runs' own calls (fields,
- * diagnostics, checkpoints, lbm_step) only on the same stream or after
- * synchronising it.  A run whose sticky status is set stops the batch
+ * diagnostics, checkpoints, lbm_step, lbm_set_step_form) only on the same
+ * stream or after synchronising it.  A run stepped by lbm_step between
+ * batched steps holds its state in the other copy after an odd number of
+ * steps; the next lbm_batch_step notices (as it notices a changed step form),
+ * waits for the batch's stream, rewrites the parameter blocks and work list
+ * and drops its replayed graph, then advances every run from its current
+ * state.  A run whose sticky status is set stops the batch
  * (LBM_ERR_STATE).  lbm_batch_info reports the tile count, the chosen width
  * cap and map (0-3), the grid size (0 for map 3) and the tuned microseconds
  * per step.
@@ -379,10 +384,18 @@ int lbm_server_destroy(lbm_server* s);
  * Who needs it: code whose device memory all belongs to another allocator (a
  * framework's memory pool, or a serving loop that has already handed out its
  * HBM budget) and latency-critical paths where cudaMalloc/cudaFree would
- * synchronise the device.  The call computes the same four FP64 quantities as
+ * synchronise the device.  The call computes the four FP64 quantities of
  * lbm_diag -- out[0] melt fraction, out[1] hot-wall Nusselt number, out[2]
  * total enthalpy, out[3] mass -- from field arrays the caller already holds
  * (for instance written by lbm_fields with dst_on_device = 1), without a handle.
+ * Precision: the sums are FP64, but they see only the fields as stored.  For
+ * LBM_F64 the four values agree with lbm_diag to FP64 rounding.  For the
+ * other modes the fields are FP32: out[0] and out[1] agree with lbm_diag to
+ * FP64 rounding of the same FP32 values, while out[2] and out[3] carry about
+ * 1e-7 relative error -- the H_f field is the high part of the PCM enthalpy
+ * (lbm_diag adds the float-float low part of LBM_F32 and of Dirichlet wall
+ * nodes) and rho is rounded to FP32 (lbm_diag sums 1 + (rho - 1)).  Use
+ * lbm_diag for conservation-drift checks.
  *
  * Arguments: p describes the run (as for lbm_create); T_f, T_s, f_l, rho and
  * H_f are device arrays [ny][nx] of the run's element type (LBM_FIELD_* of
@@ -401,8 +414,10 @@ int lbm_server_destroy(lbm_server* s);
  * threads on the same device) race and give wrong sums; serialise them.
  *
  * Set-up: the first call on each device looks up the array's device address
- * (cudaGetSymbolAddress, with that device current) and caches it; make that
- * first call before any stream capture.
+ * (cudaGetSymbolAddress, with that device current) and caches it together
+ * with the ID of the device's current context; a call in a new context (after
+ * cudaDeviceReset) looks it up again.  Make the first call on a device, and
+ * the first call after a reset, before any stream capture.
  *
  * Errors: LBM_ERR_ARG for a null pointer or invalid p (LBM_ERR_STABILITY as
  * in lbm_derive), LBM_ERR_TOO_LARGE as above, LBM_ERR_CUDA if the symbol

@@ -869,7 +869,8 @@ struct lbm_batch {
     char* dev = nullptr;          // params[n][2] then tiles
     size_t params_stride = 0;     // bytes of one StepParams
     void* params = nullptr;
-    std::vector<int> flip;        // run's current copy relative to the batch parity at creation
+    std::vector<int> flip;        // run's current copy relative to the batch parity
+    std::vector<int> form;        // each run's step form when the parameters were uploaded
     std::vector<int> shape;       // map 3: block shape of each run (index into kShapes)
     lbmk::Tile* tiles = nullptr;
     size_t tile_capacity = 0;     // tiles that fit in the allocation
@@ -1115,6 +1116,29 @@ int build_batch_graph(lbm_batch* b) {
     return LBM_OK;
 }
 
+// A run advanced by its own calls since the last batched step (lbm_step on
+// the same stream, or after a synchronisation) may now read the other copy,
+// and lbm_set_step_form may have changed its kernel.  Re-derive each run's
+// copy relative to the batch parity; where anything moved, wait for the work
+// in flight, rewrite the parameter blocks and the work list, and drop the
+// replayed graph (map 3 bakes every run's copy and kernel into it).
+int resync_runs(lbm_batch* b) {
+    bool moved = false;
+    for (size_t r = 0; r < b->runs.size(); ++r) {
+        const int want = b->runs[r]->cur ^ b->parity;
+        if (b->flip[r] != want || b->form[r] != b->runs[r]->form) moved = true;
+        b->flip[r] = want;
+        b->form[r] = b->runs[r]->form;
+    }
+    if (!moved) return LBM_OK;
+    if (cudaStreamSynchronize(b->stream) != cudaSuccess) {
+        cudaGetLastError();
+        return LBM_ERR_CUDA;
+    }
+    batch_destroy_graph(b);
+    return upload_batch(b, make_tiles(b->runs, b->flip, b->width_cap));
+}
+
 int batch_advance(lbm_batch* b, int64_t n) {
     auto single = [&]() -> int {
         cudaError_t e = cudaSuccess;
@@ -1213,7 +1237,10 @@ int lbm_batch_create(lbm_handle* const* runs, int32_t n_runs, int32_t autotune, 
     b->release = runs[0]->release;
     b->ctx = runs[0]->ctx;
     b->parity = 0;
-    for (int r = 0; r < n_runs; ++r) b->flip.push_back(runs[r]->cur);
+    for (int r = 0; r < n_runs; ++r) {
+        b->flip.push_back(runs[r]->cur);
+        b->form.push_back(runs[r]->form);
+    }
     // the single-run kernel's own shape rule until tuned (64 x 2 small, 128 x 1 large)
     for (int r = 0; r < n_runs; ++r) {
         const dim3 sb = lbmk::step_block(runs[r]->p.nx, runs[r]->p.ny);
@@ -1253,6 +1280,7 @@ int lbm_batch_create(lbm_handle* const* runs, int32_t n_runs, int32_t autotune, 
                 ok = false;
                 break;
             }
+            c->form = h->form;   // time the kernels the runs themselves will take
             clones.push_back(c);
         }
         if (ok) {
@@ -1323,7 +1351,8 @@ int lbm_batch_step(lbm_batch* b, int64_t nsteps) {
     if (!b || nsteps < 0) return LBM_ERR_ARG;
     for (lbm_handle* h : b->runs)
         if (h->sticky != LBM_OK) return LBM_ERR_STATE;
-    const int rc = batch_advance(b, nsteps);
+    int rc = resync_runs(b);
+    if (rc == LBM_OK) rc = batch_advance(b, nsteps);
     for (size_t r = 0; r < b->runs.size(); ++r) {
         lbm_handle* h = b->runs[r];
         h->cur = b->flip[r] ^ b->parity;

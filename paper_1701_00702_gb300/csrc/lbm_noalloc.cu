@@ -12,6 +12,9 @@
 #include <cstdint>
 #include <mutex>
 
+#include <cuda.h>
+#include <cuda_runtime.h>
+
 #include "lbm.h"
 
 namespace {
@@ -89,25 +92,68 @@ __global__ void __launch_bounds__(kThreads) finish(const double* __restrict__ pa
 }
 
 std::mutex g_setup_mutex;
-double* g_partials_addr[kMaxDevices] = {nullptr};
 
-// Device address of g_partials on the current device, looked up once per device.
+// The device address of g_partials belongs to the module as loaded in one
+// CUDA context.  It is looked up once per device and context: a context
+// created after cudaDeviceReset may load the module elsewhere, so each
+// cached address carries the unique ID of the context it was taken in.
+struct Slot {
+    double* addr = nullptr;
+    unsigned long long ctx_id = 0;
+};
+Slot g_slots[kMaxDevices];
+
+using CtxGetCurrentFn = CUresult (*)(CUcontext*);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long*);
+CtxGetCurrentFn g_ctx_get_current = nullptr;
+CtxGetIdFn g_ctx_get_id = nullptr;
+
+// Unique ID of the current context (driver entry points, looked up once).
+int current_context_id(unsigned long long* id) {
+    if (!g_ctx_get_current || !g_ctx_get_id) {
+        cudaDriverEntryPointQueryResult q1 = cudaDriverEntryPointSymbolNotFound, q2 = q1;
+        void* f1 = nullptr;
+        void* f2 = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) != cudaSuccess ||
+            cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) != cudaSuccess ||
+            q1 != cudaDriverEntryPointSuccess || q2 != cudaDriverEntryPointSuccess || !f1 || !f2) {
+            cudaGetLastError();
+            return LBM_ERR_CUDA;
+        }
+        g_ctx_get_current = reinterpret_cast<CtxGetCurrentFn>(f1);
+        g_ctx_get_id = reinterpret_cast<CtxGetIdFn>(f2);
+    }
+    CUcontext ctx = nullptr;
+    if (g_ctx_get_current(&ctx) != CUDA_SUCCESS || !ctx || g_ctx_get_id(ctx, id) != CUDA_SUCCESS)
+        return LBM_ERR_CUDA;
+    return LBM_OK;
+}
+
+// Device address of g_partials on the current device: looked up (with that
+// device current) on the first call in each context, then cached.
 int partials_on_current_device(double** out) {
     int dev = -1;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+    // cudaSetDevice makes the device's primary context current on this thread
+    // (creating it if needed) without allocating anything
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices || cudaSetDevice(dev) != cudaSuccess) {
         cudaGetLastError();
         return LBM_ERR_CUDA;
     }
     std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (!g_partials_addr[dev]) {
+    unsigned long long id = 0;
+    const int rc = current_context_id(&id);
+    if (rc != LBM_OK) return rc;
+    Slot& slot = g_slots[dev];
+    if (!slot.addr || slot.ctx_id != id) {
         void* p = nullptr;
         if (cudaGetSymbolAddress(&p, g_partials) != cudaSuccess || !p) {
             cudaGetLastError();
             return LBM_ERR_CUDA;
         }
-        g_partials_addr[dev] = static_cast<double*>(p);
+        slot.addr = static_cast<double*>(p);
+        slot.ctx_id = id;
     }
-    *out = g_partials_addr[dev];
+    *out = slot.addr;
     return LBM_OK;
 }
 

@@ -14,12 +14,22 @@
 #include <vector>
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "lbm.h"
 
 namespace {
 
 using Clock = std::chrono::steady_clock;
+
+// NVTX range for the lifetime of a scope (a no-op unless a profiler that
+// records NVTX ranges is attached).
+struct Range {
+    explicit Range(const char* name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+    Range(const Range&) = delete;
+    Range& operator=(const Range&) = delete;
+};
 
 struct Request {
     int64_t id = 0;
@@ -88,6 +98,28 @@ void finish(lbm_server* s, Request& r, int status) {
     s->done.push_back(out);
 }
 
+// Admission in arrival order, while a slot and the budget allow.
+void admit(lbm_server* s) {
+    const Range range("admit");
+    while (!s->queue.empty() && (int)s->active.size() < s->max_active &&
+           s->used + s->queue.front().bytes <= s->budget) {
+        Request r = s->queue.front();
+        const int rc = lbm_create_ex(&r.p, s->stream, s->alloc, s->release, s->ctx, &r.h);
+        if (rc == LBM_ERR_OOM && !s->active.empty()) break;   // wait for memory to come back
+        s->queue.pop_front();
+        r.admit_s = since(s);
+        s->used += r.bytes;
+        s->peak_used = std::max(s->peak_used, s->used);
+        if (rc != LBM_OK) {
+            r.h = nullptr;
+            finish(s, r, rc);
+            continue;
+        }
+        s->active.push_back(r);
+        s->changed = true;
+    }
+}
+
 }  // namespace
 
 extern "C" {
@@ -152,26 +184,11 @@ int lbm_server_submit(lbm_server* s, const lbm_params* p, int64_t nsteps, int64_
 
 int lbm_server_tick(lbm_server* s, int32_t* n_active, int32_t* n_queued, int32_t* n_done) {
     if (!s) return LBM_ERR_ARG;
-    // admission in arrival order, while a slot and the budget allow
-    while (!s->queue.empty() && (int)s->active.size() < s->max_active &&
-           s->used + s->queue.front().bytes <= s->budget) {
-        Request r = s->queue.front();
-        const int rc = lbm_create_ex(&r.p, s->stream, s->alloc, s->release, s->ctx, &r.h);
-        if (rc == LBM_ERR_OOM && !s->active.empty()) break;   // wait for memory to come back
-        s->queue.pop_front();
-        r.admit_s = since(s);
-        s->used += r.bytes;
-        s->peak_used = std::max(s->peak_used, s->used);
-        if (rc != LBM_OK) {
-            r.h = nullptr;
-            finish(s, r, rc);
-            continue;
-        }
-        s->active.push_back(r);
-        s->changed = true;
-    }
+    const Range tick_range("lbm_server_tick");
+    admit(s);
     int rc = LBM_OK;
     if (!s->active.empty()) {
+        const Range advance_range("advance");
         int64_t q = s->quantum;
         for (const Request& r : s->active) q = std::min(q, r.remaining);
         const auto t = Clock::now();
@@ -201,6 +218,7 @@ int lbm_server_tick(lbm_server* s, int32_t* n_active, int32_t* n_queued, int32_t
         bool any = false;
         for (const Request& r : s->active) any = any || r.remaining == 0 || rc != LBM_OK;
         if (any) {
+            const Range retire_range("retire");
             drop_batch(s);
             std::vector<Request> keep;
             for (Request& r : s->active) {

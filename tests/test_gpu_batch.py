@@ -231,3 +231,72 @@ def test_node_pair_runs_under_map_3_equal_lbm_step(lbm, prec):
     b.close()
     for s in runs + solo:
         s.close()
+
+
+@pytest.mark.parametrize("mapping", [0, 3])
+def test_a_run_stepped_on_its_own_between_batch_steps(lbm, mapping):
+    """lbm_step on a member run between batched steps (same stream) moves that
+    run to the other state copy; the next batched step follows it instead of
+    advancing the stale copy, and every run matches its individually stepped
+    twin."""
+    ps = _mixed_params(1)
+    runs = [lbm.Solver(p) for p in ps]
+    twins = [lbm.Solver(p) for p in ps]
+    b = lbm.Batch(runs, autotune=False).configure(128, mapping)
+    b.step(70)                  # one replayed graph and six single steps
+    runs[1].step(1)             # an odd number of the run's own steps
+    runs[3].step(2)
+    b.step(70)
+    for k, t in enumerate(twins):
+        t.step(140 + (1 if k == 1 else 2 if k == 3 else 0))
+    for r, t in zip(runs, twins):
+        assert r.steps == t.steps
+        assert _same_state(r, t, mapping == 3)
+    b.close()
+    for s in runs + twins:
+        s.close()
+
+
+# one step from a state on the storage grid, as the single-run parity tests:
+# FP64 1e-12, FP32 5e-6, FP16/BF16 four 16-bit roundings (2 x 2^-11, 2 x 2^-8)
+ORACLE_TOL = {0: 1e-12, 1: 5e-6, 2: 8 * 2.0 ** -11, 3: 8 * 2.0 ** -8}
+
+
+@pytest.mark.parametrize("prec", [0, 1, 2, 3])
+@pytest.mark.parametrize("mapping", [0, 1, 2])
+def test_tile_maps_match_the_oracle(lbm, oracle_mod, prec, mapping):
+    """The tile kernel (maps 0-2: many runs in one launch per step, parameters
+    from each run's block in global memory) advances every run of a batch as
+    the FP64 oracle advances it alone, element by element, after one and after
+    three steps from random states (solid, mushy and liquid nodes; walled,
+    half-periodic and periodic runs; ragged tiles)."""
+    shapes = [(131, 7, 0, 0), (70, 33, 1, 0), (64, 64, 1, 1)]
+    runs, orcs = [], []
+    for k, (nx, ny, px, py) in enumerate(shapes):
+        p = inputs.cavity(nx, ny=ny, precision=prec, periodic_x=px, periodic_y=py, L_char=100.0, Ra=1e7)
+        lc = oracle_mod.lattice_config(p)
+        F, G, Hm, dT = inputs.random_state(nx, ny, 5, seed=90 + k, f_base=W9.ravel(),
+                                           H_range=(lc["T_fs"] - 0.3, lc["T_fl"] + lc["L_a"] + 0.3))
+        dt = np.float64 if prec == 0 else np.float32
+        s = lbm.Solver(p)
+        s.set_state((F - W9).astype(dt), G.astype(dt), Hm.astype(dt), dT.astype(dt))
+        f0, g0, h0, d0 = s.get_state()          # the oracle starts from what the solver holds
+        o = oracle_mod.Oracle(p)
+        o.set_state(f0.astype(np.float64) + W9, g0.astype(np.float64), h0.astype(np.float64),
+                    d0.astype(np.float64))
+        runs.append(s)
+        orcs.append(o)
+    b = lbm.Batch(runs, autotune=False).configure(64, mapping)
+    for steps, margin in ((1, 1.0), (2, 2.0)):
+        b.step(steps)
+        for s, o in zip(runs, orcs):
+            o.run(steps)
+            f, g, h, d = s.get_state()
+            Fo, Go, Ho, Do = o.state()
+            for a, ref, name in ((f, Fo - W9, "f - w"), (g, Go, "g"), (h, Ho, "h"), (d, Do, "dT")):
+                scale = max(np.abs(ref).max(), 1.0 if name == "dT" else 1e-3)
+                err = np.abs(a.astype(np.float64) - ref).max() / scale
+                assert err < margin * ORACLE_TOL[prec], (s.params["nx"], steps, name, err)
+    b.close()
+    for s in runs:
+        s.close()
