@@ -551,9 +551,7 @@ int lbm_step_form_for(const lbm_params* p, int32_t form, int32_t* used) {
     if (!p || !used || form < LBM_STEP_FORM_AUTO || form > LBM_STEP_FORM_PAIRS) return LBM_ERR_ARG;
     const int rc = derive_impl(p, nullptr);
     if (rc != LBM_OK) return rc;
-    *used = lbmk::pairs_for(p->precision, p->thermal_q, p->flow, p->solid_scheme, (long long)p->nx * p->ny, form)
-                ? LBM_STEP_FORM_PAIRS
-                : LBM_STEP_FORM_SINGLE;
+    *used = lbmk::form_for(p->precision, p->thermal_q, p->flow, p->solid_scheme, (long long)p->nx * p->ny, form);
     return LBM_OK;
 }
 

@@ -533,36 +533,53 @@ __device__ __forceinline__ int col_off(int x) {
 
 // Pull streaming around node (xs, ys): the population along e_i comes from
 // xs - e_i.  The index wrap is also correct for interior nodes of a walled
-// direction, which never reach the edge.
+// direction, which never reach the edge.  PullAt holds the addressing (one
+// 64-bit row pointer per source row, one 32-bit offset per source column);
+// pull_flow and pull_thermal load one side each, so that the flow and the
+// thermal lattices of a node can also be pulled by two different threads.
+// Source column and row (x - e_x, y - e_y) of direction q, D2Q9 order of Eq. 11,
+// as 0 (x - 1 or y - 1), 1 (x or y), 2 (x + 1 or y + 1): columns 1 0 1 2 1 0 2 2 0,
+// rows 1 1 0 1 2 0 0 2 2, two bits per direction.
+__host__ __device__ constexpr int src_col(int q) { return (0xa191 >> (2 * q)) & 3; }
+__host__ __device__ constexpr int src_row(int q) { return (0x28245 >> (2 * q)) & 3; }
+
 template <int M, int QT, bool FLOW>
-__device__ __forceinline__ void pull_moments(const StepParams<typename ModeTraits<M>::R>& P, int xs, int ys,
-                                             NodeState<M, QT, FLOW>& n) {
+struct PullAt {
+    const char* row[3];
+    int dc[3];
+    int xm, xs, xp, c0;
+    __device__ __forceinline__ PullAt(const StepParams<typename ModeTraits<M>::R>& P, int x, int ys) : xs(x) {
+        xm = xs == 0 ? P.nx - 1 : xs - 1;
+        xp = xs == P.nx - 1 ? 0 : xs + 1;
+        const int ym = ys == 0 ? P.ny - 1 : ys - 1;
+        const int yp = ys == P.ny - 1 ? 0 : ys + 1;
+        const int rb = P.cpr * Chunk<M, QT, FLOW>::bytes;
+        c0 = col_off<M, QT, FLOW>(xs);
+        const char* own = P.src + ((long long)ys * rb + c0);
+        row[0] = own + (long long)(ym - ys) * rb;
+        row[1] = own;
+        row[2] = own + (long long)(yp - ys) * rb;
+        dc[0] = col_off<M, QT, FLOW>(xm) - c0;
+        dc[1] = 0;
+        dc[2] = col_off<M, QT, FLOW>(xp) - c0;
+    }
+    // the source node of direction q: its element in bulk plane 0
+    __device__ __forceinline__ const typename ModeTraits<M>::B* src(int q) const {
+        return reinterpret_cast<const typename ModeTraits<M>::B*>(row[src_row(q)] + dc[src_col(q)]);
+    }
+};
+
+// Flow moments of the pulled populations (Eqs. 13, 15), deviation form.
+template <int M, int QT, bool FLOW>
+__device__ __forceinline__ void pull_flow(const StepParams<typename ModeTraits<M>::R>& P, const PullAt<M, QT, FLOW>& a,
+                                          NodeState<M, QT, FLOW>& n) {
     using R = typename ModeTraits<M>::R;
-    using B = typename ModeTraits<M>::B;
-    using PL = Planes<M, QT, FLOW>;
-    constexpr int ND = FLOW ? 9 : QT;   // directions pulled
-    const int xm = xs == 0 ? P.nx - 1 : xs - 1;
-    const int xp = xs == P.nx - 1 ? 0 : xs + 1;
-    const int ym = ys == 0 ? P.ny - 1 : ys - 1;
-    const int yp = ys == P.ny - 1 ? 0 : ys + 1;
-    // source column and row (x - e_x, y - e_y) of direction q, D2Q9 order of Eq. 11
-    constexpr int ci[9] = {1, 0, 1, 2, 1, 0, 2, 2, 0};
-    constexpr int ri[9] = {1, 1, 0, 1, 2, 0, 0, 2, 2};
-    // one 64-bit row pointer per source row, one 32-bit offset per source column
-    const int rb = P.cpr * Chunk<M, QT, FLOW>::bytes;
-    const int c0 = col_off<M, QT, FLOW>(xs);
-    const char* own = P.src + ((long long)ys * rb + c0);
-    const char* row[3] = {own + (long long)(ym - ys) * rb, own, own + (long long)(yp - ys) * rb};
-    const int dc[3] = {col_off<M, QT, FLOW>(xm) - c0, 0, col_off<M, QT, FLOW>(xp) - c0};
-    const B* sb[ND];   // the source node's element in bulk plane 0
-#pragma unroll
-    for (int q = 0; q < ND; ++q) sb[q] = reinterpret_cast<const B*>(row[ri[q]] + dc[ci[q]]);
     if constexpr (FLOW) {
-        R f0 = ldb<M>(sb[0]);
+        R f0 = ldb<M>(a.src(0));
         V2<R> F[4];
 #pragma unroll
         for (int j = 0; j < 4; ++j)
-            F[j] = {ldb<M>(sb[2 * j + 1] + (2 * j + 1) * kChunk), ldb<M>(sb[2 * j + 2] + (2 * j + 2) * kChunk)};
+            F[j] = {ldb<M>(a.src(2 * j + 1) + (2 * j + 1) * kChunk), ldb<M>(a.src(2 * j + 2) + (2 * j + 2) * kChunk)};
         if constexpr (M == MODE_F16) {
             constexpr R is = R(1.0 / 1024.0);
             f0 *= is;
@@ -576,31 +593,40 @@ __device__ __forceinline__ void pull_moments(const StepParams<typename ModeTrait
         n.mp[4] = m[2].x; n.mp[6] = m[2].y;
         n.mp[7] = m[3].x; n.mp[8] = m[3].y;
     }
+}
+
+// PCM and metal moments of the pulled populations (Eqs. 33, 44, B1).
+template <int M, int QT, bool FLOW>
+__device__ __forceinline__ void pull_thermal(const StepParams<typename ModeTraits<M>::R>& P,
+                                             const PullAt<M, QT, FLOW>& a, NodeState<M, QT, FLOW>& n) {
+    using R = typename ModeTraits<M>::R;
+    using PL = Planes<M, QT, FLOW>;
     V2<R> t[QT];   // (g_q, h_q)
     if constexpr (kSplit<M>) {
         const float* sw[QT];   // the source node's element in wide plane 0 (PCM rest; metal rest follows)
 #pragma unroll
         for (int q = 0; q < QT; ++q) {
-            const int dw = col_off<M, QT, FLOW, true>(ci[q] == 0 ? xm : (ci[q] == 1 ? xs : xp)) - c0;
-            sw[q] = reinterpret_cast<const float*>(row[ri[q]] + dw);
+            const int dw = col_off<M, QT, FLOW, true>(src_col(q) == 0 ? a.xm : (src_col(q) == 1 ? a.xs : a.xp)) - a.c0;
+            sw[q] = reinterpret_cast<const float*>(a.row[src_row(q)] + dw);
         }
         t[0] = {__ldg(sw[0]), __ldg(sw[0] + kChunk)};
 #pragma unroll
         for (int q = 1; q < QT; ++q) {   // deviation + reference of the sending node
-            const V2<R> dev = {ldb<M>(sb[q] + PL::pcm(q) * kChunk), ldb<M>(sb[q] + PL::met(q) * kChunk)};
+            const V2<R> dev = {ldb<M>(a.src(q) + PL::pcm(q) * kChunk), ldb<M>(a.src(q) + PL::met(q) * kChunk)};
             const V2<R> ref = {pcm_ref(P, __ldg(sw[q])), __ldg(sw[q] + kChunk)};
             t[q] = fma2(P.wmv[QT == 5 ? 1 : q], ref, dev);   // D2Q5: one weight varpi/4 for all movers (App. B)
         }
     } else {
 #pragma unroll
-        for (int q = 0; q < QT; ++q) t[q] = {ldb<M>(sb[q] + PL::pcm(q) * kChunk), ldb<M>(sb[q] + PL::met(q) * kChunk)};
+        for (int q = 0; q < QT; ++q)
+            t[q] = {ldb<M>(a.src(q) + PL::pcm(q) * kChunk), ldb<M>(a.src(q) + PL::met(q) * kChunk)};
     }
     fwd2<R, QT>(t, n.th);
     n.Hlo = R(0);
     n.Elo = R(0);
     if constexpr (kComp<M>) {
         // H = (g_0 hi + g_0 lo) + sum of movers, without rounding loss
-        const float lo = ldb<M>(sb[0] + PL::lo * kChunk);
+        const float lo = ldb<M>(a.src(0) + PL::lo * kChunk);
         float g[QT];
 #pragma unroll
         for (int q = 0; q < QT; ++q) g[q] = t[q].x;
@@ -610,14 +636,29 @@ __device__ __forceinline__ void pull_moments(const StepParams<typename ModeTrait
     }
 }
 
-// Macroscopic state from the moments (Eqs. 21, 23-25, 37-39, 48, 7).
 template <int M, int QT, bool FLOW>
-__device__ __forceinline__ void macro(const StepParams<typename ModeTraits<M>::R>& P, NodeState<M, QT, FLOW>& n,
-                                      bool wall) {
-    using R = typename ModeTraits<M>::R;
+__device__ __forceinline__ void pull_moments(const StepParams<typename ModeTraits<M>::R>& P, int xs, int ys,
+                                             NodeState<M, QT, FLOW>& n) {
+    const PullAt<M, QT, FLOW> a(P, xs, ys);
+    pull_flow<M, QT, FLOW>(P, a, n);
+    pull_thermal<M, QT, FLOW>(P, a, n);
+}
+
+// Macroscopic state from the moments (Eqs. 21, 23-25, 37-39, 48, 7): the
+// thermal side (H -> T_f, f_l; T_m) and the flow side, which needs T_f and
+// f_l (buoyancy, Eq. 7; the blended momentum, Eq. 24).
+template <int M, int QT, bool FLOW>
+__device__ __forceinline__ void thermal_macro(const StepParams<typename ModeTraits<M>::R>& P,
+                                              NodeState<M, QT, FLOW>& n) {
     n.H = n.th[0].x;
     enthalpy_state(P, n.H, n.Tf, n.fl);
     n.Tm = n.th[0].y;   // h_0 moment = c_pm T_m, c_pm = 1
+}
+
+template <int M, int QT, bool FLOW>
+__device__ __forceinline__ void flow_macro(const StepParams<typename ModeTraits<M>::R>& P, NodeState<M, QT, FLOW>& n,
+                                           bool wall) {
+    using R = typename ModeTraits<M>::R;
     if constexpr (FLOW) {
         n.drho = n.mp[0];
         n.rho = R(1) + n.drho;
@@ -649,22 +690,59 @@ __device__ __forceinline__ void macro(const StepParams<typename ModeTraits<M>::R
     }
 }
 
-// Full state of node (x, y): interior nodes pull at themselves; wall nodes pull
-// at x_f = x_b + inward normal and apply Eq. 52 in moment space.
 template <int M, int QT, bool FLOW>
-__device__ __forceinline__ void node_state(const StepParams<typename ModeTraits<M>::R>& P, int x, int y,
-                                           NodeState<M, QT, FLOW>& n, bool& wall) {
-    using R = typename ModeTraits<M>::R;
+__device__ __forceinline__ void macro(const StepParams<typename ModeTraits<M>::R>& P, NodeState<M, QT, FLOW>& n,
+                                      bool wall) {
+    thermal_macro<M, QT, FLOW>(P, n);
+    flow_macro<M, QT, FLOW>(P, n, wall);
+}
+
+// Wall nodes: x_f = x_b + inward normal (diagonal at corners) and the side
+// whose temperature rule applies (the left/right wall at corners).
+struct WallAt {
+    bool wall;
+    int xs, ys, side;
+};
+
+template <typename R>
+__device__ __forceinline__ WallAt wall_at(const StepParams<R>& P, int x, int y) {
     const bool wx = !P.per_x && (x == 0 || x == P.nx - 1);
     const bool wy = !P.per_y && (y == 0 || y == P.ny - 1);
-    wall = wx || wy;
-    const int xs = wx ? (x == 0 ? 1 : P.nx - 2) : x;
-    const int ys = wy ? (y == 0 ? 1 : P.ny - 2) : y;
-    pull_moments<M, QT, FLOW>(P, xs, ys, n);
-    macro<M, QT, FLOW>(P, n, false);
-    if (!wall) return;
+    WallAt w;
+    w.wall = wx || wy;
+    w.xs = wx ? (x == 0 ? 1 : P.nx - 2) : x;
+    w.ys = wy ? (y == 0 ? 1 : P.ny - 2) : y;
+    w.side = wx ? (x == 0 ? 0 : 1) : (y == 0 ? 2 : 3);
+    return w;
+}
 
-    const int side = wx ? (x == 0 ? 0 : 1) : (y == 0 ? 2 : 3);
+// Eq. 52 in moment space on the flow lattice: m+(x_b) = m+(x_f) +
+// m^eq(rho_f, u_b = 0) - m^eq(rho_f, u_f), written out so that the rho r
+// parts cancel exactly (n holds the state of x_f).
+template <int M, int QT, bool FLOW>
+__device__ __forceinline__ void flow_wall(const StepParams<typename ModeTraits<M>::R>& P, NodeState<M, QT, FLOW>& n) {
+    using R = typename ModeTraits<M>::R;
+    if constexpr (FLOW) {
+        const R rho = n.rho, ip = P.inv_phi;
+        const R q = R(3) * rho * (n.ux * n.ux + n.uy * n.uy) * ip;
+        n.mp[1] -= q;
+        n.mp[2] += q;
+        n.mp[3] -= rho * n.ux;
+        n.mp[4] += rho * n.ux;
+        n.mp[5] -= rho * n.uy;
+        n.mp[6] += rho * n.uy;
+        n.mp[7] -= rho * (n.ux * n.ux - n.uy * n.uy) * ip;
+        n.mp[8] -= rho * n.ux * n.uy * ip;
+    }
+}
+
+// Eq. 52 on the PCM and metal lattices, with the wall's temperature
+// (Dirichlet: T_f = T_m = T_w, H = H(T_w); adiabatic: those of x_f) and the
+// velocity u_f of x_f in the PCM equilibrium.
+template <int M, int QT, bool FLOW>
+__device__ __forceinline__ void thermal_wall(const StepParams<typename ModeTraits<M>::R>& P,
+                                             NodeState<M, QT, FLOW>& n, int side) {
+    using R = typename ModeTraits<M>::R;
     const bool dirichlet = P.wall_kind[side] == 0;
     R Tb, Hb, Tmb;
     if (dirichlet) {
@@ -677,19 +755,6 @@ __device__ __forceinline__ void node_state(const StepParams<typename ModeTraits<
         Tmb = n.Tm;
     }
     R a[QT], b[QT];
-    if constexpr (FLOW) {
-        // m^eq(rho_f, 0) - m^eq(rho_f, u_f), written out so that the rho r parts cancel exactly
-        const R rho = n.rho, ip = P.inv_phi;
-        const R q = R(3) * rho * (n.ux * n.ux + n.uy * n.uy) * ip;
-        n.mp[1] -= q;
-        n.mp[2] += q;
-        n.mp[3] -= rho * n.ux;
-        n.mp[4] += rho * n.ux;
-        n.mp[5] -= rho * n.uy;
-        n.mp[6] += rho * n.uy;
-        n.mp[7] -= rho * (n.ux * n.ux - n.uy * n.uy) * ip;
-        n.mp[8] -= rho * n.ux * n.uy * ip;
-    }
     neq_pcm<R, QT>(P, Hb, Tb, R(0), R(0), a);
     neq_pcm<R, QT>(P, n.H, n.Tf, n.ux, n.uy, b);
 #pragma unroll
@@ -711,6 +776,20 @@ __device__ __forceinline__ void node_state(const StepParams<typename ModeTraits<
 #pragma unroll
         for (int k = 0; k < QT; ++k) n.th[k].y += a[k] - b[k];
     }
+}
+
+// Full state of node (x, y): interior nodes pull at themselves; wall nodes pull
+// at x_f = x_b + inward normal and apply Eq. 52 in moment space.
+template <int M, int QT, bool FLOW>
+__device__ __forceinline__ void node_state(const StepParams<typename ModeTraits<M>::R>& P, int x, int y,
+                                           NodeState<M, QT, FLOW>& n, bool& wall) {
+    const WallAt w = wall_at(P, x, y);
+    wall = w.wall;
+    pull_moments<M, QT, FLOW>(P, w.xs, w.ys, n);
+    macro<M, QT, FLOW>(P, n, false);
+    if (!wall) return;
+    flow_wall<M, QT, FLOW>(P, n);
+    thermal_wall<M, QT, FLOW>(P, n, w.side);
     macro<M, QT, FLOW>(P, n, true);
 }
 
@@ -787,30 +866,12 @@ __device__ __forceinline__ void store_thermal(const StepParams<typename ModeTrai
 // The fused step
 // ---------------------------------------------------------------------------
 
-// One time step of node (x, y): steps a1-a9 (pull, walls, state, blend,
-// velocity, three collisions, store).  PH = true compiles the Eq. 9 variant's
-// per-node PCM rates in (taken where P.phase_k is set); PH = false leaves them
-// out of the kernel altogether.
-// velocity, three collisions, store).
-template <int M, int QT, bool FLOW, bool PH = false>
-__device__ __forceinline__ void step_node(const StepParams<typename ModeTraits<M>::R>& P, int x, int y) {
+// Flow collision and store of one node (Eqs. 3, 14, 18-20): f* at db, this
+// node's element in flow plane 0 of the next copy.
+template <int M, int QT, bool FLOW>
+__device__ __forceinline__ void flow_collide(const StepParams<typename ModeTraits<M>::R>& P,
+                                             const NodeState<M, QT, FLOW>& n, typename ModeTraits<M>::B* db) {
     using R = typename ModeTraits<M>::R;
-    using PL = Planes<M, QT, FLOW>;
-    NodeState<M, QT, FLOW> n;
-    bool wall;
-    node_state<M, QT, FLOW>(P, x, y, n, wall);
-
-    const int o = y * P.pitch + x;                                  // exchange history
-    // read before any store: the compiler cannot move it above stores that may
-    // alias it, and a load after them adds a memory round trip to the step
-    // (256^2 FP32: 2.47 -> 2.37 us per step)
-    const R dTp = P.dT[o];
-    // this node in the next copy
-    const long long ro = (long long)y * (P.cpr * Chunk<M, QT, FLOW>::bytes);
-    typename ModeTraits<M>::B* db = reinterpret_cast<typename ModeTraits<M>::B*>(P.dst + (ro + col_off<M, QT, FLOW>(x)));
-    float* dw = nullptr;
-    if constexpr (kSplit<M>) dw = reinterpret_cast<float*>(P.dst + (ro + col_off<M, QT, FLOW, true>(x)));
-
     if constexpr (FLOW) {
       if (P.solid_scheme && n.fl <= R(0.5)) {
         // bounce-back solid node: f*_i = f+_opp(i); reversing every link flips the
@@ -859,7 +920,18 @@ __device__ __forceinline__ void step_node(const StepParams<typename ModeTraits<M
         store_flow<M>(db, f0, Fo);
       }
     }
+}
 
+// PCM and metal collisions and stores of one node (Eqs. 32, 36, 43, 47 with
+// the backward difference of Remark III): dTp is the node's exchange history,
+// db/dw its element in bulk and wide plane 0 of the next copy; returns the new
+// history T_m - T_f.
+template <int M, int QT, bool FLOW, bool PH>
+__device__ __forceinline__ typename ModeTraits<M>::R thermal_collide(const StepParams<typename ModeTraits<M>::R>& P,
+                                                                     NodeState<M, QT, FLOW>& n,
+                                                                     typename ModeTraits<M>::R dTp,
+                                                                     typename ModeTraits<M>::B* db, float* dw) {
+    using R = typename ModeTraits<M>::R;
     // exchange sources, Eqs. 36 and 47 with the backward difference of Remark III
     const R dTn = n.Tm - n.Tf;
     const R Sx = R(1.5) * dTn - R(0.5) * dTp;
@@ -874,46 +946,85 @@ __device__ __forceinline__ void step_node(const StepParams<typename ModeTraits<M
     const R hm = hm_base + S_met;
     const R S_pcm = (hm - hm_base) * P.x_pm;
 
-    {
-        // PCM (Eq. 32) and metal (Eq. 43) collisions side by side
-        R neg[QT], nem[QT];
-        neq_pcm<R, QT>(P, n.H, n.Tf, n.ux, n.uy, neg);
-        neq_metal<R, QT>(P, n.Tm, nem);
-        V2<R> nr[QT];
+    // PCM (Eq. 32) and metal (Eq. 43) collisions side by side
+    R neg[QT], nem[QT];
+    neq_pcm<R, QT>(P, n.H, n.Tf, n.ux, n.uy, neg);
+    neq_metal<R, QT>(P, n.Tm, nem);
+    V2<R> nr[QT];
 #pragma unroll
-        for (int k = 1; k < QT; ++k) nr[k] = P.nrate[QT == 5 && k == 2 ? 1 : k];   // D2Q5: j_x, j_y share a rate (App. B)
-        if (PH && P.phase_k) {
-            // Eq. 9 at the node's liquid fraction -> zeta_alpha (Eq. A19) -> zeta_e (Eq. 53)
-            const R za = fast_rcp(R(0.5) + P.ks_c + n.fl * (P.kl_c - P.ks_c));
+    for (int k = 1; k < QT; ++k) nr[k] = P.nrate[QT == 5 && k == 2 ? 1 : k];   // D2Q5: j_x, j_y share a rate (App. B)
+    if (PH && P.phase_k) {
+        // Eq. 9 at the node's liquid fraction -> zeta_alpha (Eq. A19) -> zeta_e (Eq. 53)
+        const R za = fast_rcp(R(0.5) + P.ks_c + n.fl * (P.kl_c - P.ks_c));
 #pragma unroll
-            for (int k = 1; k < QT; ++k) nr[k].x = -(P.zr_a[k] + P.zr_b[k] * za);
-        }
-#pragma unroll
-        for (int k = 1; k < QT; ++k) {
-            // both equilibria vanish for k = 4 (D2Q5) and k = 7, 8 (D2Q9)
-            const bool zero = QT == 5 ? k == 4 : k >= 7;
-            const V2<R> d = zero ? n.th[k] : sub2(n.th[k], V2<R>{neg[k], nem[k]});
-            n.th[k] = fma2(nr[k], d, n.th[k]);
-        }
-        if constexpr (QT == 9) {
-            n.th[1] = fma2(V2<R>{R(-2), R(-2)}, V2<R>{S_pcm, S_met}, n.th[1]);
-            n.th[2] = add2(n.th[2], V2<R>{S_pcm, S_met});
-        } else {
-            n.th[3] = fma2(V2<R>{P.varpi, P.varpi}, V2<R>{S_pcm, S_met}, n.th[3]);
-        }
-        // n_0* = H + S_PCM (n_0 is conserved up to the source, Eq. 32)
-        R hi, lo;
-        if constexpr (kComp<M>) {
-            const FF n0 = ff_add(FF{n.th[0].x, n.Hlo}, S_pcm);
-            hi = n0.hi;
-            lo = n0.lo;
-        } else {
-            hi = n.th[0].x + S_pcm;
-            lo = R(0);
-        }
-        store_thermal<M, QT, FLOW>(P, n.th, hi, lo, hm, db, dw);
+        for (int k = 1; k < QT; ++k) nr[k].x = -(P.zr_a[k] + P.zr_b[k] * za);
     }
-    P.dT[o] = dTn;
+#pragma unroll
+    for (int k = 1; k < QT; ++k) {
+        // both equilibria vanish for k = 4 (D2Q5) and k = 7, 8 (D2Q9)
+        const bool zero = QT == 5 ? k == 4 : k >= 7;
+        const V2<R> d = zero ? n.th[k] : sub2(n.th[k], V2<R>{neg[k], nem[k]});
+        n.th[k] = fma2(nr[k], d, n.th[k]);
+    }
+    if constexpr (QT == 9) {
+        n.th[1] = fma2(V2<R>{R(-2), R(-2)}, V2<R>{S_pcm, S_met}, n.th[1]);
+        n.th[2] = add2(n.th[2], V2<R>{S_pcm, S_met});
+    } else {
+        n.th[3] = fma2(V2<R>{P.varpi, P.varpi}, V2<R>{S_pcm, S_met}, n.th[3]);
+    }
+    // n_0* = H + S_PCM (n_0 is conserved up to the source, Eq. 32)
+    R hi, lo;
+    if constexpr (kComp<M>) {
+        const FF n0 = ff_add(FF{n.th[0].x, n.Hlo}, S_pcm);
+        hi = n0.hi;
+        lo = n0.lo;
+    } else {
+        hi = n.th[0].x + S_pcm;
+        lo = R(0);
+    }
+    store_thermal<M, QT, FLOW>(P, n.th, hi, lo, hm, db, dw);
+    return dTn;
+}
+
+// Node (x, y)'s element in bulk plane 0 and in wide plane 0 (16-bit modes) of
+// the next copy.
+template <int M, int QT, bool FLOW>
+__device__ __forceinline__ typename ModeTraits<M>::B* next_bulk(const StepParams<typename ModeTraits<M>::R>& P, int x,
+                                                                int y) {
+    const long long ro = (long long)y * (P.cpr * Chunk<M, QT, FLOW>::bytes);
+    return reinterpret_cast<typename ModeTraits<M>::B*>(P.dst + (ro + col_off<M, QT, FLOW>(x)));
+}
+
+template <int M, int QT, bool FLOW>
+__device__ __forceinline__ float* next_wide(const StepParams<typename ModeTraits<M>::R>& P, int x, int y) {
+    if constexpr (kSplit<M>) {
+        const long long ro = (long long)y * (P.cpr * Chunk<M, QT, FLOW>::bytes);
+        return reinterpret_cast<float*>(P.dst + (ro + col_off<M, QT, FLOW, true>(x)));
+    } else {
+        return nullptr;
+    }
+}
+
+// One time step of node (x, y): steps a1-a9 (pull, walls, state, blend,
+// velocity, three collisions, store).  PH = true compiles the Eq. 9 variant's
+// per-node PCM rates in (taken where P.phase_k is set); PH = false leaves them
+// out of the kernel altogether.
+template <int M, int QT, bool FLOW, bool PH = false>
+__device__ __forceinline__ void step_node(const StepParams<typename ModeTraits<M>::R>& P, int x, int y) {
+    using R = typename ModeTraits<M>::R;
+    NodeState<M, QT, FLOW> n;
+    bool wall;
+    node_state<M, QT, FLOW>(P, x, y, n, wall);
+
+    const int o = y * P.pitch + x;                                  // exchange history
+    // read before any store: the compiler cannot move it above stores that may
+    // alias it, and a load after them adds a memory round trip to the step
+    // (256^2 FP32: 2.47 -> 2.37 us per step)
+    const R dTp = P.dT[o];
+    typename ModeTraits<M>::B* db = next_bulk<M, QT, FLOW>(P, x, y);
+    float* dw = next_wide<M, QT, FLOW>(P, x, y);
+    flow_collide<M, QT, FLOW>(P, n, db);
+    P.dT[o] = thermal_collide<M, QT, FLOW, PH>(P, n, dTp, db, dw);
 
     // non-finite or runaway state: raise the sticky flag (no trap)
     // (a NaN anywhere fails a comparison; the sum overflows if any term is huge)

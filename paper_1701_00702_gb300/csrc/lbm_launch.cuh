@@ -161,17 +161,19 @@ inline dim3 step_block(int nx, int ny) {
 enum : int { FORM_AUTO = 0, FORM_SINGLE = 1, FORM_PAIRS = 2 };
 constexpr long long kPairMinNodes = 1ll << 22;
 
-// The rule (host code; lbm_step_form_for reports it).  mode: MODE_*.
-inline bool pairs_for(int mode, int qt, int flow, int solid_scheme, long long nodes, int form) {
-    const bool can = mode != MODE_F64 && qt == 5 && flow && !solid_scheme;
-    if (form == FORM_PAIRS) return can;
-    if (form == FORM_SINGLE) return false;
-    return can && (mode == MODE_F16 || mode == MODE_BF16) && nodes >= kPairMinNodes;
+// The rule (host code; lbm_step_form_for reports it): the form a run takes,
+// FORM_SINGLE or FORM_PAIRS.  mode: MODE_*.
+inline int form_for(int mode, int qt, int flow, int solid_scheme, long long nodes, int form) {
+    const bool pairs = mode != MODE_F64 && qt == 5 && flow && !solid_scheme;
+    if (form == FORM_PAIRS) return pairs ? FORM_PAIRS : FORM_SINGLE;
+    if (form == FORM_SINGLE) return FORM_SINGLE;
+    if (pairs && (mode == MODE_F16 || mode == MODE_BF16) && nodes >= kPairMinNodes) return FORM_PAIRS;
+    return FORM_SINGLE;
 }
 
 template <int M>
-inline bool use_pairs(const StepParams<typename ModeTraits<M>::R>& P, int qt, int flow, int form) {
-    return pairs_for(M, qt, flow, P.solid_scheme, (long long)P.nx * P.ny, form);
+inline int form_of(const StepParams<typename ModeTraits<M>::R>& P, int qt, int flow, int form) {
+    return form_for(M, qt, flow, P.solid_scheme, (long long)P.nx * P.ny, form);
 }
 
 // The step kernel of a run, with its grid: one node per thread in blocks of
@@ -185,7 +187,7 @@ template <int M>
 StepLaunch step_launch(const StepParams<typename ModeTraits<M>::R>& P, int qt, int flow, int form, dim3 b) {
     StepLaunch L{nullptr, dim3(), b};
     if constexpr (M != MODE_F64) {
-        if (use_pairs<M>(P, qt, flow, form)) {
+        if (form_of<M>(P, qt, flow, form) == FORM_PAIRS) {
             L.fn = P.phase_k ? (const void*)fused_step_pair<M, true> : (const void*)fused_step_pair<M, false>;
             L.block = dim3(64, 2);
             L.grid = dim3((unsigned)(((P.nx + 1) / 2 + 63) / 64), (unsigned)((P.ny + 1) / 2), 1u);
