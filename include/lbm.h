@@ -192,8 +192,11 @@ int lbm_step(lbm_handle* h, int64_t nsteps);
  * two neighbouring nodes per thread, each FP32 operation one packed
  * instruction for both; taken only by runs in the default configuration (flow,
  * D2Q5 thermal lattices, volumetric blend, FP32/FP16/BF16 storage), the others
- * keep one node per thread.  LBM_STEP_FORM_AUTO (the default): node pairs for
- * FP16/BF16 runs of at least 4,194,304 (2048 x 2048) nodes.  Both forms compute the same
+ * keep one node per thread.  On grids of at least 1,572,864 nodes (state far
+ * beyond L2) each node-pair block also asks L2 for the rows that blocks 48
+ * rows further on will read (bulk L2 prefetch).  LBM_STEP_FORM_AUTO (the
+ * default): node pairs for FP16/BF16 runs of at least 1,572,864 (1536 x 1024)
+ * nodes.  Both forms compute the same
  * step to within a few roundings of the FP32 arithmetic.  Applies to later
  * lbm_step calls and to batches created afterwards; synchronises the run's
  * stream when it drops a captured graph.  LBM_ERR_ARG for another value. */

@@ -239,6 +239,8 @@ lbmk::StepParams<R> make_params(const lbm_handle* h, int from) {
     P.per_x = p.periodic_x;
     P.per_y = p.periodic_y;
     P.solid_scheme = p.solid_scheme;
+    P.prefetch_rows = lbmk::prefetch_rows_for(p.precision, p.thermal_q, p.flow, p.solid_scheme,
+                                              (long long)p.nx * p.ny, h->form);
     for (int s = 0; s < 4; ++s) {
         P.wall_kind[s] = p.wall_kind[s];
         P.wall_T[s] = (R)p.wall_T[s];

@@ -177,6 +177,7 @@ struct StepParams {
     int cpr;             // chunks per row
     int per_x, per_y;
     int solid_scheme;    // 0: volumetric blend; 1: bounce-back where f_l <= 0.5 (Sec. V B)
+    int prefetch_rows;   // > 0: each block asks L2 for its chunk this many rows ahead
     int wall_kind[4];
     R wall_T[4], wall_T_lo[4], wall_H[4], wall_H_lo[4];
     R fscale, finv;      // flow deviations are stored times fscale (a power of two)
@@ -546,7 +547,8 @@ __host__ __device__ constexpr int src_row(int q) { return (0x28245 >> (2 * q)) &
 template <int M, int QT, bool FLOW>
 struct PullAt {
     const char* row[3];
-    int dc[3];
+    int dc[3];   // bulk plane 0 of source columns x - 1, x, x + 1, from this node's
+    int dw[3];   // wide plane 0 of the same columns (16-bit modes)
     int xm, xs, xp, c0;
     __device__ __forceinline__ PullAt(const StepParams<typename ModeTraits<M>::R>& P, int x, int ys) : xs(x) {
         xm = xs == 0 ? P.nx - 1 : xs - 1;
@@ -562,24 +564,37 @@ struct PullAt {
         dc[0] = col_off<M, QT, FLOW>(xm) - c0;
         dc[1] = 0;
         dc[2] = col_off<M, QT, FLOW>(xp) - c0;
+        if constexpr (kSplit<M>) {
+            dw[0] = col_off<M, QT, FLOW, true>(xm) - c0;
+            dw[1] = col_off<M, QT, FLOW, true>(xs) - c0;
+            dw[2] = col_off<M, QT, FLOW, true>(xp) - c0;
+        }
     }
     // the source node of direction q: its element in bulk plane 0
     __device__ __forceinline__ const typename ModeTraits<M>::B* src(int q) const {
         return reinterpret_cast<const typename ModeTraits<M>::B*>(row[src_row(q)] + dc[src_col(q)]);
     }
+    // bulk plane `plane` and wide plane w (16-bit modes) of the source node of direction q
+    __device__ __forceinline__ typename ModeTraits<M>::R bulk(int q, int plane) const {
+        return ldb<M>(src(q) + plane * kChunk);
+    }
+    __device__ __forceinline__ float wide(int q, int w) const {
+        return __ldg(reinterpret_cast<const float*>(row[src_row(q)] + dw[src_col(q)]) + w * kChunk);
+    }
 };
 
-// Flow moments of the pulled populations (Eqs. 13, 15), deviation form.
-template <int M, int QT, bool FLOW>
-__device__ __forceinline__ void pull_flow(const StepParams<typename ModeTraits<M>::R>& P, const PullAt<M, QT, FLOW>& a,
+// Flow moments of the pulled populations (Eqs. 13, 15), deviation form.  A
+// is the accessor of the pulled neighbourhood: PullAt (the state copy in
+// global memory) or a staged copy in shared memory.
+template <int M, int QT, bool FLOW, typename A>
+__device__ __forceinline__ void pull_flow(const StepParams<typename ModeTraits<M>::R>& P, const A& a,
                                           NodeState<M, QT, FLOW>& n) {
     using R = typename ModeTraits<M>::R;
     if constexpr (FLOW) {
-        R f0 = ldb<M>(a.src(0));
+        R f0 = a.bulk(0, 0);
         V2<R> F[4];
 #pragma unroll
-        for (int j = 0; j < 4; ++j)
-            F[j] = {ldb<M>(a.src(2 * j + 1) + (2 * j + 1) * kChunk), ldb<M>(a.src(2 * j + 2) + (2 * j + 2) * kChunk)};
+        for (int j = 0; j < 4; ++j) F[j] = {a.bulk(2 * j + 1, 2 * j + 1), a.bulk(2 * j + 2, 2 * j + 2)};
         if constexpr (M == MODE_F16) {
             constexpr R is = R(1.0 / 1024.0);
             f0 *= is;
@@ -596,37 +611,30 @@ __device__ __forceinline__ void pull_flow(const StepParams<typename ModeTraits<M
 }
 
 // PCM and metal moments of the pulled populations (Eqs. 33, 44, B1).
-template <int M, int QT, bool FLOW>
-__device__ __forceinline__ void pull_thermal(const StepParams<typename ModeTraits<M>::R>& P,
-                                             const PullAt<M, QT, FLOW>& a, NodeState<M, QT, FLOW>& n) {
+template <int M, int QT, bool FLOW, typename A>
+__device__ __forceinline__ void pull_thermal(const StepParams<typename ModeTraits<M>::R>& P, const A& a,
+                                             NodeState<M, QT, FLOW>& n) {
     using R = typename ModeTraits<M>::R;
     using PL = Planes<M, QT, FLOW>;
     V2<R> t[QT];   // (g_q, h_q)
     if constexpr (kSplit<M>) {
-        const float* sw[QT];   // the source node's element in wide plane 0 (PCM rest; metal rest follows)
-#pragma unroll
-        for (int q = 0; q < QT; ++q) {
-            const int dw = col_off<M, QT, FLOW, true>(src_col(q) == 0 ? a.xm : (src_col(q) == 1 ? a.xs : a.xp)) - a.c0;
-            sw[q] = reinterpret_cast<const float*>(a.row[src_row(q)] + dw);
-        }
-        t[0] = {__ldg(sw[0]), __ldg(sw[0] + kChunk)};
+        t[0] = {a.wide(0, 0), a.wide(0, 1)};
 #pragma unroll
         for (int q = 1; q < QT; ++q) {   // deviation + reference of the sending node
-            const V2<R> dev = {ldb<M>(a.src(q) + PL::pcm(q) * kChunk), ldb<M>(a.src(q) + PL::met(q) * kChunk)};
-            const V2<R> ref = {pcm_ref(P, __ldg(sw[q])), __ldg(sw[q] + kChunk)};
+            const V2<R> dev = {a.bulk(q, PL::pcm(q)), a.bulk(q, PL::met(q))};
+            const V2<R> ref = {pcm_ref(P, a.wide(q, 0)), a.wide(q, 1)};
             t[q] = fma2(P.wmv[QT == 5 ? 1 : q], ref, dev);   // D2Q5: one weight varpi/4 for all movers (App. B)
         }
     } else {
 #pragma unroll
-        for (int q = 0; q < QT; ++q)
-            t[q] = {ldb<M>(a.src(q) + PL::pcm(q) * kChunk), ldb<M>(a.src(q) + PL::met(q) * kChunk)};
+        for (int q = 0; q < QT; ++q) t[q] = {a.bulk(q, PL::pcm(q)), a.bulk(q, PL::met(q))};
     }
     fwd2<R, QT>(t, n.th);
     n.Hlo = R(0);
     n.Elo = R(0);
     if constexpr (kComp<M>) {
         // H = (g_0 hi + g_0 lo) + sum of movers, without rounding loss
-        const float lo = ldb<M>(a.src(0) + PL::lo * kChunk);
+        const float lo = a.bulk(0, PL::lo);
         float g[QT];
 #pragma unroll
         for (int q = 0; q < QT; ++q) g[q] = t[q].x;
@@ -778,6 +786,20 @@ __device__ __forceinline__ void thermal_wall(const StepParams<typename ModeTrait
     }
 }
 
+// State of a node from its pulled neighbourhood a (pulled at x_f on walls,
+// then Eq. 52 in moment space).
+template <int M, int QT, bool FLOW, typename A>
+__device__ __forceinline__ void node_state_from(const StepParams<typename ModeTraits<M>::R>& P, const A& a,
+                                                const WallAt& w, NodeState<M, QT, FLOW>& n) {
+    pull_flow<M, QT, FLOW>(P, a, n);
+    pull_thermal<M, QT, FLOW>(P, a, n);
+    macro<M, QT, FLOW>(P, n, false);
+    if (!w.wall) return;
+    flow_wall<M, QT, FLOW>(P, n);
+    thermal_wall<M, QT, FLOW>(P, n, w.side);
+    macro<M, QT, FLOW>(P, n, true);
+}
+
 // Full state of node (x, y): interior nodes pull at themselves; wall nodes pull
 // at x_f = x_b + inward normal and apply Eq. 52 in moment space.
 template <int M, int QT, bool FLOW>
@@ -785,12 +807,8 @@ __device__ __forceinline__ void node_state(const StepParams<typename ModeTraits<
                                            NodeState<M, QT, FLOW>& n, bool& wall) {
     const WallAt w = wall_at(P, x, y);
     wall = w.wall;
-    pull_moments<M, QT, FLOW>(P, w.xs, w.ys, n);
-    macro<M, QT, FLOW>(P, n, false);
-    if (!wall) return;
-    flow_wall<M, QT, FLOW>(P, n);
-    thermal_wall<M, QT, FLOW>(P, n, w.side);
-    macro<M, QT, FLOW>(P, n, true);
+    const PullAt<M, QT, FLOW> a(P, w.xs, w.ys);
+    node_state_from<M, QT, FLOW>(P, a, w, n);
 }
 
 // Post-collision thermal populations of both lattices from their moments
@@ -1051,6 +1069,26 @@ constexpr int kMinBlocks = (QT == 5 && FLOW) ? (M == MODE_F64 ? 1 : 5) : 1;
 // 2.50).
 __device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
+// L2 prefetch ahead of the blocks that will run next (large grids): a block's
+// first thread asks L2, by bulk prefetches (cp.async.bulk.prefetch.L2), for
+// the chunk of x in `rows` rows starting at y0 and for their exchange
+// history, so that the block launched for those rows later finds them in L2
+// instead of waiting for HBM.  No registers or shared memory hold the data;
+// rows past the grid are skipped.
+__device__ __forceinline__ void l2_prefetch(const void* p, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
+template <int M, int QT, bool FLOW>
+__device__ __forceinline__ void prefetch_rows(const StepParams<typename ModeTraits<M>::R>& P, int x, int y0, int rows) {
+    using R = typename ModeTraits<M>::R;
+    constexpr uint32_t cb = Chunk<M, QT, FLOW>::bytes;   // a multiple of 16, as is every chunk's offset
+    for (int y = y0; y < y0 + rows && y < P.ny; ++y) {
+        l2_prefetch(P.src + ((long long)y * P.cpr + (x >> kChunkShift)) * cb, cb);
+        l2_prefetch(P.dT + (long long)y * P.pitch + (x & ~(kChunk - 1)), kChunk * (uint32_t)sizeof(R));
+    }
+}
+
 // One run: one thread per node, 256 threads per block (128 x 2 by default;
 // the batch's map 3 may take other shapes).
 template <int M, int QT, bool FLOW, bool PH>
@@ -1059,6 +1097,8 @@ __global__ void __launch_bounds__(256, (kMinBlocks<M, QT, FLOW>)) fused_step(con
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     if (x >= P.nx || y >= P.ny) return;
     griddep_wait();
+    if (P.prefetch_rows > 0 && threadIdx.x == 0 && threadIdx.y == 0)
+        prefetch_rows<M, QT, FLOW>(P, x, y + P.prefetch_rows, blockDim.y);
     step_node<M, QT, FLOW, PH>(P, x, y);
 }
 
@@ -1181,31 +1221,71 @@ __device__ __forceinline__ void f_from_m5w(const W* n, W* g) {
     g[4] = fma2(wb(-0.5f), n[2], q);
 }
 
-template <int M, bool PH>
-__device__ __forceinline__ void step_pair(const StepParams<float>& P, int x0, int y) {
+// Source of a node pair's pulled neighbourhood in the state copy in global
+// memory: plane `plane` in source row r (0: y - 1, 1: y, 2: y + 1) of the pair
+// (x0, x0 + 1), of its west neighbours (x0 - 1, x0) and of its east ones
+// (x0 + 1, x0 + 2); the wide planes (16-bit modes) of the pair and of the
+// nodes x0 - 1, x0 + 2; the pair's exchange history.
+template <int M>
+struct PairAt {
     using B = typename ModeTraits<M>::B;
-    using PL = Planes<M, 5, true>;
     using CH = Chunk<M, 5, true>;
-    constexpr int es = (int)sizeof(B);
-    constexpr int pb = kChunk * es;   // bytes from one bulk plane to the next
-    // neighbour columns of the pair (periodic wrap; no walls reach here)
-    const int xm = x0 == 0 ? P.nx - 1 : x0 - 1;   // west of x0
-    const int xp = x0 + 2 == P.nx ? 0 : x0 + 2;   // east of x0 + 1
-    const int ym = y == 0 ? P.ny - 1 : y - 1;
-    const int yp = y == P.ny - 1 ? 0 : y + 1;
-    const int rb = P.cpr * CH::bytes;
-    const char* row[3] = {P.src + (long long)ym * rb, P.src + (long long)y * rb, P.src + (long long)yp * rb};
-    const int c0 = col_off<M, 5, true>(x0), cm = col_off<M, 5, true>(xm), cp = col_off<M, 5, true>(xp);
-    // plane q in row r: the pair (x0, x0+1), its west neighbours (x0-1, x0), its east ones (x0+1, x0+2)
-    auto own = [&](int r, int q) { return ldw<M>(row[r] + c0 + q * pb); };
-    auto west = [&](int r, int q) {
+    static constexpr int es = (int)sizeof(B);
+    static constexpr int pb = kChunk * es;   // bytes from one bulk plane to the next
+    static constexpr int wpl = kChunk * 4;   // bytes from one wide plane to the next
+    const char* row[3];
+    int c0, cm, cp, w0, wm, wp;
+    const float* dT;
+    __device__ __forceinline__ PairAt(const StepParams<float>& P, int x0, int y) {
+        // neighbour columns of the pair (periodic wrap; no walls reach here)
+        const int xm = x0 == 0 ? P.nx - 1 : x0 - 1;   // west of x0
+        const int xp = x0 + 2 == P.nx ? 0 : x0 + 2;   // east of x0 + 1
+        const int ym = y == 0 ? P.ny - 1 : y - 1;
+        const int yp = y == P.ny - 1 ? 0 : y + 1;
+        const int rb = P.cpr * CH::bytes;
+        row[0] = P.src + (long long)ym * rb;
+        row[1] = P.src + (long long)y * rb;
+        row[2] = P.src + (long long)yp * rb;
+        c0 = col_off<M, 5, true>(x0);
+        cm = col_off<M, 5, true>(xm);
+        cp = col_off<M, 5, true>(xp);
+        w0 = c0 + CH::wide_off + (x0 & (kChunk - 1)) * 2;   // wide element of x0
+        wm = cm + CH::wide_off + (xm & (kChunk - 1)) * 2;
+        wp = cp + CH::wide_off + (xp & (kChunk - 1)) * 2;
+        dT = P.dT + (long long)y * P.pitch + x0;
+    }
+    __device__ __forceinline__ W own(int r, int q) const { return ldw<M>(row[r] + c0 + q * pb); }
+    __device__ __forceinline__ W west(int r, int q) const {
         return W{ldb<M>(reinterpret_cast<const B*>(row[r] + cm + q * pb)),
                  ldb<M>(reinterpret_cast<const B*>(row[r] + c0 + q * pb))};
-    };
-    auto east = [&](int r, int q) {
+    }
+    __device__ __forceinline__ W east(int r, int q) const {
         return W{ldb<M>(reinterpret_cast<const B*>(row[r] + c0 + q * pb) + 1),
                  ldb<M>(reinterpret_cast<const B*>(row[r] + cp + q * pb))};
-    };
+    }
+    __device__ __forceinline__ W own_wide(int r, int w) const { return ldwf(row[r] + w0 + w * wpl); }
+    __device__ __forceinline__ float west_wide(int r, int w) const {
+        return __ldg(reinterpret_cast<const float*>(row[r] + wm + w * wpl));
+    }
+    __device__ __forceinline__ float east_wide(int r, int w) const {
+        return __ldg(reinterpret_cast<const float*>(row[r] + wp + w * wpl));
+    }
+    __device__ __forceinline__ W history() const { return ldwf(reinterpret_cast<const char*>(dT)); }
+};
+
+// One time step of the node pair (x0, x0 + 1) of row y, its neighbourhood
+// read through the source S (PairAt or a staged copy in shared memory); the
+// results go to the next copy and the history array in global memory.
+template <int M, bool PH, typename S>
+__device__ __forceinline__ void step_pair_from(const StepParams<float>& P, const S& src, int x0, int y) {
+    using PL = Planes<M, 5, true>;
+    using CH = Chunk<M, 5, true>;
+    constexpr int pb = kChunk * (int)sizeof(typename ModeTraits<M>::B);   // plane stride of the next copy
+    const int c0 = col_off<M, 5, true>(x0);
+    const int rb = P.cpr * CH::bytes;
+    auto own = [&](int r, int q) { return src.own(r, q); };
+    auto west = [&](int r, int q) { return src.west(r, q); };
+    auto east = [&](int r, int q) { return src.east(r, q); };
 
     // ---- pull (Eq. 15) and flow moments (Eq. 13) ----
     W f[9] = {own(1, 0), west(1, 1), own(0, 2), east(1, 3), own(2, 4), west(0, 5), east(0, 6), east(2, 7), west(2, 8)};
@@ -1234,17 +1314,12 @@ __device__ __forceinline__ void step_pair(const StepParams<float>& P, int x0, in
     W g[5], h[5];
     W Hlo = wb(0.0f);
     if constexpr (kSplit<M>) {
-        constexpr int wo = CH::wide_off;
-        const int w0 = c0 + wo + (x0 & (kChunk - 1)) * 2;               // wide element of x0
-        const int wm = cm + wo + (xm & (kChunk - 1)) * 2, wp = cp + wo + (xp & (kChunk - 1)) * 2;
-        constexpr int wpl = kChunk * 4;                                  // PCM rest -> metal rest plane
-        const W g0o = ldwf(row[1] + w0), h0o = ldwf(row[1] + w0 + wpl);
+        const W g0o = src.own_wide(1, 0), h0o = src.own_wide(1, 1);
         // senders' rest populations for movers 1..4 (from x - e_q)
-        const W sg[5] = {g0o, W{__ldg(reinterpret_cast<const float*>(row[1] + wm)), g0o.x}, ldwf(row[0] + w0),
-                         W{g0o.y, __ldg(reinterpret_cast<const float*>(row[1] + wp))}, ldwf(row[2] + w0)};
-        const W sh[5] = {h0o, W{__ldg(reinterpret_cast<const float*>(row[1] + wm + wpl)), h0o.x},
-                         ldwf(row[0] + w0 + wpl), W{h0o.y, __ldg(reinterpret_cast<const float*>(row[1] + wp + wpl))},
-                         ldwf(row[2] + w0 + wpl)};
+        const W sg[5] = {g0o, W{src.west_wide(1, 0), g0o.x}, src.own_wide(0, 0), W{g0o.y, src.east_wide(1, 0)},
+                         src.own_wide(2, 0)};
+        const W sh[5] = {h0o, W{src.west_wide(1, 1), h0o.x}, src.own_wide(0, 1), W{h0o.y, src.east_wide(1, 1)},
+                         src.own_wide(2, 1)};
         const W dg[5] = {wb(0.0f), west(1, PL::pcm(1)), own(0, PL::pcm(2)), east(1, PL::pcm(3)), own(2, PL::pcm(4))};
         const W dh[5] = {wb(0.0f), west(1, PL::met(1)), own(0, PL::met(2)), east(1, PL::met(3)), own(2, PL::met(4))};
         const float wg = P.wmv[1].x, wk = P.wmv[1].y;   // D2Q5: one weight for all movers (App. B)
@@ -1342,7 +1417,7 @@ __device__ __forceinline__ void step_pair(const StepParams<float>& P, int x0, in
     // against 70.2 us per step at 2048^2)
     float* dTp_ptr = P.dT + (long long)y * P.pitch + x0;
     const W dTn = sub2(Tm, Tf);
-    const W dTp = ldwf(reinterpret_cast<const char*>(dTp_ptr));
+    const W dTp = src.history();
     const W Sx = fma2(wb(1.5f), dTn, mul2(wb(-0.5f), dTp));
     const W S_met = mul2(wb(-P.a_m), Sx);
     W hm_base;
@@ -1440,6 +1515,12 @@ __device__ __forceinline__ void step_pair(const StepParams<float>& P, int x0, in
     if (bad) atomicOr(P.status, STATUS_UNSTABLE);
 }
 
+template <int M, bool PH>
+__device__ __forceinline__ void step_pair(const StepParams<float>& P, int x0, int y) {
+    const PairAt<M> src(P, x0, y);
+    step_pair_from<M, PH>(P, src, x0, y);
+}
+
 // Node pairs of the default configuration: a block of 64 x 2 threads covers
 // 128 x 2 nodes.  A pair with a wall node or without a second node (or a run
 // of the bounce-back variant) takes step_node.  Seven blocks per SM cap the
@@ -1451,6 +1532,8 @@ __global__ void __launch_bounds__(128, 7) fused_step_pair(const __grid_constant_
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     if (x0 >= P.nx || y >= P.ny) return;
     griddep_wait();
+    if (P.prefetch_rows > 0 && threadIdx.x == 0 && threadIdx.y == 0)
+        prefetch_rows<M, 5, true>(P, x0, y + P.prefetch_rows, blockDim.y);
     const bool single = P.solid_scheme || x0 + 1 >= P.nx || (!P.per_x && (x0 == 0 || x0 + 1 == P.nx - 1)) ||
                         (!P.per_y && (y == 0 || y == P.ny - 1));
     if (single) {

@@ -154,12 +154,14 @@ inline dim3 step_block(int nx, int ny) {
 
 // Step forms: one node per thread (fused_step) or node pairs
 // (fused_step_pair, the default configuration only: flow, D2Q5, volumetric
-// blend, FP32 arithmetic).  Automatic: node pairs for the 16-bit forms from
-// 2048 x 2048 nodes up (measured on GB300: 2048^2 FP16 69.6 against 73.4 us
-// per step; at 1024^2, and in FP32, where the step is bound by HBM, one node
-// per thread is faster).
+// blend, FP32 arithmetic).  Automatic: node pairs, with the L2 prefetch, for
+// the 16-bit forms from 1536 x 1024 nodes up (measured on GB300, us per step:
+// FP16 2048^2 62.1 against 72.7, 2048 x 1024 34.1 against 38.1, 1448^2 37.3
+// against 39.2; at 1024^2, whose state nearly fits in L2, one node per thread
+// is faster, 18.9 against 19.4; in FP32, bound by HBM, one node per thread is
+// faster at every size).
 enum : int { FORM_AUTO = 0, FORM_SINGLE = 1, FORM_PAIRS = 2 };
-constexpr long long kPairMinNodes = 1ll << 22;
+constexpr long long kPairMinNodes = 3ll << 19;
 
 // The rule (host code; lbm_step_form_for reports it): the form a run takes,
 // FORM_SINGLE or FORM_PAIRS.  mode: MODE_*.
@@ -174,6 +176,19 @@ inline int form_for(int mode, int qt, int flow, int solid_scheme, long long node
 template <int M>
 inline int form_of(const StepParams<typename ModeTraits<M>::R>& P, int qt, int flow, int form) {
     return form_for(M, qt, flow, P.solid_scheme, (long long)P.nx * P.ny, form);
+}
+
+// L2 prefetch distance of the node-pair kernel in rows (0: off): grids of at
+// least kPrefetchMinNodes nodes, whose state is far larger than L2, prefetch
+// each block's chunk rows this far ahead, past most of the blocks resident at
+// the same time.  One node per thread takes no prefetch: in FP32 it already
+// runs at the copy bandwidth, and the extra requests slowed it down.
+constexpr long long kPrefetchMinNodes = 3ll << 19;
+constexpr int kPrefetchRowsPairs = 48;
+
+inline int prefetch_rows_for(int mode, int qt, int flow, int solid_scheme, long long nodes, int form) {
+    if (nodes < kPrefetchMinNodes) return 0;
+    return form_for(mode, qt, flow, solid_scheme, nodes, form) == FORM_PAIRS ? kPrefetchRowsPairs : 0;
 }
 
 // The step kernel of a run, with its grid: one node per thread in blocks of

@@ -138,11 +138,13 @@ def test_create_without_gpu_fails_cleanly(lbm):
 
 
 @pytest.mark.parametrize("params,form,expected", [
-    # automatic: node pairs for FP16/BF16 runs of the default configuration from 2048^2 nodes
+    # automatic: node pairs for FP16/BF16 runs of the default configuration from 1536 x 1024 nodes
     (dict(n=2048, precision=2), 0, 2),
     (dict(n=2048, precision=3), 0, 2),
     (dict(n=2048, ny=4096, precision=2), 0, 2),
-    (dict(n=2048, ny=2047, precision=2), 0, 1),            # one row short of 2^22 nodes
+    (dict(n=2048, ny=1024, precision=2), 0, 2),
+    (dict(n=1536, ny=1024, precision=3), 0, 2),
+    (dict(n=1536, ny=1023, precision=2), 0, 1),            # one row short of 1,572,864 nodes
     (dict(n=1024, precision=2), 0, 1),
     (dict(n=2048, precision=1), 0, 1),                      # FP32: HBM-bound, one node per thread
     (dict(n=2048, precision=0), 0, 1),

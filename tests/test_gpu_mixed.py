@@ -210,7 +210,7 @@ def test_config2_size_against_fp32(lbm, prec):
 @pytest.mark.parametrize("eq9", [0, 1])
 def test_node_pair_kernel_one_step(lbm, oracle_mod, prec, rtol, shape, eq9):
     """The two-nodes-per-thread form (LBM_STEP_FORM_PAIRS, automatic for the
-    16-bit forms from 2048^2 nodes) in FP16 and BF16: one step from a random
+    16-bit forms from 1536 x 1024 nodes) in FP16 and BF16: one step from a random
     state against the oracle, with and without the Eq. 9 per-node rates."""
     nx, ny, px, py = shape
     extra = dict(ks_over_kl=0.5, cps_over_cpl=1.4) if eq9 else {}
