@@ -283,20 +283,27 @@ const char* lbm_strerror(int code);
  * kernel once per run and step, each run a chain of kernel nodes in one
  * graph and the chains independent, so small runs overlap large ones; each
  * run's kernel takes one of the block shapes 128 x 2, 64 x 4, 32 x 8, 256 x 1
- * (256 threads), 128 x 1, 64 x 2, 32 x 4 (128) or 64 x 1, 32 x 2 (64).  With autotune = 1 the call times, on freshly created copies of
- * the runs (the runs themselves do not move, but the copies hold as much
- * device memory again while tuning), map 3 with the block shape chosen per
- * size class (grid width <= 64, <= 128, <= 256, wider; one class at a time,
- * keeping the fastest shape) and every combination of tile-width cap (64,
- * 128, 256) and map 0-2, and keeps the fastest; otherwise it takes width cap
- * 128, map 0, and for map 3 lbm_step's own block shapes (64 x 2 up to 32,768
- * nodes, 128 x 1 above).  Under
- * map 3 a batched step equals lbm_step on each run bit for bit.  Maps 0-2
- * inline the same per-node code into another kernel, where the compiler may
- * fuse a few multiply-adds differently: their states can differ from
- * lbm_step's by a few roundings of the arithmetic (FP32: 1-3 ulps in about
- * 1e-4 of the flow populations per step), which a 16-bit store sometimes
- * carries into the last stored bit.
+ * (256 threads), 128 x 1, 64 x 2, 32 x 4 (128) or 64 x 1, 32 x 2 (64).  Map
+ * 4 launches one kernel per step for up to about 40 runs (23 in FP64) at a
+ * time, their parameter blocks in the launch's own parameters: each run in
+ * tiles of w x 128/w nodes (w = 32, 64 or 128, whichever leaves the fewest
+ * of the run's threads idle; node pairs over 128 x 2 nodes for FP16/BF16
+ * runs that lbm_step would step in pairs); larger batches take several such
+ * launches, each group of runs a chain of its own in the graph.  With
+ * autotune = 1 the call times, on freshly created copies of the runs (the
+ * runs themselves do not move, but the copies hold as much device memory
+ * again while tuning), map 3 with the block shape chosen per size class
+ * (grid width <= 64, <= 128, <= 256, wider; one class at a time, keeping the
+ * fastest shape), map 4, and every combination of tile-width cap (64, 128,
+ * 256) and map 0-2, and keeps the fastest; otherwise it takes width cap 128,
+ * map 0, and for map 3 lbm_step's own block shapes (64 x 2 up to 32,768
+ * nodes, 128 x 1 above).  Under map 3 a batched step equals lbm_step on each
+ * run bit for bit.  Maps 0-2 and 4 inline the same per-node code into
+ * another kernel, where the compiler may fuse a few multiply-adds
+ * differently: their states can differ from lbm_step's by a few roundings of
+ * the arithmetic (FP32: 1-3 ulps in about 1e-4 of the flow populations per
+ * step), which a 16-bit store sometimes carries into the last stored bit.  A
+ * run's steps under map 4 do not depend on the other runs of its launch.
  *
  * lbm_batch_step enqueues nsteps steps of every run on the batch's stream
  * and advances each run's step count.  Use the runs' own calls (fields,
@@ -308,8 +315,8 @@ const char* lbm_strerror(int code);
  * and drops its replayed graph, then advances every run from its current
  * state.  A run whose sticky status is set stops the batch
  * (LBM_ERR_STATE).  lbm_batch_info reports the tile count, the chosen width
- * cap and map (0-3), the grid size (0 for map 3) and the tuned microseconds
- * per step.
+ * cap and map (0-4), the grid size (0 for maps 3 and 4) and the tuned
+ * microseconds per step.
  * lbm_batch_destroy synchronises and frees the batch (not its runs).
  * The batch allocates its work list and parameter blocks through the first
  * run's allocation hooks (or the CUDA stream-ordered allocator).
@@ -318,7 +325,7 @@ typedef struct lbm_batch lbm_batch;
 int lbm_batch_create(lbm_handle* const* runs, int32_t n_runs, int32_t autotune, void* cuda_stream,
                      lbm_batch** out);
 int lbm_batch_step(lbm_batch* b, int64_t nsteps);
-/* Forces a tile-width cap (32, 64, 128 or 256) and a map (0-3); synchronises. */
+/* Forces a tile-width cap (32, 64, 128 or 256) and a map (0-4); synchronises. */
 int lbm_batch_configure(lbm_batch* b, int32_t width_cap, int32_t mapping);
 int lbm_batch_info(const lbm_batch* b, int32_t* n_tiles, int32_t* width_cap, int32_t* mapping, int32_t* grid,
                    double* tuned_us_per_step);
@@ -340,14 +347,17 @@ int lbm_batch_destroy(lbm_batch* b);
  *   2. advances all active runs together by min(quantum, the smallest number
  *      of steps any active run still needs) through one lbm_batch (batched =
  *      1; the batch is rebuilt when membership changes, with the tile width
- *      cap and map of lbm_server_configure, default 128 and map 3, the runs'
- *      own kernels in concurrent chains), then synchronises the stream;
+ *      cap and map of lbm_server_configure, default 128 and map 4, every
+ *      active run in one grouped launch per step), then synchronises the
+ *      stream;
  *   3. retires every run that has taken its steps: its FP64 diagnostics
  *      (lbm_diag) go into a result record and its device memory is freed.
  * A request that arrives while others run joins them at the next tick.
  * With batched = 0 the engine is the plain form: one request at a time, in
- * arrival order, each advanced by lbm_step.  With the default map 3 a run is
- * the same alone and in the mix, bit for bit.
+ * arrival order, each advanced by lbm_step.  A run's result is the same
+ * alone and in the mix, bit for bit: under map 4 (the default) a run's steps
+ * do not depend on the other runs of the launch, under map 3 they equal
+ * lbm_step's.
  *
  * All requests of a server share precision, thermal_q and flow (LBM_ERR_ARG
  * otherwise); a request whose state alone exceeds the budget is refused at

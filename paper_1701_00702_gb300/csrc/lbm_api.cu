@@ -4,6 +4,7 @@
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <memory>
 #include <new>
 #include <vector>
 
@@ -872,6 +873,7 @@ struct lbm_batch {
     std::vector<int> flip;        // run's current copy relative to the batch parity
     std::vector<int> form;        // each run's step form when the parameters were uploaded
     std::vector<int> shape;       // map 3: block shape of each run (index into kShapes)
+    std::vector<std::vector<int>> groups;   // map 4: the runs of each grouped launch
     lbmk::Tile* tiles = nullptr;
     size_t tile_capacity = 0;     // tiles that fit in the allocation
     int ntiles = 0, width_cap = 128, chunk = 1, grid = 0, parity = 0, mapping = 0;
@@ -1000,9 +1002,22 @@ int batch_blocks_per_sm(const lbm_batch* b) {
 // contiguous chunks of tiles, 2 persistent blocks striding over the tiles,
 // 3 one single-run kernel per run and step, the runs' chains concurrent in
 // one graph.
+// Map 4: the runs in order, at most kGroupRuns per grouped launch.
+void make_groups(lbm_batch* b) {
+    b->groups.clear();
+    const int cap = b->precision == LBM_F64 ? lbmk::kGroupRuns<double> : lbmk::kGroupRuns<float>;
+    const int n = (int)b->runs.size();
+    for (int r = 0; r < n; r += cap) {
+        std::vector<int> g;
+        for (int k = r; k < std::min(r + cap, n); ++k) g.push_back(k);
+        b->groups.push_back(g);
+    }
+}
+
 void set_mapping(lbm_batch* b, int mapping, int resident_blocks) {
     b->mapping = mapping;
-    if (mapping == 3) {
+    if (mapping == 4) make_groups(b);
+    if (mapping >= 3) {
         b->grid = 0;
         b->chunk = 0;
     } else if (mapping == 0) {
@@ -1092,8 +1107,131 @@ int build_chain_graph(lbm_batch* b, int steps, cudaGraphExec_t* out) {
     return LBM_OK;
 }
 
+// Map 4: the parameters of one grouped launch -- its runs' parameter blocks
+// for a step from batch parity `parity`, their tiles, and the prefix sums of
+// their block counts.  Returns the launch's block count; *pairs: some run takes
+// node-pair tiles.
+template <typename R>
+long long fill_group(const lbm_batch* b, const std::vector<int>& g, int parity, lbmk::GroupParams<R>& G,
+                     bool* pairs) {
+    std::memset(&G, 0, sizeof G);
+    G.nruns = (int)g.size();
+    long long acc = 0;
+    *pairs = false;
+    for (size_t i = 0; i < g.size(); ++i) {
+        lbm_handle* h = b->runs[g[i]];
+        const lbm_params& p = h->p;
+        G.first_block[i] = (int)acc;
+        G.tile[i] = lbmk::group_tile(p.precision, p.thermal_q, p.flow, p.solid_scheme, p.nx, p.ny);
+        G.run[i] = make_params<R>(h, b->flip[g[i]] ^ parity);
+        *pairs = *pairs || G.tile[i] == lbmk::kGroupPairs;
+        acc += lbmk::group_blocks(p.nx, p.ny, G.tile[i]);
+    }
+    G.first_block[g.size()] = (int)acc;
+    return acc;
+}
+
+const void* group_fn(const lbm_batch* b, bool pairs) {
+    const int ph = batch_phase(b);
+    switch (b->precision) {
+        case LBM_F64: return lbmk::group_kernel<lbmk::MODE_F64>(b->qt, b->flow, ph, false);
+        case LBM_F32: return lbmk::group_kernel<lbmk::MODE_F32>(b->qt, b->flow, ph, false);
+        case LBM_F16: return lbmk::group_kernel<lbmk::MODE_F16>(b->qt, b->flow, ph, pairs);
+        default: return lbmk::group_kernel<lbmk::MODE_BF16>(b->qt, b->flow, ph, pairs);
+    }
+}
+
+// The launch configuration and the parameters of one grouped launch.
+struct GroupArgs {
+    std::unique_ptr<lbmk::GroupParams<double>> d;
+    std::unique_ptr<lbmk::GroupParams<float>> f;
+    void* args[1];
+    dim3 grid, block;
+    const void* fn;
+};
+
+void group_args(const lbm_batch* b, const std::vector<int>& g, int parity, GroupArgs& a) {
+    long long blocks;
+    bool pairs = false;
+    if (b->precision == LBM_F64) {
+        if (!a.d) a.d = std::make_unique<lbmk::GroupParams<double>>();
+        blocks = fill_group<double>(b, g, parity, *a.d, &pairs);
+        a.args[0] = a.d.get();
+    } else {
+        if (!a.f) a.f = std::make_unique<lbmk::GroupParams<float>>();
+        blocks = fill_group<float>(b, g, parity, *a.f, &pairs);
+        a.args[0] = a.f.get();
+    }
+    a.grid = dim3((unsigned)blocks, 1u, 1u);
+    a.block = dim3(128, 1, 1);
+    a.fn = group_fn(b, pairs);
+}
+
+// One batched step under map 4: each group's launch, as a programmatic
+// dependent of the previous launch in the stream.
+cudaError_t group_step_all(lbm_batch* b, int parity, cudaStream_t s) {
+    GroupArgs a;
+    for (const std::vector<int>& g : b->groups) {
+        group_args(b, g, parity, a);
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[0].val.programmaticStreamSerializationAllowed = 1;
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = a.grid;
+        cfg.blockDim = a.block;
+        cfg.stream = s;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        const cudaError_t e = cudaLaunchKernelExC(&cfg, a.fn, a.args);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+// Map 4: a graph of `steps` steps with one chain of grouped launches per
+// group (programmatic edges within a chain; the chains are independent).
+int build_group_graph(lbm_batch* b, int steps, cudaGraphExec_t* out) {
+    cudaGraph_t g = nullptr;
+    if (cudaGraphCreate(&g, 0) != cudaSuccess) return LBM_ERR_CUDA;
+    cudaError_t e = cudaSuccess;
+    GroupArgs a;
+    for (size_t gi = 0; gi < b->groups.size() && e == cudaSuccess; ++gi) {
+        cudaGraphNode_t prev = nullptr;
+        for (int k = 0; k < steps && e == cudaSuccess; ++k) {
+            group_args(b, b->groups[gi], k & 1, a);
+            cudaKernelNodeParams kp = {};
+            kp.func = const_cast<void*>(a.fn);
+            kp.gridDim = a.grid;
+            kp.blockDim = a.block;
+            kp.sharedMemBytes = 0;
+            kp.kernelParams = a.args;
+            kp.extra = nullptr;
+            cudaGraphNode_t node = nullptr;
+            e = cudaGraphAddKernelNode(&node, g, nullptr, 0, &kp);
+            if (e == cudaSuccess && prev) {
+                cudaGraphEdgeData ed = {};
+                ed.from_port = cudaGraphKernelNodePortProgrammatic;
+                ed.to_port = cudaGraphKernelNodePortDefault;
+                ed.type = cudaGraphDependencyTypeProgrammatic;
+                e = cudaGraphAddDependencies(g, &prev, &node, &ed, 1);
+            }
+            prev = node;
+        }
+    }
+    cudaGraphExec_t exec = nullptr;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return LBM_ERR_CUDA;
+    }
+    *out = exec;
+    return LBM_OK;
+}
+
 int build_batch_graph(lbm_batch* b) {
     if (b->graph) return LBM_OK;
+    if (b->mapping == 4) return build_group_graph(b, kGraphSteps, &b->graph);
     if (b->mapping == 3) return build_chain_graph(b, kGraphSteps, &b->graph);
     if (!b->cap && cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess) return LBM_ERR_CUDA;
     if (cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return LBM_ERR_CUDA;
@@ -1142,7 +1280,9 @@ int resync_runs(lbm_batch* b) {
 int batch_advance(lbm_batch* b, int64_t n) {
     auto single = [&]() -> int {
         cudaError_t e = cudaSuccess;
-        if (b->mapping == 3) {
+        if (b->mapping == 4) {
+            e = group_step_all(b, b->parity, b->stream);
+        } else if (b->mapping == 3) {
             for (size_t r = 0; r < b->runs.size() && e == cudaSuccess; ++r)
                 e = enqueue_one(b->runs[r], b->flip[r] ^ b->parity, b->stream);
         } else {
@@ -1185,7 +1325,8 @@ double time_batch(lbm_batch* b, int steps) {
         return 1e30;
     }
     cudaGraphExec_t g = nullptr;
-    if (b->mapping == 3 && build_chain_graph(b, steps, &g) != LBM_OK) {
+    if ((b->mapping == 3 && build_chain_graph(b, steps, &g) != LBM_OK) ||
+        (b->mapping == 4 && build_group_graph(b, steps, &g) != LBM_OK)) {
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
         return 1e30;
@@ -1317,6 +1458,13 @@ int lbm_batch_create(lbm_handle* const* runs, int32_t n_runs, int32_t autotune, 
                     best_cap = 128;
                     best_map = 3;
                 }
+                set_mapping(b, 4, resident);
+                const double t4 = time_batch(b, 16);
+                if (t4 < best) {
+                    best = t4;
+                    best_cap = 128;
+                    best_map = 4;
+                }
             }
             for (int cap : {64, 128, 256}) {
                 if (upload_batch(b, make_tiles(b->runs, b->flip, cap)) != LBM_OK) continue;
@@ -1364,7 +1512,7 @@ int lbm_batch_step(lbm_batch* b, int64_t nsteps) {
 
 int lbm_batch_configure(lbm_batch* b, int32_t width_cap, int32_t mapping) {
     if (!b || (width_cap != 32 && width_cap != 64 && width_cap != 128 && width_cap != 256) || mapping < 0 ||
-        mapping > 3)
+        mapping > 4)
         return LBM_ERR_ARG;
     if (cudaStreamSynchronize(b->stream) != cudaSuccess) {
         cudaGetLastError();

@@ -43,7 +43,7 @@ struct Request {
 
 struct lbm_server {
     int64_t budget = 0, used = 0, peak_used = 0;
-    int max_active = 1, batched = 1, quantum = 256, width_cap = 128, mapping = 3;
+    int max_active = 1, batched = 1, quantum = 256, width_cap = 128, mapping = 4;
     int precision = LBM_F32, thermal_q = 5, flow = 1;
     cudaStream_t stream = nullptr;
     lbm_alloc_fn alloc = nullptr;
@@ -153,7 +153,7 @@ int lbm_server_create(int64_t hbm_budget_bytes, int32_t max_active, int32_t batc
 
 int lbm_server_configure(lbm_server* s, int32_t width_cap, int32_t mapping) {
     if (!s || (width_cap != 32 && width_cap != 64 && width_cap != 128 && width_cap != 256) || mapping < 0 ||
-        mapping > 3)
+        mapping > 4)
         return LBM_ERR_ARG;
     s->width_cap = width_cap;
     s->mapping = mapping;

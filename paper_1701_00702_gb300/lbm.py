@@ -404,7 +404,7 @@ class Batch:
     """Runs advanced together from CUDA graphs (lbm_batch_*)."""
 
     MAPS = ("one block per tile", "persistent contiguous chunks", "persistent grid stride",
-            "single-run kernel chains")
+            "single-run kernel chains", "grouped launches")
 
     def __init__(self, runs, autotune: bool = True, stream=None):
         import torch
@@ -463,7 +463,7 @@ class Server:
 
     def __init__(self, hbm_budget_bytes: int, max_active: int = 64, batched: bool = True, quantum: int = 256,
                  precision: int = F16, thermal_q: int = 5, flow: int = 1, stream=None, device=None,
-                 width_cap: int = 128, mapping: int = 3):
+                 width_cap: int = 128, mapping: int = 4):
         import torch
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)

@@ -2,7 +2,8 @@
 
 Map 3 launches lbm_step's own kernel per run, so a batched step equals
 lbm_step bit for bit in every storage mode.  Maps 0-2 inline the same per-node
-code into the tile kernel, where the compiler may fuse a few multiply-adds
+code into the tile kernel and map 4 into the grouped kernel (node pairs for
+the 16-bit forms), where the compiler may fuse a few multiply-adds
 differently: their states agree with lbm_step to within a few roundings of
 the storage format (TILE_TOL, relative to each array's scale).
 """
@@ -86,7 +87,7 @@ def test_every_map_gives_the_same_state(lbm, prec):
     for s in ref:
         s.step(40)
     for cap in (32, 64, 128, 256):
-        for mapping in (0, 1, 2, 3):
+        for mapping in (0, 1, 2, 3, 4):
             runs = [lbm.Solver(p) for p in ps]
             b = lbm.Batch(runs, autotune=False).configure(cap, mapping)
             b.step(40)
@@ -149,7 +150,7 @@ W9 = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)[:, None, None]   # Eq. 27 we
 
 
 @pytest.mark.parametrize("prec,qt", [(1, 5), (1, 9), (2, 5), (2, 9), (0, 9)])
-@pytest.mark.parametrize("mapping", [0, 1, 2, 3])
+@pytest.mark.parametrize("mapping", [0, 1, 2, 3, 4])
 def test_batch_from_random_states(lbm, prec, qt, mapping):
     """Runs holding random states (populations spread over solid, mushy and
     liquid nodes, flow near rest) advance in a batch exactly as alone."""
@@ -233,7 +234,7 @@ def test_node_pair_runs_under_map_3_equal_lbm_step(lbm, prec):
         s.close()
 
 
-@pytest.mark.parametrize("mapping", [0, 3])
+@pytest.mark.parametrize("mapping", [0, 3, 4])
 def test_a_run_stepped_on_its_own_between_batch_steps(lbm, mapping):
     """lbm_step on a member run between batched steps (same stream) moves that
     run to the other state copy; the next batched step follows it instead of
@@ -263,10 +264,11 @@ ORACLE_TOL = {0: 1e-12, 1: 5e-6, 2: 8 * 2.0 ** -11, 3: 8 * 2.0 ** -8}
 
 
 @pytest.mark.parametrize("prec", [0, 1, 2, 3])
-@pytest.mark.parametrize("mapping", [0, 1, 2])
+@pytest.mark.parametrize("mapping", [0, 1, 2, 4])
 def test_tile_maps_match_the_oracle(lbm, oracle_mod, prec, mapping):
     """The tile kernel (maps 0-2: many runs in one launch per step, parameters
-    from each run's block in global memory) advances every run of a batch as
+    from each run's block in global memory) and the grouped kernel (map 4:
+    parameters in the launch's constant bank) advance every run of a batch as
     the FP64 oracle advances it alone, element by element, after one and after
     three steps from random states (solid, mushy and liquid nodes; walled,
     half-periodic and periodic runs; ragged tiles)."""
@@ -299,4 +301,25 @@ def test_tile_maps_match_the_oracle(lbm, oracle_mod, prec, mapping):
                 assert err < margin * ORACLE_TOL[prec], (s.params["nx"], steps, name, err)
     b.close()
     for s in runs:
+        s.close()
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+def test_grouped_launches_split_large_batches(lbm, prec):
+    """A batch larger than one grouped launch holds (the parameter blocks of up
+    to ~40 runs fit in a launch) runs in several groups, each a chain of its
+    own in the replayed graph; every run still matches lbm_step."""
+    draws = inputs.batch_draws(count=50, seed=21, n_lo=16, n_hi=48)
+    runs = [lbm.Solver(dict(p, precision=prec)) for p in draws]
+    solo = [lbm.Solver(dict(p, precision=prec)) for p in draws]
+    b = lbm.Batch(runs, autotune=False).configure(128, 4)
+    b.step(3)
+    b.step(130)
+    for s in solo:
+        s.step(133)
+    for r, s in zip(runs, solo):
+        assert r.steps == 133
+        assert _same_state(r, s, False, prec)
+    b.close()
+    for s in runs + solo:
         s.close()

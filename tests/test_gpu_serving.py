@@ -1,8 +1,11 @@
 """Continuous-batching serving engine (lbm_server_*).
 
 A request's result must be the same alone and in the mix: runs admitted at
-different ticks advance together in one batched launch, and batched steps
-equal single steps bit for bit, so the diagnostics must match exactly.
+different ticks advance together in one batched launch per step.  Under map 3
+(each run's own kernel) batched steps equal lbm_step bit for bit; under map 4
+(the default: grouped launches) a run's steps do not depend on the other runs
+in the launch, so its result equals, bit for bit, the same server's result
+for the request alone.
 """
 import numpy as np
 import pytest
@@ -35,7 +38,7 @@ def _requests(prec, count=10, seed=3):
 @pytest.mark.parametrize("prec", [2, 1])
 def test_each_result_is_the_same_alone_and_in_the_mix(lbm, prec):
     reqs = _requests(prec)
-    srv = lbm.Server(hbm_budget_bytes=1 << 40, max_active=6, batched=True, quantum=64, precision=prec)
+    srv = lbm.Server(hbm_budget_bytes=1 << 40, max_active=6, batched=True, quantum=64, precision=prec, mapping=3)
     ids = {}
     for p, n in reqs[:5]:
         ids[srv.submit(p, n)] = (p, n)
@@ -122,3 +125,27 @@ def test_replay_of_poisson_arrivals(lbm):
     assert len(res) == 8 and all(r["status"] == 0 for r in res)
     assert all(r["finish_s"] >= r["admit_s"] >= r["submit_s"] for r in res)
     srv.close()
+
+
+def test_grouped_launches_serve_each_result_as_alone(lbm):
+    """With grouped launches (map 4: every active run in one launch per step)
+    a request's result in the mix equals, bit for bit, its result when the
+    same server configuration serves it alone."""
+    reqs = _requests(2, count=8, seed=13)
+
+    def serve(batch):
+        srv = lbm.Server(hbm_budget_bytes=1 << 40, max_active=8, batched=True, quantum=64, precision=2, mapping=4)
+        ids = {srv.submit(p, n): k for k, (p, n) in enumerate(batch)}
+        out = []
+        while len(out) < len(batch):
+            srv.tick()
+            out += srv.results()
+        srv.close()
+        return {ids[r["id"]]: r for r in out}
+
+    mixed = serve(reqs)
+    for k, req in enumerate(reqs):
+        alone = serve([req])[0]
+        assert mixed[k]["status"] == 0 and alone["status"] == 0
+        for key in KEYS:
+            assert mixed[k][key] == alone[key], (k, key)
