@@ -183,7 +183,7 @@ int lbm_create_ex(const lbm_params* p, void* cuda_stream, lbm_alloc_fn alloc,
  * flag).  Large nsteps are replayed from a captured CUDA graph.  Each step is
  * launched as a programmatic dependent of the previous one in the stream.
  * The step kernel runs one node per thread in blocks of 64 x 2 threads on
- * grids of up to 32,768 nodes and 128 x 1 on larger ones, or node pairs (see
+ * grids of up to 40,000 nodes and 128 x 1 on larger ones, or node pairs (see
  * lbm_set_step_form). */
 int lbm_step(lbm_handle* h, int64_t nsteps);
 
@@ -296,7 +296,7 @@ const char* lbm_strerror(int code);
  * (grid width <= 64, <= 128, <= 256, wider; one class at a time, keeping the
  * fastest shape), map 4, and every combination of tile-width cap (64, 128,
  * 256) and map 0-2, and keeps the fastest; otherwise it takes width cap 128,
- * map 0, and for map 3 lbm_step's own block shapes (64 x 2 up to 32,768
+ * map 0, and for map 3 lbm_step's own block shapes (64 x 2 up to 40,000
  * nodes, 128 x 1 above).  Under map 3 a batched step equals lbm_step on each
  * run bit for bit.  Maps 0-2 and 4 inline the same per-node code into
  * another kernel, where the compiler may fuse a few multiply-adds

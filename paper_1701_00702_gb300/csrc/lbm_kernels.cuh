@@ -1069,12 +1069,12 @@ constexpr int kMinBlocks = (QT == 5 && FLOW) ? (M == MODE_F64 ? 1 : 5) : 1;
 // 2.50).
 __device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
-// L2 prefetch ahead of the blocks that will run next (large grids): a block's
-// first thread asks L2, by bulk prefetches (cp.async.bulk.prefetch.L2), for
-// the chunk of x in `rows` rows starting at y0 and for their exchange
-// history, so that the block launched for those rows later finds them in L2
-// instead of waiting for HBM.  No registers or shared memory hold the data;
-// rows past the grid are skipped.
+// L2 prefetch ahead of the blocks that will run next (node pairs on large
+// grids): a block's first thread asks L2, by bulk prefetches
+// (cp.async.bulk.prefetch.L2), for the chunk of x in `rows` rows starting at
+// y0 and for their exchange history, so that the block launched for those
+// rows later finds them in L2 instead of waiting for HBM.  No registers or
+// shared memory hold the data; rows past the grid are skipped.
 __device__ __forceinline__ void l2_prefetch(const void* p, uint32_t bytes) {
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
@@ -1097,8 +1097,6 @@ __global__ void __launch_bounds__(256, (kMinBlocks<M, QT, FLOW>)) fused_step(con
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     if (x >= P.nx || y >= P.ny) return;
     griddep_wait();
-    if (P.prefetch_rows > 0 && threadIdx.x == 0 && threadIdx.y == 0)
-        prefetch_rows<M, QT, FLOW>(P, x, y + P.prefetch_rows, blockDim.y);
     step_node<M, QT, FLOW, PH>(P, x, y);
 }
 

@@ -145,11 +145,11 @@ inline cudaError_t dispatch_step(int qt, int flow, int ph, Fn&& fn) {
 }
 
 // Block shape of the single-run step kernel by grid size (measured on GB300,
-// us per step: 64^2 and 128^2 finish sooner in 64 x 2 blocks, 1.63 and 1.67
-// against 1.76 and 1.79 in 128 x 1; from 256^2 up one-row blocks do best,
-// 2.34 against 2.40 at 256^2).
+// us per step: 128^2 and 192^2 finish sooner in 64 x 2 blocks, 1.63 and 1.86
+// against 1.73 and 2.11 in 128 x 1; from 256^2 up one-row blocks do as well or
+// better, 2.37 against 2.47 at 256^2).
 inline dim3 step_block(int nx, int ny) {
-    return (long long)nx * ny <= 32768 ? dim3(64, 2) : dim3(128, 1);
+    return (long long)nx * ny <= 40000 ? dim3(64, 2) : dim3(128, 1);
 }
 
 // Step forms: one node per thread (fused_step) or node pairs
