@@ -325,17 +325,22 @@ def bench_serving(args, lbm, inputs, stream, plain_mlups: float, seed: int = 170
     grids = ((128, 128), (256, 256), (512, 512), (1024, 1024), (2048, 1024))
     mean_nodes = float(np.mean([a * b for a, b in grids]))
     mean_steps = (hi - lo) / np.log(hi / lo)
-    rate = 0.8 * plain_mlups * 1e6 / (mean_nodes * mean_steps)   # ~80 % of the plain form's capacity
+    capacity = plain_mlups * 1e6 / (mean_nodes * mean_steps)   # requests per second of the plain form, roughly
+    rate = 0.8 * capacity
     base = inputs.serving_arrivals(count=count, rate_per_s=rate, seed=seed, grids=grids,
                                    steps_lo=lo, steps_hi=hi)
     out = {"requests": len(base), "arrival_rate_per_s": rate, "step_range": [lo, hi],
            "note": ("the stated trace: 10k..500k steps" if scale == 1.0 else
                     f"step counts of the 1e4..5e5 serving trace scaled by {scale}"), "forms": []}
-    forms = [("plain FP32 (one at a time)", False, 1, 150.0), ("continuous batching FP16", True, 2, 150.0)]
+    # (name, batched, precision, HBM budget GB, arrival-rate factor)
+    forms = [("plain FP32 (one at a time)", False, 1, 150.0, 1.0), ("continuous batching FP16", True, 2, 150.0, 1.0)]
     if args.serve_full:
-        forms.append(("continuous batching FP16, tight budget", True, 2, args.serve_tight_budget_gb))
-    for name, batched, prec, budget_gb in forms:
-        trace = [dict(r, params=dict(r["params"], precision=prec)) for r in base]
+        forms += [("continuous batching FP16, tight budget", True, 2, args.serve_tight_budget_gb, 1.0),
+                  ("plain FP32 (one at a time), arrivals at 2x its capacity", False, 1, 150.0, 2.5),
+                  ("continuous batching FP16, arrivals at 2x the plain capacity", True, 2, 150.0, 2.5)]
+    for name, batched, prec, budget_gb, speed in forms:
+        # the same requests; a factor > 1 compresses their arrival times (0.8 x 2.5 = 2x capacity)
+        trace = [dict(r, arrival_s=r["arrival_s"] / speed, params=dict(r["params"], precision=prec)) for r in base]
         srv = lbm.Server(hbm_budget_bytes=int(budget_gb * 1e9), max_active=64, batched=batched, quantum=256,
                          precision=prec, stream=stream)
         res = srv.replay(trace)
@@ -346,6 +351,7 @@ def bench_serving(args, lbm, inputs, stream, plain_mlups: float, seed: int = 170
         span = max(r["finish_s"] for r in res) - min(r["submit_s"] for r in res)
         out["forms"].append({
             "form": name, "ok": all(r["status"] == 0 for r in res), "hbm_budget_gb": budget_gb,
+            "arrival_rate_per_s": rate * speed,
             "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
             "p50_queue_s": float(np.percentile(wait, 50)), "max_queue_s": float(wait.max()),
             "runs_per_s": len(res) / span, "aggregate_mlups": st["node_steps"] / span / 1e6,

@@ -284,12 +284,13 @@ const char* lbm_strerror(int code);
  * graph and the chains independent, so small runs overlap large ones; each
  * run's kernel takes one of the block shapes 128 x 2, 64 x 4, 32 x 8, 256 x 1
  * (256 threads), 128 x 1, 64 x 2, 32 x 4 (128) or 64 x 1, 32 x 2 (64).  Map
- * 4 launches one kernel per step for up to about 40 runs (23 in FP64) at a
- * time, their parameter blocks in the launch's own parameters: each run in
- * tiles of w x 128/w nodes (w = 32, 64 or 128, whichever leaves the fewest
- * of the run's threads idle; node pairs over 128 x 2 nodes for FP16/BF16
- * runs that lbm_step would step in pairs); larger batches take several such
- * launches, each group of runs a chain of its own in the graph.  With
+ * 4 steps the runs below 1,048,576 nodes in grouped launches, one kernel per
+ * step for up to about 40 runs (23 in FP64) at a time, their parameter
+ * blocks in the launch's own parameters, each run in tiles of w x 128/w
+ * nodes (w = 32, 64 or 128, whichever leaves the fewest of the run's threads
+ * idle); each group of runs is a chain of its own in the graph, and larger
+ * runs keep their own step kernel in chains of their own, as under map 3.
+ * With
  * autotune = 1 the call times, on freshly created copies of the runs (the
  * runs themselves do not move, but the copies hold as much device memory
  * again while tuning), map 3 with the block shape chosen per size class

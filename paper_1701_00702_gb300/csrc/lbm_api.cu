@@ -874,6 +874,7 @@ struct lbm_batch {
     std::vector<int> form;        // each run's step form when the parameters were uploaded
     std::vector<int> shape;       // map 3: block shape of each run (index into kShapes)
     std::vector<std::vector<int>> groups;   // map 4: the runs of each grouped launch
+    std::vector<int> solo;                  // map 4: runs that keep their own step kernel
     lbmk::Tile* tiles = nullptr;
     size_t tile_capacity = 0;     // tiles that fit in the allocation
     int ntiles = 0, width_cap = 128, chunk = 1, grid = 0, parity = 0, mapping = 0;
@@ -1002,16 +1003,20 @@ int batch_blocks_per_sm(const lbm_batch* b) {
 // contiguous chunks of tiles, 2 persistent blocks striding over the tiles,
 // 3 one single-run kernel per run and step, the runs' chains concurrent in
 // one graph.
-// Map 4: the runs in order, at most kGroupRuns per grouped launch.
+// Map 4: the runs below kGroupMaxNodes nodes in order, at most kGroupRuns per
+// grouped launch; the larger runs keep their own step kernel.
 void make_groups(lbm_batch* b) {
     b->groups.clear();
+    b->solo.clear();
     const int cap = b->precision == LBM_F64 ? lbmk::kGroupRuns<double> : lbmk::kGroupRuns<float>;
-    const int n = (int)b->runs.size();
-    for (int r = 0; r < n; r += cap) {
-        std::vector<int> g;
-        for (int k = r; k < std::min(r + cap, n); ++k) g.push_back(k);
-        b->groups.push_back(g);
+    std::vector<int> small;
+    for (int r = 0; r < (int)b->runs.size(); ++r) {
+        const lbm_params& p = b->runs[r]->p;
+        if ((long long)p.nx * p.ny < lbmk::kGroupMaxNodes) small.push_back(r);
+        else b->solo.push_back(r);
     }
+    for (size_t i = 0; i < small.size(); i += cap)
+        b->groups.emplace_back(small.begin() + i, small.begin() + std::min(small.size(), i + cap));
 }
 
 void set_mapping(lbm_batch* b, int mapping, int resident_blocks) {
@@ -1045,13 +1050,14 @@ void free_batch(lbm_batch* b) {
     delete b;
 }
 
-// Map 3: a graph of `steps` steps with one chain of kernel nodes per run; a
-// run's step k reads the copy flip ^ (k mod 2), starting from batch parity 0.
-int build_chain_graph(lbm_batch* b, int steps, cudaGraphExec_t* out) {
-    cudaGraph_t g = nullptr;
-    if (cudaGraphCreate(&g, 0) != cudaSuccess) return LBM_ERR_CUDA;
+// Adds to graph g one chain of `steps` step-kernel nodes for each listed run
+// (the kernel, grid and block lbm_step would launch for the run, with the
+// run's block shape), programmatic edges within a chain; a run's step k reads
+// the copy flip ^ (k mod 2), starting from batch parity 0.
+cudaError_t add_run_chains(lbm_batch* b, cudaGraph_t g, const std::vector<int>& which, int steps) {
     cudaError_t e = cudaSuccess;
-    for (size_t r = 0; r < b->runs.size() && e == cudaSuccess; ++r) {
+    for (size_t i = 0; i < which.size() && e == cudaSuccess; ++i) {
+        const int r = which[i];
         lbm_handle* h = b->runs[r];
         cudaGraphNode_t prev = nullptr;
         for (int k = 0; k < steps && e == cudaSuccess; ++k) {
@@ -1096,6 +1102,10 @@ int build_chain_graph(lbm_batch* b, int steps, cudaGraphExec_t* out) {
             prev = node;
         }
     }
+    return e;
+}
+
+int instantiate(cudaGraph_t g, cudaError_t e, cudaGraphExec_t* out) {
     cudaGraphExec_t exec = nullptr;
     if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, g, 0);
     cudaGraphDestroy(g);
@@ -1107,37 +1117,41 @@ int build_chain_graph(lbm_batch* b, int steps, cudaGraphExec_t* out) {
     return LBM_OK;
 }
 
+// Map 3: a graph of `steps` steps with one chain of kernel nodes per run.
+int build_chain_graph(lbm_batch* b, int steps, cudaGraphExec_t* out) {
+    cudaGraph_t g = nullptr;
+    if (cudaGraphCreate(&g, 0) != cudaSuccess) return LBM_ERR_CUDA;
+    std::vector<int> all(b->runs.size());
+    for (size_t r = 0; r < all.size(); ++r) all[r] = (int)r;
+    return instantiate(g, add_run_chains(b, g, all, steps), out);
+}
+
 // Map 4: the parameters of one grouped launch -- its runs' parameter blocks
 // for a step from batch parity `parity`, their tiles, and the prefix sums of
-// their block counts.  Returns the launch's block count; *pairs: some run takes
-// node-pair tiles.
+// their block counts.  Returns the launch's block count.
 template <typename R>
-long long fill_group(const lbm_batch* b, const std::vector<int>& g, int parity, lbmk::GroupParams<R>& G,
-                     bool* pairs) {
+long long fill_group(const lbm_batch* b, const std::vector<int>& g, int parity, lbmk::GroupParams<R>& G) {
     std::memset(&G, 0, sizeof G);
     G.nruns = (int)g.size();
     long long acc = 0;
-    *pairs = false;
     for (size_t i = 0; i < g.size(); ++i) {
         lbm_handle* h = b->runs[g[i]];
-        const lbm_params& p = h->p;
         G.first_block[i] = (int)acc;
-        G.tile[i] = lbmk::group_tile(p.precision, p.thermal_q, p.flow, p.solid_scheme, p.nx, p.ny);
+        G.tile[i] = lbmk::group_tile(h->p.nx);
         G.run[i] = make_params<R>(h, b->flip[g[i]] ^ parity);
-        *pairs = *pairs || G.tile[i] == lbmk::kGroupPairs;
-        acc += lbmk::group_blocks(p.nx, p.ny, G.tile[i]);
+        acc += lbmk::group_blocks(h->p.nx, h->p.ny, G.tile[i]);
     }
     G.first_block[g.size()] = (int)acc;
     return acc;
 }
 
-const void* group_fn(const lbm_batch* b, bool pairs) {
+const void* group_fn(const lbm_batch* b) {
     const int ph = batch_phase(b);
     switch (b->precision) {
-        case LBM_F64: return lbmk::group_kernel<lbmk::MODE_F64>(b->qt, b->flow, ph, false);
-        case LBM_F32: return lbmk::group_kernel<lbmk::MODE_F32>(b->qt, b->flow, ph, false);
-        case LBM_F16: return lbmk::group_kernel<lbmk::MODE_F16>(b->qt, b->flow, ph, pairs);
-        default: return lbmk::group_kernel<lbmk::MODE_BF16>(b->qt, b->flow, ph, pairs);
+        case LBM_F64: return lbmk::group_kernel<lbmk::MODE_F64>(b->qt, b->flow, ph);
+        case LBM_F32: return lbmk::group_kernel<lbmk::MODE_F32>(b->qt, b->flow, ph);
+        case LBM_F16: return lbmk::group_kernel<lbmk::MODE_F16>(b->qt, b->flow, ph);
+        default: return lbmk::group_kernel<lbmk::MODE_BF16>(b->qt, b->flow, ph);
     }
 }
 
@@ -1152,23 +1166,22 @@ struct GroupArgs {
 
 void group_args(const lbm_batch* b, const std::vector<int>& g, int parity, GroupArgs& a) {
     long long blocks;
-    bool pairs = false;
     if (b->precision == LBM_F64) {
         if (!a.d) a.d = std::make_unique<lbmk::GroupParams<double>>();
-        blocks = fill_group<double>(b, g, parity, *a.d, &pairs);
+        blocks = fill_group<double>(b, g, parity, *a.d);
         a.args[0] = a.d.get();
     } else {
         if (!a.f) a.f = std::make_unique<lbmk::GroupParams<float>>();
-        blocks = fill_group<float>(b, g, parity, *a.f, &pairs);
+        blocks = fill_group<float>(b, g, parity, *a.f);
         a.args[0] = a.f.get();
     }
     a.grid = dim3((unsigned)blocks, 1u, 1u);
     a.block = dim3(128, 1, 1);
-    a.fn = group_fn(b, pairs);
+    a.fn = group_fn(b);
 }
 
-// One batched step under map 4: each group's launch, as a programmatic
-// dependent of the previous launch in the stream.
+// One batched step under map 4: each group's launch and each large run's own
+// step, as programmatic dependents of the previous launch in the stream.
 cudaError_t group_step_all(lbm_batch* b, int parity, cudaStream_t s) {
     GroupArgs a;
     for (const std::vector<int>& g : b->groups) {
@@ -1185,11 +1198,16 @@ cudaError_t group_step_all(lbm_batch* b, int parity, cudaStream_t s) {
         const cudaError_t e = cudaLaunchKernelExC(&cfg, a.fn, a.args);
         if (e != cudaSuccess) return e;
     }
+    for (int r : b->solo) {
+        const cudaError_t e = enqueue_one(b->runs[r], b->flip[r] ^ parity, s);
+        if (e != cudaSuccess) return e;
+    }
     return cudaSuccess;
 }
 
-// Map 4: a graph of `steps` steps with one chain of grouped launches per
-// group (programmatic edges within a chain; the chains are independent).
+// Map 4: a graph of `steps` steps with one chain of grouped launches per group
+// and one chain of step kernels per large run (programmatic edges within a
+// chain; the chains are independent).
 int build_group_graph(lbm_batch* b, int steps, cudaGraphExec_t* out) {
     cudaGraph_t g = nullptr;
     if (cudaGraphCreate(&g, 0) != cudaSuccess) return LBM_ERR_CUDA;
@@ -1218,15 +1236,8 @@ int build_group_graph(lbm_batch* b, int steps, cudaGraphExec_t* out) {
             prev = node;
         }
     }
-    cudaGraphExec_t exec = nullptr;
-    if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, g, 0);
-    cudaGraphDestroy(g);
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        return LBM_ERR_CUDA;
-    }
-    *out = exec;
-    return LBM_OK;
+    if (e == cudaSuccess) e = add_run_chains(b, g, b->solo, steps);
+    return instantiate(g, e, out);
 }
 
 int build_batch_graph(lbm_batch* b) {

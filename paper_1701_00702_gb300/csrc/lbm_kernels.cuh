@@ -1542,21 +1542,18 @@ __global__ void __launch_bounds__(128, 7) fused_step_pair(const __grid_constant_
     step_pair<M, PH>(P, x0, y);
 }
 
-// Many runs in one launch per step, each run on the code of the single-run
-// kernels (map 4 of a batch).  The parameter blocks of up to kGroupRuns runs
-// travel in the kernel's own parameter space (the constant bank, up to
-// 32 KB), with the prefix sums of the runs' block counts; block b finds its run
-// by a binary search over them (uniform across the block) and takes block
-// b - first_block[run] of that run's tiles.  Blocks have 128 threads.  A run's
-// tile (tile[run]): 0, 1, 2 -- w x (128 / w) nodes with w = 32, 64, 128, one
-// node per thread (fused_step's arithmetic), w chosen so that the run's width
-// leaves the fewest threads idle; kGroupPairs -- node pairs over 128 x 2 nodes
-// (fused_step_pair's arithmetic, with its one-node fallback; compiled in only
-// when PAIRS).  With all runs in one grid the device sees one large launch
-// instead of many small ones.
+// Many small runs in one launch per step, each run on the code of the
+// single-run kernel (map 4 of a batch).  The parameter blocks of up to
+// kGroupRuns runs travel in the kernel's own parameter space (the constant
+// bank, up to 32 KB), with the prefix sums of the runs' block counts; block b
+// finds its run by a binary search over them (uniform across the block) and
+// takes block b - first_block[run] of that run's tiles: w x (128 / w) nodes,
+// one node per thread (fused_step's arithmetic), w = 32 << tile[run] chosen so
+// that the run's width leaves the fewest threads idle.  With all small runs in
+// one grid the device sees one large launch instead of many small ones, each
+// bound by the latency of a few warps.
 template <typename R>
 constexpr int kGroupRuns = (32000 - 16) / (int)(sizeof(StepParams<R>) + 2 * sizeof(int));
-constexpr int kGroupPairs = 3;
 
 template <typename R>
 struct GroupParams {
@@ -1566,8 +1563,8 @@ struct GroupParams {
     StepParams<R> run[kGroupRuns<R>];
 };
 
-template <int M, int QT, bool FLOW, bool PH, bool PAIRS>
-__global__ void __launch_bounds__(128, PAIRS ? 7 : 2 * kMinBlocks<M, QT, FLOW>) group_step(
+template <int M, int QT, bool FLOW, bool PH>
+__global__ void __launch_bounds__(128, 2 * kMinBlocks<M, QT, FLOW>) group_step(
     const __grid_constant__ GroupParams<typename ModeTraits<M>::R> G) {
     using R = typename ModeTraits<M>::R;
     const int b = blockIdx.x;
@@ -1579,28 +1576,8 @@ __global__ void __launch_bounds__(128, PAIRS ? 7 : 2 * kMinBlocks<M, QT, FLOW>) 
     }
     const StepParams<R>& P = G.run[lo];
     const int lb = b - G.first_block[lo];
-    const int tile = G.tile[lo];
+    const int lw = 5 + G.tile[lo];   // log2 of the tile width
     const int t = (int)threadIdx.x;
-    if constexpr (PAIRS) {
-        if (tile == kGroupPairs) {
-            const int gx = ((P.nx + 1) / 2 + 63) / 64;
-            const int x0 = 2 * ((lb % gx) * 64 + (t & 63));
-            const int y = (lb / gx) * 2 + (t >> 6);
-            if (x0 >= P.nx || y >= P.ny) return;
-            griddep_wait();
-            if (P.prefetch_rows > 0 && t == 0) prefetch_rows<M, 5, true>(P, x0, y + P.prefetch_rows, 2);
-            const bool single = P.solid_scheme || x0 + 1 >= P.nx || (!P.per_x && (x0 == 0 || x0 + 1 == P.nx - 1)) ||
-                                (!P.per_y && (y == 0 || y == P.ny - 1));
-            if (single) {
-                step_node<M, 5, true, PH>(P, x0, y);
-                if (x0 + 1 < P.nx) step_node<M, 5, true, PH>(P, x0 + 1, y);
-                return;
-            }
-            step_pair<M, PH>(P, x0, y);
-            return;
-        }
-    }
-    const int lw = 5 + tile;                 // log2 of the tile width
     const int gx = (P.nx + (1 << lw) - 1) >> lw;
     const int x = (lb % gx) * (1 << lw) + (t & ((1 << lw) - 1));
     const int y = (lb / gx) * (128 >> lw) + (t >> lw);

@@ -217,15 +217,15 @@ StepLaunch step_launch(const StepParams<typename ModeTraits<M>::R>& P, int qt, i
     return L;
 }
 
-// Grouped launches (map 4 of a batch): the tile of a run -- node pairs where
-// the run's own step would take them (16-bit forms of the default
-// configuration from kPairMinNodes nodes), else the narrowest waste of
-// threads among tiles 32, 64 and 128 nodes wide (ties to the wider).
-inline int group_tile(int mode, int qt, int flow, int solid_scheme, int nx, int ny) {
-    if (form_for(mode, qt, flow, solid_scheme, (long long)nx * ny, FORM_AUTO) == FORM_PAIRS &&
-        (mode == MODE_F16 || mode == MODE_BF16))
-        return kGroupPairs;
-    // idle fraction of the covered columns, (cover - nx) / cover, compared exactly
+// Grouped launches (map 4 of a batch): runs below kGroupMaxNodes nodes share
+// grouped launches; larger runs, whose own step kernel fills the device,
+// keep it (a chain of their own, as under map 3).
+constexpr long long kGroupMaxNodes = 1ll << 20;
+
+// The tile of a run in a grouped launch: the narrowest waste of threads among
+// tiles 32, 64 and 128 nodes wide (ties to the wider); the idle fraction of the
+// covered columns, (cover - nx) / cover, compared exactly.
+inline int group_tile(int nx) {
     int best = 2;
     long long best_cover = ((nx + 127) / 128) * 128ll;
     for (int k = 1; k >= 0; --k) {
@@ -241,21 +241,15 @@ inline int group_tile(int mode, int qt, int flow, int solid_scheme, int nx, int 
 
 // Blocks of one run in a grouped launch (blocks of 128 threads).
 inline long long group_blocks(int nx, int ny, int tile) {
-    if (tile == kGroupPairs) return (long long)(((nx + 1) / 2 + 63) / 64) * ((ny + 1) / 2);
     const int w = 32 << tile;
     return (long long)((nx + w - 1) / w) * ((ny + (128 / w) - 1) / (128 / w));
 }
 
-// The grouped kernel of a group; pairs: some run of it takes node-pair tiles.
 template <int M>
-const void* group_kernel(int qt, int flow, int ph, bool pairs) {
-    if constexpr (M == MODE_F16 || M == MODE_BF16) {
-        if (pairs && qt == 5 && flow)
-            return ph ? (const void*)group_step<M, 5, true, true, true> : (const void*)group_step<M, 5, true, false, true>;
-    }
+const void* group_kernel(int qt, int flow, int ph) {
     const void* fn = nullptr;
     dispatch_step<M>(qt, flow, ph, [&]<int MM, int Q, bool F, bool PH>() {
-        fn = (const void*)group_step<MM, Q, F, PH, false>;
+        fn = (const void*)group_step<MM, Q, F, PH>;
         return cudaSuccess;
     });
     return fn;
@@ -354,7 +348,7 @@ int batch_blocks_per_sm(int qt, int flow, int ph) {
     template cudaError_t launch_batch<M>(const StepParams<ModeTraits<M>::R>*, const Tile*, int, int, int, int, int, \
                                          int, int, cudaStream_t);                                               \
     template int batch_blocks_per_sm<M>(int, int, int);                                                   \
-    template const void* group_kernel<M>(int, int, int, bool);                                              \
+    template const void* group_kernel<M>(int, int, int);                                                    \
     template StepLaunch step_launch<M>(const StepParams<ModeTraits<M>::R>&, int, int, int, dim3);
 
 #define LBMK_INSTANTIATE_CONVERT(M)                                                                           \

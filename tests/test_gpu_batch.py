@@ -2,8 +2,8 @@
 
 Map 3 launches lbm_step's own kernel per run, so a batched step equals
 lbm_step bit for bit in every storage mode.  Maps 0-2 inline the same per-node
-code into the tile kernel and map 4 into the grouped kernel (node pairs for
-the 16-bit forms), where the compiler may fuse a few multiply-adds
+code into the tile kernel and map 4 into the grouped kernel (runs below
+2^20 nodes), where the compiler may fuse a few multiply-adds
 differently: their states agree with lbm_step to within a few roundings of
 the storage format (TILE_TOL, relative to each array's scale).
 """
@@ -308,8 +308,11 @@ def test_tile_maps_match_the_oracle(lbm, oracle_mod, prec, mapping):
 def test_grouped_launches_split_large_batches(lbm, prec):
     """A batch larger than one grouped launch holds (the parameter blocks of up
     to ~40 runs fit in a launch) runs in several groups, each a chain of its
-    own in the replayed graph; every run still matches lbm_step."""
+    own in the replayed graph, beside a run large enough to keep its own step
+    kernel (1024 x 1100 nodes, node pairs in FP16); every run still matches
+    lbm_step."""
     draws = inputs.batch_draws(count=50, seed=21, n_lo=16, n_hi=48)
+    draws.append(inputs.cavity(1024, ny=1100))
     runs = [lbm.Solver(dict(p, precision=prec)) for p in draws]
     solo = [lbm.Solver(dict(p, precision=prec)) for p in draws]
     b = lbm.Batch(runs, autotune=False).configure(128, 4)
