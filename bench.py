@@ -83,10 +83,11 @@ def stored_bytes_per_update(qt: int, flow: int, precision: int) -> int:
 # one ncu capture, taken for the kernel sources whose code hash is given; the
 # bench reports it only while the sources still hash to that value.
 ROOFLINE_TRAFFIC = {
-    "bytes_per_launch": 651068928,
-    "kernel_sources_sha256_16": "0713aeeb754d7d30",
-    "gpu__dram_throughput_pct": 83.5,
-    "captured": "2026-12-03, ncu --set full --clock-control none, one launch after two",
+    "bytes_per_launch": 649179904,
+    "kernel_sources_sha256_16": "f39d41fb270ad124",
+    "gpu__dram_throughput_pct": 84.2,
+    "captured": "2026-12-04, ncu --set full --clock-control none, one launch after two "
+                "(profiles/fused_step_cavity2048_fp32.md)",
 }
 
 
