@@ -9,14 +9,16 @@ Pr = 50, Da = 1e-4, porosity 0.9, Ste = 1, conductivity ratio 100,
 H_v = 5.9, hot left / cold right walls, adiabatic top and bottom.  One
 benchmark step advances the run by ``--lb-steps`` time steps (a chunk of the
 200k-step solve); L2 is flushed between benchmark steps.  The metric is MLUPS
-(million node updates per second, every node counted).
+(million node updates per second, every node counted).  The run takes the
+library's automatic step form: two time steps per launch at 256 x 256.
 
 Besides the headline number the line carries:
-  * roofline: the same kernel on the 2048 x 2048 cavity (0.7 GB of state, far
-    beyond L2), algorithmic 168 B per node update (19 FP32 populations, the
-    low part of the PCM rest population and the exchange history, each read
-    and written once) against the measured HBM
-    copy bandwidth;
+  * roofline: the one-step kernel (one node per thread, one step per launch)
+    on the 2048 x 2048 cavity (0.7 GB of state, far beyond L2), algorithmic
+    160 B per node update (19 FP32 populations and the exchange history, each
+    read and written once) against the measured HBM copy bandwidth;
+  * two_step: the automatic form on that cavity, two steps per launch (the
+    state crosses HBM once per two node updates);
   * e2e: the same workload through the C ABI with host buffers: each step
     uploads the full state from pinned memory, advances it and reads back
     T_f, T_s, f_l, u_x, u_y;
@@ -49,6 +51,17 @@ L2_FLUSH_BYTES = 512 << 20
 
 
 PREC_NAMES = {0: "f64", 1: "f32", 2: "f16", 3: "bf16"}
+FORM_NAMES = {1: "one node per thread", 2: "node pairs", 3: "two steps per launch"}
+
+
+def launches_per_call(form: int, nsteps: int) -> int:
+    """Kernel launches of one lbm_step(nsteps) call from state copy 0 with an
+    even nsteps: 64-step graphs (32 launches each in the two-step form), then
+    pairs of two-step launches for 4 steps each, then single steps."""
+    if form != 3:
+        return nsteps
+    graphs, rest = divmod(nsteps, 64)
+    return graphs * 32 + (rest // 4) * 2 + rest % 4
 
 
 def bytes_per_update(qt: int, flow: int, precision: int) -> int:
@@ -79,9 +92,10 @@ def stored_bytes_per_update(qt: int, flow: int, precision: int) -> int:
 
 
 # DRAM traffic of one launch of the roofline kernel (fused_step, FP32, D2Q5,
-# flow, 2048 x 2048 cavity): dram__bytes_read.sum + dram__bytes_write.sum from
-# one ncu capture, taken for the kernel sources whose code hash is given; the
-# bench reports it only while the sources still hash to that value.
+# flow, 2048 x 2048 cavity) and of the two-step kernel on the same cavity:
+# dram__bytes_read.sum + dram__bytes_write.sum from one ncu capture each,
+# taken for the kernel sources whose code hash is given; the bench reports
+# them only while the sources still hash to that value.
 ROOFLINE_TRAFFIC = {
     "bytes_per_launch": 649179904,
     "kernel_sources_sha256_16": "f39d41fb270ad124",
@@ -89,14 +103,20 @@ ROOFLINE_TRAFFIC = {
     "captured": "2026-12-04, ncu --set full --clock-control none, one launch after two "
                 "(profiles/fused_step_cavity2048_fp32.md)",
 }
+TWO_STEP_TRAFFIC = {
+    "bytes_per_launch": None,
+    "kernel_sources_sha256_16": None,
+    "gpu__dram_throughput_pct": None,
+    "captured": None,
+}
 
 
-def measured_traffic(n: int):
-    """ncu DRAM bytes per launch of the roofline kernel, or None for another
-    grid size or once the kernel sources have changed since the capture."""
-    if n != 2048 or kernel_sources_hash() != ROOFLINE_TRAFFIC["kernel_sources_sha256_16"]:
+def measured_traffic(n: int, table: dict = ROOFLINE_TRAFFIC):
+    """ncu DRAM bytes per launch from `table`, or None for another grid size
+    or once the kernel sources have changed since the capture."""
+    if n != 2048 or kernel_sources_hash() != table["kernel_sources_sha256_16"]:
         return None
-    return ROOFLINE_TRAFFIC["bytes_per_launch"]
+    return table["bytes_per_launch"]
 
 
 def kernel_sources_hash() -> str:
@@ -481,6 +501,7 @@ def main():
     prec = {"f64": 0, "f32": 1, "f16": 2, "bf16": 3}[args.precision]
     p = inputs.cavity(args.n, precision=prec)
     cells = p["nx"] * p["ny"]
+    form = lbm.step_form_for(p, 0)
     bpu = bytes_per_update(p["thermal_q"], p["flow"], p["precision"])
     props = torch.cuda.get_device_properties(dev)
     bus = getattr(props, "pci_bus_id", None)
@@ -546,9 +567,9 @@ def main():
         s.close()
         del flush
 
-        def time_form(prec: int, n: int, per: int, reps: int = 3):
+        def time_form(prec: int, n: int, per: int, reps: int = 3, step_form: int = 0):
             pf = inputs.cavity(n, precision=prec)
-            sf = lbm.Solver(pf, stream=stream)
+            sf = lbm.Solver(pf, stream=stream).set_step_form(step_form)
             sf.step(64)
             stream.synchronize()
             e = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
@@ -564,25 +585,11 @@ def main():
                 raise SystemExit(f"form {PREC_NAMES[prec]} {n}^2 reported an unstable state")
             return ms
 
-        # roofline: the same kernel on a state far larger than L2
-        roof = None
+        # roofline: the one-step kernel on a state far larger than L2
+        roof, two_step = None, None
         if args.roofline_n > 0:
             pr = inputs.cavity(args.roofline_n, precision=1)
-            sr = lbm.Solver(pr, stream=stream)
-            sr.step(64)
-            stream.synchronize()
-            reps, per = 3, 128
-            e = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
-            for a, b in e:
-                a.record(stream)
-                sr.step(per)
-                b.record(stream)
-            stream.synchronize()
-            ms = sum(a.elapsed_time(b) for a, b in e) / (reps * per)
-            rc = sr.status()
-            sr.close()
-            if rc != 0:
-                raise SystemExit("roofline run reported an unstable state")
+            ms = time_form(1, args.roofline_n, 128, step_form=1)
             peaks = json.loads((ROOT / "MEASURED_PEAKS.json").read_text()) if (ROOT / "MEASURED_PEAKS.json").exists() else {}
             peak = float(peaks.get("hbm_gbs", 6800.0))
             nodes = pr["nx"] * pr["ny"]
@@ -592,7 +599,7 @@ def main():
             traffic = measured_traffic(pr["nx"])
             roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                     "frac": achieved / peak, "traffic": traffic,
-                    "kernel": "fused_step<float, Q_T=5, flow>",
+                    "kernel": "fused_step<float, Q_T=5, flow> (one node per thread, one step per launch)",
                     "workload": f"square-cavity melting {pr['nx']}x{pr['ny']} FP32 (state {lbm.state_bytes(pr) / 2**30:.2f} GiB)",
                     "bytes_per_update": b_alg,
                     "bytes_basis": "algorithmic: 19 FP32 populations and the FP32 exchange history, each read and "
@@ -607,6 +614,29 @@ def main():
                     "traffic_source": (f"ncu dram__bytes_read.sum + dram__bytes_write.sum, {ROOFLINE_TRAFFIC['captured']}"
                                        if traffic else "no capture of the current kernel sources"),
                     "ncu_gpu__dram_throughput_pct": ROOFLINE_TRAFFIC["gpu__dram_throughput_pct"] if traffic else None}
+            # the automatic form on the same cavity: two steps per launch, the state
+            # through HBM once per launch
+            ms2 = time_form(1, args.roofline_n, 128)
+            t2 = measured_traffic(pr["nx"], TWO_STEP_TRAFFIC)
+            launch_s = 2 * ms2 / 1e3
+            two_step = {"kernel": "fused_step2<float, Q_T=5, flow> (blocks of 34 x 12 threads, inner tiles 32 x 10)",
+                        "step_form": FORM_NAMES[lbm.step_form_for(pr, 0)],
+                        "workload": roof["workload"], "us_per_step": ms2 * 1e3, "avg_launch_us": launch_s * 1e6,
+                        "mlups": nodes / (ms2 / 1e3) / 1e6, "speedup_over_one_step": ms / ms2,
+                        "hbm_bytes_per_launch_algorithmic": b_alg * nodes,
+                        "hbm_basis": "the state read and written once per launch (two node updates): 160 B per "
+                                     "node per launch, 80 B per node update",
+                        "gbs_hbm_algorithmic": b_alg * nodes / launch_s / 1e9,
+                        "frac_of_measured_hbm": b_alg * nodes / launch_s / 1e9 / peak,
+                        "gbs_per_update_basis": b_alg * nodes / (ms2 / 1e3) / 1e9,
+                        "per_update_basis_note": "160 B per node update over the per-step time: the one-step "
+                                                 "kernel's roofline quantity, above the copy bandwidth because "
+                                                 "two updates share one HBM round trip",
+                        "traffic": t2,
+                        "traffic_source": (f"ncu dram__bytes_read.sum + dram__bytes_write.sum, {TWO_STEP_TRAFFIC['captured']}"
+                                           if t2 else "no capture of the current kernel sources"),
+                        "bound": "instruction issue (the ring's redundant updates and both steps' arithmetic), "
+                                 "not HBM"}
 
         # many unequal cavities: plain per-run FP32 vs one launch per step for all runs
         batched = None
@@ -628,7 +658,9 @@ def main():
                     ms = time_form(fprec, n, per)
                     b = bytes_per_update(5, 1, fprec)
                     gbs = b * n * n / (ms / 1e3) / 1e9
-                    forms.append({"precision": PREC_NAMES[fprec], "grid": n, "us_per_step": ms * 1e3,
+                    forms.append({"precision": PREC_NAMES[fprec], "grid": n,
+                                  "step_form": FORM_NAMES[lbm.step_form_for(inputs.cavity(n, precision=fprec), 0)],
+                                  "us_per_step": ms * 1e3,
                                   "mlups": n * n / (ms / 1e3) / 1e6, "bytes_per_update": b,
                                   "overhead_bytes_per_update": stored_bytes_per_update(5, 1, fprec) - b,
                                   "gbs_algorithmic": gbs, "frac_of_measured_hbm": gbs / peak})
@@ -644,17 +676,19 @@ def main():
         "scaling": "weak", "vs_baseline": None, "dtype": PREC_NAMES[prec], "data": "synthetic",
         "config": workload_config(args, p, chunk),
         "roofline": roof,
-        "l2_resident": {"avg_launch_us": launch_ms_small * 1e3,
-                        "gbs_algorithmic": bpu * cells / (launch_ms_small / 1e3) / 1e9,
+        "two_step": two_step,
+        "l2_resident": {"step_form": FORM_NAMES[form], "us_per_step": launch_ms_small * 1e3,
+                        "avg_launch_us": launch_ms_small * 1e3 * chunk / launches_per_call(form, chunk),
+                        "gbs_algorithmic_per_update_basis": bpu * cells / (launch_ms_small / 1e3) / 1e9,
                         "bytes_per_update": bpu,
-                        "note": "256x256 state (10 MB) is L2-resident; launch-to-launch time inside CUDA graphs"},
+                        "note": f"{p['nx']}x{p['ny']} state is L2-resident; launch-to-launch time inside CUDA graphs"},
         "forms": forms if args.roofline_n > 0 else None,
         "accuracy": accuracy,
         "batched": batched,
         "serving": serving,
         "cpu_baseline": cpu,
         "e2e": e2e,
-        "gpu_launches": args.steps * chunk,
+        "gpu_launches": args.steps * launches_per_call(form, chunk),
         "clocks": clk,
     }
     print(json.dumps(line), flush=True)

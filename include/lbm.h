@@ -165,7 +165,10 @@ void lbm_params_default(lbm_params* p);
 int lbm_derive(const lbm_params* p, lbm_derived* d);
 
 /* Device bytes a run will hold (two copies of the distributions, the exchange
- * history and small scratch).  -1 if p is invalid. */
+ * history and small scratch).  A run that lbm_step advances two steps per
+ * launch (lbm_set_step_form) adds a second exchange-history array, 4 bytes
+ * per node of row pitch, at its first such lbm_step; batches and the server
+ * never allocate it.  -1 if p is invalid. */
 int64_t lbm_state_bytes(const lbm_params* p);
 
 /* Creates a run, allocates its device state (through alloc/release when
@@ -183,8 +186,8 @@ int lbm_create_ex(const lbm_params* p, void* cuda_stream, lbm_alloc_fn alloc,
  * flag).  Large nsteps are replayed from a captured CUDA graph.  Each step is
  * launched as a programmatic dependent of the previous one in the stream.
  * The step kernel runs one node per thread in blocks of 64 x 2 threads on
- * grids of up to 40,000 nodes and 128 x 1 on larger ones, or node pairs (see
- * lbm_set_step_form). */
+ * grids of up to 40,000 nodes and 128 x 1 on larger ones, or node pairs, or
+ * two steps per launch (see lbm_set_step_form). */
 int lbm_step(lbm_handle* h, int64_t nsteps);
 
 /* Step form of a run (the paper has no counterpart: an implementation
@@ -194,18 +197,34 @@ int lbm_step(lbm_handle* h, int64_t nsteps);
  * D2Q5 thermal lattices, volumetric blend, FP32/FP16/BF16 storage), the others
  * keep one node per thread.  On grids of at least 1,572,864 nodes (state far
  * beyond L2) each node-pair block also asks L2 for the rows that blocks 48
- * rows further on will read (bulk L2 prefetch).  LBM_STEP_FORM_AUTO (the
- * default): node pairs for FP16/BF16 runs of at least 1,572,864 (1536 x 1024)
- * nodes.  Both forms compute the same
- * step to within a few roundings of the FP32 arithmetic.  Applies to later
- * lbm_step calls and to batches created afterwards; synchronises the run's
+ * rows further on will read (bulk L2 prefetch).  LBM_STEP_FORM_TWO_STEPS:
+ * two time steps per launch for runs with flow in FP32/FP16/BF16 storage (the
+ * others step one node per thread): each block of 34 x H threads advances its
+ * tile and the one-node ring around it one step into shared memory, then the
+ * tile's 32 x (H - 2) inner nodes a second step into the other state copy (H
+ * from 4 to 16 per grid: one tile per SM where the grid allows, else H = 12);
+ * lbm_step takes it for 4 steps or more (an odd remainder and steps that bring
+ * the run back to state copy 0 are single steps).  LBM_STEP_FORM_AUTO (the
+ * default), for runs with flow and the D2Q5 thermal lattices: two steps per
+ * launch on grids of up to 65,536 nodes in FP32/FP16/BF16 and on FP32 grids
+ * of at least 786,432 nodes (state beyond L2); node pairs for FP16/BF16 runs
+ * of at least 1,572,864 (1536 x 1024) nodes; otherwise one node per thread.
+ * Two steps per launch give the states of one step per launch bit for bit;
+ * node pairs agree with them to within a few roundings of the FP32
+ * arithmetic.  A run that steps two steps per launch keeps a second
+ * exchange-history array (4 bytes per node of row pitch), allocated on the
+ * run's allocator at the first lbm_step that uses the form (LBM_ERR_OOM if
+ * that fails; nothing stepped).  Applies to later lbm_step calls and to
+ * batches created afterwards (batches advance one step per launch: a run in
+ * the two-step form steps there one node per thread); synchronises the run's
  * stream when it drops a captured graph.  LBM_ERR_ARG for another value. */
 #define LBM_STEP_FORM_AUTO 0
 #define LBM_STEP_FORM_SINGLE 1
 #define LBM_STEP_FORM_PAIRS 2
+#define LBM_STEP_FORM_TWO_STEPS 3
 int lbm_set_step_form(lbm_handle* h, int32_t form);
 
-/* The form (LBM_STEP_FORM_SINGLE or LBM_STEP_FORM_PAIRS) a run with
+/* The form (LBM_STEP_FORM_SINGLE, _PAIRS or _TWO_STEPS) a run with
  * parameters p steps in when set to `form`, written to *used.  Host only,
  * needs no GPU.  Returns lbm_derive's error for invalid p, LBM_ERR_ARG for
  * another form value or NULL pointers. */

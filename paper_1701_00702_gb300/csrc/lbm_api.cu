@@ -6,10 +6,16 @@
 #include <cstring>
 #include <memory>
 #include <new>
+#include <type_traits>
+#include <utility>
 #include <vector>
 
 #include "lbm.h"
 #include "lbm_launch.cuh"
+
+static_assert(LBM_STEP_FORM_AUTO == lbmk::FORM_AUTO && LBM_STEP_FORM_SINGLE == lbmk::FORM_SINGLE &&
+                  LBM_STEP_FORM_PAIRS == lbmk::FORM_PAIRS && LBM_STEP_FORM_TWO_STEPS == lbmk::FORM_TWO_STEPS,
+              "step form values");
 
 namespace {
 
@@ -192,6 +198,8 @@ struct lbm_handle {
     char* base = nullptr;
     void* buf[2] = {nullptr, nullptr};
     void* dT = nullptr;
+    void* dT2 = nullptr;   // second history array of the two-step form (allocated on first use)
+    int t2h = 0;              // its block height (chosen with dT2)
     unsigned int* status = nullptr;
     double* scratch = nullptr;
     double* diag_out = nullptr;
@@ -233,6 +241,7 @@ lbmk::StepParams<R> make_params(const lbm_handle* h, int from) {
     P.dst = static_cast<char*>(h->buf[1 - from]);
     P.cpr = h->L.cpr;
     P.dT = static_cast<R*>(h->dT);
+    P.dT_out = static_cast<R*>(h->dT2);
     P.status = h->status;
     P.nx = p.nx;
     P.ny = p.ny;
@@ -351,12 +360,51 @@ cudaError_t enqueue_one(lbm_handle* h, int from, cudaStream_t s) {
     }
 }
 
+// Two steps from copy `from` into the other copy.  The history goes from h->dT
+// to h->dT2 in the first launch of a pair and back in the second (back = 1),
+// so that it is in h->dT after every even number of launches.
+cudaError_t enqueue_two(lbm_handle* h, int from, int back, cudaStream_t s) {
+    const int q = h->p.thermal_q;
+    auto run = [&](auto P, auto tag) {
+        if (back) std::swap(P.dT, P.dT_out);
+        return lbmk::launch_step2<decltype(tag)::value>(P, q, h->t2h, s);
+    };
+    switch (h->p.precision) {
+        case LBM_F32: return run(make_params<float>(h, from), std::integral_constant<int, lbmk::MODE_F32>{});
+        case LBM_F16: return run(make_params<float>(h, from), std::integral_constant<int, lbmk::MODE_F16>{});
+        case LBM_BF16: return run(make_params<float>(h, from), std::integral_constant<int, lbmk::MODE_BF16>{});
+        default: return cudaErrorInvalidConfiguration;
+    }
+}
+
+bool two_steps(const lbm_handle* h) {
+    return lbmk::two_steps_for(h->p.precision, h->p.thermal_q, h->p.flow, (long long)h->p.nx * h->p.ny, h->form);
+}
+
+// The second history array and the block height of the two-step form, on
+// first use (the SM count of the current device).
+int ensure_dT2(lbm_handle* h) {
+    if (h->dT2) return LBM_OK;
+    int dev = 0, nsm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return cuda_fail(h);
+    h->t2h = lbmk::t2_block(h->p.nx, h->p.ny, nsm);
+    h->dT2 = dev_alloc(h, h->L.dT_bytes);
+    return h->dT2 ? LBM_OK : LBM_ERR_OOM;
+}
+
+// kGraphSteps steps from copy 0 back to copy 0: single steps, or kGraphSteps / 2
+// two-step launches (an even number, so the history ends in h->dT).
 int build_graph(lbm_handle* h) {
     if (h->graph) return LBM_OK;
     if (!h->cap && cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking) != cudaSuccess) return cuda_fail(h);
     if (cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return cuda_fail(h);
     cudaError_t e = cudaSuccess;
-    for (int i = 0; i < kGraphSteps && e == cudaSuccess; ++i) e = enqueue_one(h, i & 1, h->cap);
+    if (two_steps(h)) {
+        for (int i = 0; i < kGraphSteps / 2 && e == cudaSuccess; ++i) e = enqueue_two(h, i & 1, i & 1, h->cap);
+    } else {
+        for (int i = 0; i < kGraphSteps && e == cudaSuccess; ++i) e = enqueue_one(h, i & 1, h->cap);
+    }
     cudaGraph_t g = nullptr;
     cudaError_t e2 = cudaStreamEndCapture(h->cap, &g);
     if (e != cudaSuccess || e2 != cudaSuccess || !g) {
@@ -417,6 +465,7 @@ void free_handle(lbm_handle* h) {
     if (!h) return;
     if (h->stream) cudaStreamSynchronize(h->stream);
     if (h->graph) cudaGraphExecDestroy(h->graph);
+    if (h->dT2) dev_free(h, h->dT2);
     if (h->cap) cudaStreamDestroy(h->cap);
     dev_free(h, h->base);
     if (h->stream && !h->release) cudaStreamSynchronize(h->stream);
@@ -526,6 +575,11 @@ int lbm_step(lbm_handle* h, int64_t nsteps) {
     if (!h || nsteps < 0) return LBM_ERR_ARG;
     if (h->sticky != LBM_OK) return h->sticky;
     int64_t n = nsteps;
+    const bool two = two_steps(h);
+    if (two && n >= 4) {
+        const int rc = ensure_dT2(h);
+        if (rc != LBM_OK) return rc;
+    }
     while (n > 0 && h->cur != 0) {
         if (enqueue_one(h, h->cur, h->stream) != cudaSuccess) return cuda_fail(h);
         h->cur ^= 1;
@@ -541,6 +595,12 @@ int lbm_step(lbm_handle* h, int64_t nsteps) {
             n -= kGraphSteps;
         }
     }
+    while (two && n >= 4) {   // two launches of two steps: copy and history back where they were
+        if (enqueue_two(h, h->cur, 0, h->stream) != cudaSuccess || enqueue_two(h, h->cur ^ 1, 1, h->stream) != cudaSuccess)
+            return cuda_fail(h);
+        h->steps += 4;
+        n -= 4;
+    }
     while (n > 0) {
         if (enqueue_one(h, h->cur, h->stream) != cudaSuccess) return cuda_fail(h);
         h->cur ^= 1;
@@ -551,15 +611,18 @@ int lbm_step(lbm_handle* h, int64_t nsteps) {
 }
 
 int lbm_step_form_for(const lbm_params* p, int32_t form, int32_t* used) {
-    if (!p || !used || form < LBM_STEP_FORM_AUTO || form > LBM_STEP_FORM_PAIRS) return LBM_ERR_ARG;
+    if (!p || !used || form < LBM_STEP_FORM_AUTO || form > LBM_STEP_FORM_TWO_STEPS) return LBM_ERR_ARG;
     const int rc = derive_impl(p, nullptr);
     if (rc != LBM_OK) return rc;
-    *used = lbmk::form_for(p->precision, p->thermal_q, p->flow, p->solid_scheme, (long long)p->nx * p->ny, form);
+    const long long nodes = (long long)p->nx * p->ny;
+    *used = lbmk::two_steps_for(p->precision, p->thermal_q, p->flow, nodes, form)
+                ? LBM_STEP_FORM_TWO_STEPS
+                : lbmk::form_for(p->precision, p->thermal_q, p->flow, p->solid_scheme, nodes, form);
     return LBM_OK;
 }
 
 int lbm_set_step_form(lbm_handle* h, int32_t form) {
-    if (!h || form < LBM_STEP_FORM_AUTO || form > LBM_STEP_FORM_PAIRS) return LBM_ERR_ARG;
+    if (!h || form < LBM_STEP_FORM_AUTO || form > LBM_STEP_FORM_TWO_STEPS) return LBM_ERR_ARG;
     if (form != h->form && h->graph) {   // the captured steps used the old form
         if (cudaStreamSynchronize(h->stream) != cudaSuccess) return cuda_fail(h);
         cudaGraphExecDestroy(h->graph);

@@ -172,6 +172,7 @@ struct StepParams {
     const char* src;     // current state copy, [chunk][plane][kChunk]
     char* dst;           // next state copy
     R* dT;               // [ny][pitch] exchange history T_m - T_f of the previous step
+    R* dT_out;           // two-step kernel: the history after its second step (another array)
     unsigned int* status;
     int nx, ny, pitch;   // pitch = cpr * kChunk
     int cpr;             // chunks per row
@@ -488,15 +489,17 @@ __device__ __forceinline__ void stb(typename ModeTraits<M>::B* p, R v) {
     *p = from_f<B>(v);
 }
 
-// The nine flow populations of one node (f_0 and the pairs of f_from_m9p).
+// The nine flow populations of one node (f_0 and the pairs of f_from_m9p);
+// PS: elements from one plane to the next (kChunk in a state copy, where the
+// inlined constant folds into the addresses).
 template <int M>
 __device__ __forceinline__ void store_flow(typename ModeTraits<M>::B* db, typename ModeTraits<M>::R f0,
-                                           const V2<typename ModeTraits<M>::R>* F) {
+                                           const V2<typename ModeTraits<M>::R>* F, int PS = kChunk) {
     stb<M>(db, f0);
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-        stb<M>(db + (2 * j + 1) * kChunk, F[j].x);
-        stb<M>(db + (2 * j + 2) * kChunk, F[j].y);
+        stb<M>(db + (2 * j + 1) * PS, F[j].x);
+        stb<M>(db + (2 * j + 2) * PS, F[j].y);
     }
 }
 
@@ -818,12 +821,13 @@ __device__ __forceinline__ void node_state(const StepParams<typename ModeTraits<
 // (internal energy) that the collision produced: the FP32 PCM rest population
 // to float-float accuracy, the FP32 metal one to one rounding, the 16-bit forms
 // to FP32 rounding as readers decode them, FP64 to FP64 rounding.  db and dw
-// point at the node's element in bulk plane 0 and wide plane 0 of the next copy.
+// point at the node's element in bulk plane 0 and wide plane 0 of the next copy
+// (PS elements from one plane to the next).
 template <int M, int QT, bool FLOW>
 __device__ __forceinline__ void store_thermal(const StepParams<typename ModeTraits<M>::R>& P,
                                               V2<typename ModeTraits<M>::R>* nm, typename ModeTraits<M>::R n0ghi,
                                               typename ModeTraits<M>::R n0glo, typename ModeTraits<M>::R n0h,
-                                              typename ModeTraits<M>::B* db, float* dw) {
+                                              typename ModeTraits<M>::B* db, float* dw, int PS = kChunk) {
     using R = typename ModeTraits<M>::R;
     using B = typename ModeTraits<M>::B;
     using PL = Planes<M, QT, FLOW>;
@@ -846,8 +850,8 @@ __device__ __forceinline__ void store_thermal(const StepParams<typename ModeTrai
         for (int k = 1; k < QT; ++k) {
             const V2<float> e = fma2(P.nwmv[QT == 5 ? 1 : k], ref, v[k]);
             const B bg = from_f<B>(e.x), bh = from_f<B>(e.y);
-            db[PL::pcm(k) * kChunk] = bg;
-            db[PL::met(k) * kChunk] = bh;
+            db[PL::pcm(k) * PS] = bg;
+            db[PL::met(k) * PS] = bh;
             const V2<float> d = {to_f(bg), to_f(bh)};
             sd = k == 1 ? d : add2(sd, d);
         }
@@ -855,12 +859,12 @@ __device__ __forceinline__ void store_thermal(const StepParams<typename ModeTrai
         float T, fl;
         enthalpy_state(P, Y.x, T, fl);
         dw[0] = Y.x - P.om_cf * T;
-        dw[kChunk] = Y.y * P.rest_m;
+        dw[PS] = Y.y * P.rest_m;
     } else {
 #pragma unroll
         for (int k = 1; k < QT; ++k) {
-            stb<M>(db + PL::pcm(k) * kChunk, v[k].x);
-            stb<M>(db + PL::met(k) * kChunk, v[k].y);
+            stb<M>(db + PL::pcm(k) * PS, v[k].x);
+            stb<M>(db + PL::met(k) * PS, v[k].y);
         }
         V2<R> sm = v[1];
 #pragma unroll
@@ -871,12 +875,12 @@ __device__ __forceinline__ void store_thermal(const StepParams<typename ModeTrai
 #pragma unroll
             for (int k = 0; k < QT; ++k) vg[k] = v[k].x;
             const FF r = ff_accumulate<QT>(FF{n0ghi, n0glo}, vg, -1.0f);
-            stb<M>(db + PL::pcm(0) * kChunk, r.hi);
-            stb<M>(db + PL::lo * kChunk, r.lo);
+            stb<M>(db + PL::pcm(0) * PS, r.hi);
+            stb<M>(db + PL::lo * PS, r.lo);
         } else {
-            stb<M>(db + PL::pcm(0) * kChunk, rest.x);
+            stb<M>(db + PL::pcm(0) * PS, rest.x);
         }
-        stb<M>(db + PL::met(0) * kChunk, rest.y);
+        stb<M>(db + PL::met(0) * PS, rest.y);
     }
 }
 
@@ -888,7 +892,8 @@ __device__ __forceinline__ void store_thermal(const StepParams<typename ModeTrai
 // node's element in flow plane 0 of the next copy.
 template <int M, int QT, bool FLOW>
 __device__ __forceinline__ void flow_collide(const StepParams<typename ModeTraits<M>::R>& P,
-                                             const NodeState<M, QT, FLOW>& n, typename ModeTraits<M>::B* db) {
+                                             const NodeState<M, QT, FLOW>& n, typename ModeTraits<M>::B* db,
+                                             int PS = kChunk) {
     using R = typename ModeTraits<M>::R;
     if constexpr (FLOW) {
       if (P.solid_scheme && n.fl <= R(0.5)) {
@@ -898,7 +903,7 @@ __device__ __forceinline__ void flow_collide(const StepParams<typename ModeTrait
         R f0;
         V2<R> F[4];
         f_from_m9p<R, kFlowScale<M>>(n.mp[0], m, f0, F);
-        store_flow<M>(db, f0, F);
+        store_flow<M>(db, f0, F, PS);
       } else {
         // Eq. 3 at the node's velocity (u = u_b = 0 on walls)
         const R drag = P.drag_lin + P.drag_forch * n.um;
@@ -935,7 +940,7 @@ __device__ __forceinline__ void flow_collide(const StepParams<typename ModeTrait
         R f0;
         V2<R> Fo[4];
         f_from_m9p<R, kFlowScale<M>>(drho, m, f0, Fo);
-        store_flow<M>(db, f0, Fo);
+        store_flow<M>(db, f0, Fo, PS);
       }
     }
 }
@@ -948,7 +953,8 @@ template <int M, int QT, bool FLOW, bool PH>
 __device__ __forceinline__ typename ModeTraits<M>::R thermal_collide(const StepParams<typename ModeTraits<M>::R>& P,
                                                                      NodeState<M, QT, FLOW>& n,
                                                                      typename ModeTraits<M>::R dTp,
-                                                                     typename ModeTraits<M>::B* db, float* dw) {
+                                                                     typename ModeTraits<M>::B* db, float* dw,
+                                                                     int PS = kChunk) {
     using R = typename ModeTraits<M>::R;
     // exchange sources, Eqs. 36 and 47 with the backward difference of Remark III
     const R dTn = n.Tm - n.Tf;
@@ -1000,7 +1006,7 @@ __device__ __forceinline__ typename ModeTraits<M>::R thermal_collide(const StepP
         hi = n.th[0].x + S_pcm;
         lo = R(0);
     }
-    store_thermal<M, QT, FLOW>(P, n.th, hi, lo, hm, db, dw);
+    store_thermal<M, QT, FLOW>(P, n.th, hi, lo, hm, db, dw, PS);
     return dTn;
 }
 
@@ -1098,6 +1104,122 @@ __global__ void __launch_bounds__(256, (kMinBlocks<M, QT, FLOW>)) fused_step(con
     if (x >= P.nx || y >= P.ny) return;
     griddep_wait();
     step_node<M, QT, FLOW, PH>(P, x, y);
+}
+
+// ---------------------------------------------------------------------------
+// Two time steps per launch
+// ---------------------------------------------------------------------------
+// On small grids (state resident in L2) a step costs the launch-to-launch floor
+// of a dependent launch plus one warp's dependency chain with its L2 loads,
+// more than the issue time of the work itself; on grids whose state exceeds
+// L2 a step moves the whole state through HBM.  fused_step2 advances two time
+// steps per launch.  A block of kT2W x H threads (one node each, 4 <= H <=
+// kT2H) owns an inner tile of (kT2W - 2) x (H - 2) nodes and the one-node ring
+// around it:
+//   1. every thread advances its node one step from the state in global
+//      memory (the ring's nodes belong to neighbouring tiles and are advanced
+//      there too), storing the result in shared memory in the storage
+//      encoding of a state copy, as a global store would;
+//   2. after a barrier, the inner nodes advance a second step with their
+//      neighbourhood read from shared memory, and store to the next copy.
+// Tile origins are clamped to the grid (the last tile along an axis ends at
+// the grid's edge, overlapping its neighbour), so that a wall node's x_f and
+// the neighbours of x_f lie in the tile (H >= 4).  Nodes of overlapping tiles
+// are computed by both blocks with the same inputs and code, and written with
+// the same values.  The history is read from P.dT and written to P.dT_out:
+// other blocks still read the previous history of their rings.  Flow runs
+// only.  The host picks H per grid (t2_block in the launcher).  Two builds of
+// the kernel: HM = kT2H (any H up to 16; one block per SM on the grids that
+// take it) and HM = kT2HMany (H = 12 for grids of many tiles per SM, launch
+// bounds that leave three FP32 D2Q5 blocks resident: at 52 registers only two
+// fit, 2048^2 FP32 104 against 84 us per step; two blocks of the other builds,
+// which would spill under the three-block cap).
+constexpr int kT2W = 34, kT2H = 16, kT2HMany = 12, kT2Max = kT2W * kT2H;
+
+template <int HM, int M, int QT>
+constexpr int kT2Blocks = HM == kT2HMany ? (M == MODE_F32 && QT == 5 ? 3 : 2) : 1;
+
+// Dynamic shared memory of a two-step block of up to HM rows, planes
+// kT2W * HM elements apart: the bulk planes (storage type), the wide planes
+// (FP32) and the history.
+template <int M, int QT, int HM>
+struct Tile2 {
+    using PL = Planes<M, QT, true>;
+    static constexpr int n = kT2W * HM;
+    static constexpr size_t wide_off = (size_t)PL::bulk * n * sizeof(typename ModeTraits<M>::B);
+    static constexpr size_t dT_off = wide_off + (size_t)PL::wide * n * sizeof(float);
+    static constexpr size_t bytes = dT_off + (size_t)n * sizeof(typename ModeTraits<M>::R);
+    static_assert(wide_off % 16 == 0 && dT_off % 16 == 0, "16-byte aligned parts");
+};
+
+// Neighbourhood of the node at tile index i (pull node) in the tile, planes
+// PS elements apart.
+template <int M, int PS>
+struct PullTile {
+    const typename ModeTraits<M>::B* b;
+    const float* wd;
+    int i;
+    __device__ __forceinline__ int at(int q) const { return i + (src_row(q) - 1) * kT2W + (src_col(q) - 1); }
+    __device__ __forceinline__ typename ModeTraits<M>::R bulk(int q, int plane) const {
+        return to_f(b[plane * PS + at(q)]);
+    }
+    __device__ __forceinline__ float wide(int q, int p) const { return wd[p * PS + at(q)]; }
+};
+
+// First node of the ring of tile k along an axis of n nodes with inner width w.
+__host__ __device__ __forceinline__ int t2_origin(int k, int w, int n) {
+    return (n > w ? min(k * w, n - w) : 0) - 1;
+}
+
+template <int M, int QT, bool PH, int HM>
+__global__ void __launch_bounds__(kT2W * HM, (kT2Blocks<HM, M, QT>)) fused_step2(const __grid_constant__ StepParams<typename ModeTraits<M>::R> P) {
+    using R = typename ModeTraits<M>::R;
+    using B = typename ModeTraits<M>::B;
+    using TL = Tile2<M, QT, HM>;
+    extern __shared__ __align__(16) unsigned char t2_smem[];
+    B* sb = reinterpret_cast<B*>(t2_smem);
+    float* sw = reinterpret_cast<float*>(t2_smem + TL::wide_off);
+    R* sdT = reinterpret_cast<R*>(t2_smem + TL::dT_off);
+    const int H = blockDim.y;   // blockDim.x == kT2W, H <= HM
+    const int lx = threadIdx.x, ly = threadIdx.y, i = ly * kT2W + lx;
+    const int X0 = t2_origin(blockIdx.x, kT2W - 2, P.nx), Y0 = t2_origin(blockIdx.y, H - 2, P.ny);
+    // step-1 node: coordinates wrapped on periodic sides, none beyond a walled side
+    int x = X0 + lx, y = Y0 + ly;
+    bool live = true;
+    if (x < 0 || x >= P.nx) {
+        if (P.per_x) x = ((x % P.nx) + P.nx) % P.nx;
+        else live = false;
+    }
+    if (y < 0 || y >= P.ny) {
+        if (P.per_y) y = ((y % P.ny) + P.ny) % P.ny;
+        else live = false;
+    }
+    griddep_wait();
+    if (live) {
+        NodeState<M, QT, true> n;
+        bool wall;
+        node_state<M, QT, true>(P, x, y, n, wall);
+        const R dTp = P.dT[y * P.pitch + x];
+        flow_collide<M, QT, true>(P, n, sb + i, TL::n);
+        sdT[i] = thermal_collide<M, QT, true, PH>(P, n, dTp, sb + i, kSplit<M> ? sw + i : nullptr, TL::n);
+        const bool bad = !(fabs(n.H) + fabs(n.Tm) + n.rho < R(1e30)) || !(n.rho > R(0)) ||
+                         !(n.ux * n.ux + n.uy * n.uy <= R(0.09));
+        if (bad) atomicOr(P.status, STATUS_UNSTABLE);
+    }
+    __syncthreads();
+    // step 2: the inner nodes of the tile that lie in the grid
+    const int x2 = X0 + lx, y2 = Y0 + ly;
+    if (lx < 1 || lx > kT2W - 2 || ly < 1 || ly > H - 2 || x2 >= P.nx || y2 >= P.ny) return;
+    const WallAt wa = wall_at(P, x2, y2);
+    const PullTile<M, TL::n> a{sb, sw, i + (wa.ys - y2) * kT2W + (wa.xs - x2)};
+    NodeState<M, QT, true> n;
+    node_state_from<M, QT, true>(P, a, wa, n);
+    flow_collide<M, QT, true>(P, n, next_bulk<M, QT, true>(P, x2, y2));
+    P.dT_out[y2 * P.pitch + x2] =
+        thermal_collide<M, QT, true, PH>(P, n, sdT[i], next_bulk<M, QT, true>(P, x2, y2), next_wide<M, QT, true>(P, x2, y2));
+    const bool bad = !(fabs(n.H) + fabs(n.Tm) + n.rho < R(1e30)) || !(n.rho > R(0)) ||
+                     !(n.ux * n.ux + n.uy * n.uy <= R(0.09));
+    if (bad) atomicOr(P.status, STATUS_UNSTABLE);
 }
 
 // ---------------------------------------------------------------------------

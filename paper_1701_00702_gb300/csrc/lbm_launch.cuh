@@ -160,7 +160,7 @@ inline dim3 step_block(int nx, int ny) {
 // against 39.2; at 1024^2, whose state nearly fits in L2, one node per thread
 // is faster, 18.9 against 19.4; in FP32, bound by HBM, one node per thread is
 // faster at every size).
-enum : int { FORM_AUTO = 0, FORM_SINGLE = 1, FORM_PAIRS = 2 };
+enum : int { FORM_AUTO = 0, FORM_SINGLE = 1, FORM_PAIRS = 2, FORM_TWO_STEPS = 3 };
 constexpr long long kPairMinNodes = 3ll << 19;
 
 // The rule (host code; lbm_step_form_for reports it): the form a run takes,
@@ -168,9 +168,30 @@ constexpr long long kPairMinNodes = 3ll << 19;
 inline int form_for(int mode, int qt, int flow, int solid_scheme, long long nodes, int form) {
     const bool pairs = mode != MODE_F64 && qt == 5 && flow && !solid_scheme;
     if (form == FORM_PAIRS) return pairs ? FORM_PAIRS : FORM_SINGLE;
-    if (form == FORM_SINGLE) return FORM_SINGLE;
+    if (form == FORM_SINGLE || form == FORM_TWO_STEPS) return FORM_SINGLE;
     if (pairs && (mode == MODE_F16 || mode == MODE_BF16) && nodes >= kPairMinNodes) return FORM_PAIRS;
     return FORM_SINGLE;
+}
+
+// Two time steps per launch (fused_step2) for runs with flow in FP32, FP16
+// or BF16 storage: forced by FORM_TWO_STEPS; automatic, for the D2Q5 thermal
+// lattices, on grids of up to kTwoStepSmallMaxNodes nodes (the launch floor and
+// one dependency chain per step dominate there) and for FP32 on grids of at
+// least kTwoStepF32MinNodes (two state copies, 168 bytes per node, exceed the
+// 129 MB L2, and two steps per launch move the state through HBM once per two
+// steps).  Between the two the state sits in L2 and the step is bound by
+// instruction issue, which the redundant ring only adds to (FP32, us per step,
+// one against two steps per launch: 512^2 4.99 / 5.98, 768^2 11.1 / 12.2,
+// 896^2 19.1 / 16.9, 1024^2 26.5 / 21.9, 2048^2 99.7 / 81.2; FP16 320^2 3.17 /
+// 3.82).  Single steps (an odd remainder, batches) keep the form above.
+constexpr long long kTwoStepSmallMaxNodes = 65536;
+constexpr long long kTwoStepF32MinNodes = 3ll << 18;
+
+inline bool two_steps_for(int mode, int qt, int flow, long long nodes, int form) {
+    const bool can = mode != MODE_F64 && flow;
+    if (form == FORM_TWO_STEPS) return can;
+    if (form != FORM_AUTO || !can || qt != 5) return false;
+    return nodes <= kTwoStepSmallMaxNodes || (mode == MODE_F32 && nodes >= kTwoStepF32MinNodes);
 }
 
 template <int M>
@@ -274,6 +295,86 @@ cudaError_t launch_step(const StepParams<typename ModeTraits<M>::R>& P, int qt, 
     return cudaLaunchKernelExC(&cfg, L.fn, args);
 }
 
+// Block height of the two-step kernel (blocks of kT2W x H threads, inner
+// tiles of (kT2W - 2) x (H - 2) nodes) for an nx x ny grid on nsm SMs.  When
+// the grid fits in one tile per SM, H is the one whose busiest SM runs the
+// fewest node updates (its tiles, rounded up over the SMs, times the block's
+// warps for the first step and the inner tile for the second): 128^2 on 152
+// SMs takes H = 6 (128 tiles), 192^2 H = 10, 256^2 H = 16 (152 tiles).  Larger
+// grids take H = kT2HMany = 12, measured fastest there (FP32: three resident
+// blocks of 13 warps per SM; 1024^2 and 2048^2 against H = 6, 8, 10, 14, 16).
+
+inline long long t2_tiles(int n, int inner) { return n > inner ? (n + inner - 1) / inner : 1; }
+
+inline dim3 t2_grid(int nx, int ny, int h) {
+    return dim3((unsigned)t2_tiles(nx, kT2W - 2), (unsigned)t2_tiles(ny, h - 2), 1u);
+}
+
+inline int t2_block(int nx, int ny, int nsm) {
+    if (nsm < 1) nsm = 1;
+    int best = kT2H;
+    long long best_cost = -1;
+    for (int h = 4; h <= kT2H; ++h) {
+        const long long tiles = t2_tiles(nx, kT2W - 2) * t2_tiles(ny, h - 2);
+        if (tiles > nsm) continue;
+        const long long cost = (long long)((kT2W * h + 31) / 32 * 32) + (long long)(kT2W - 2) * (h - 2);
+        if (best_cost < 0 || cost < best_cost) {
+            best = h;
+            best_cost = cost;
+        }
+    }
+    return best_cost < 0 ? kT2HMany : best;
+}
+
+// Two steps from copy P.src to P.dst, history P.dT -> P.dT_out, as a
+// programmatic dependent of the previous launch in the stream.
+// The build of the kernel for block height h (h == kT2HMany: the many-tiles
+// build) and its dynamic shared memory.
+template <int M, int HM>
+const void* step2_kernel_hm(int qt, int phase_k) {
+    if (qt == 5) return phase_k ? (const void*)fused_step2<M, 5, true, HM> : (const void*)fused_step2<M, 5, false, HM>;
+    return phase_k ? (const void*)fused_step2<M, 9, true, HM> : (const void*)fused_step2<M, 9, false, HM>;
+}
+
+template <int M>
+const void* step2_kernel(int qt, int phase_k, int h) {
+    if constexpr (M != MODE_F64) {
+        return h == kT2HMany ? step2_kernel_hm<M, kT2HMany>(qt, phase_k) : step2_kernel_hm<M, kT2H>(qt, phase_k);
+    }
+    return nullptr;
+}
+
+template <int M>
+size_t step2_smem(int qt, int h) {
+    if constexpr (M != MODE_F64) {
+        if (h == kT2HMany) return qt == 5 ? Tile2<M, 5, kT2HMany>::bytes : Tile2<M, 9, kT2HMany>::bytes;
+        return qt == 5 ? Tile2<M, 5, kT2H>::bytes : Tile2<M, 9, kT2H>::bytes;
+    }
+    return 0;
+}
+
+template <int M>
+cudaError_t launch_step2(const StepParams<typename ModeTraits<M>::R>& P, int qt, int h, cudaStream_t s) {
+    if (h < 4 || h > kT2H) return cudaErrorInvalidConfiguration;
+    const void* fn = step2_kernel<M>(qt, P.phase_k, h);
+    if (!fn) return cudaErrorInvalidConfiguration;
+    const size_t smem = step2_smem<M>(qt, h);
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    void* args[1] = {const_cast<StepParams<typename ModeTraits<M>::R>*>(&P)};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = t2_grid(P.nx, P.ny, h);
+    cfg.blockDim = dim3((unsigned)kT2W, (unsigned)h, 1u);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelExC(&cfg, fn, args);
+}
+
 template <int M>
 cudaError_t launch_fields(const StepParams<typename ModeTraits<M>::R>& P,
                           const FieldOut<typename ModeTraits<M>::R>& o, int qt, int flow, cudaStream_t s) {
@@ -349,6 +450,7 @@ int batch_blocks_per_sm(int qt, int flow, int ph) {
                                          int, int, cudaStream_t);                                               \
     template int batch_blocks_per_sm<M>(int, int, int);                                                   \
     template const void* group_kernel<M>(int, int, int);                                                    \
+    template cudaError_t launch_step2<M>(const StepParams<ModeTraits<M>::R>&, int, int, cudaStream_t);     \
     template StepLaunch step_launch<M>(const StepParams<ModeTraits<M>::R>&, int, int, int, dim3);
 
 #define LBMK_INSTANTIATE_CONVERT(M)                                                                           \

@@ -293,7 +293,8 @@ class Solver:
         return self
 
     def set_step_form(self, form: int) -> "Solver":
-        """0: automatic, 1: one node per thread, 2: node pairs (lbm_set_step_form)."""
+        """0: automatic, 1: one node per thread, 2: node pairs, 3: two time steps
+        per launch (lbm_set_step_form)."""
         _check(lib().lbm_set_step_form(self._h, int(form)), "lbm_set_step_form")
         return self
 

@@ -146,7 +146,6 @@ def test_create_without_gpu_fails_cleanly(lbm):
     (dict(n=1536, ny=1024, precision=3), 0, 2),
     (dict(n=1536, ny=1023, precision=2), 0, 1),            # one row short of 1,572,864 nodes
     (dict(n=1024, precision=2), 0, 1),
-    (dict(n=2048, precision=1), 0, 1),                      # FP32: HBM-bound, one node per thread
     (dict(n=2048, precision=0), 0, 1),
     (dict(n=2048, precision=2, thermal_q=9), 0, 1),
     (dict(n=2048, precision=2, flow=0), 0, 1),
@@ -158,6 +157,32 @@ def test_create_without_gpu_fails_cleanly(lbm):
     (dict(n=64, precision=0), 2, 1),                        # no FP64 node-pair kernel
     (dict(n=64, precision=1, thermal_q=9), 2, 1),
     (dict(n=2048, precision=2), 1, 1),
+    # automatic two steps per launch (D2Q5, flow, FP32/FP16/BF16): up to 256 x 256 nodes, and
+    # FP32 from 786,432 nodes (state beyond L2); between them one step per launch
+    (dict(n=256, precision=1), 0, 3),
+    (dict(n=256, precision=2), 0, 3),
+    (dict(n=64, precision=3), 0, 3),
+    (dict(n=256, ny=257, precision=1), 0, 1),
+    (dict(n=512, precision=1), 0, 1),
+    (dict(n=768, precision=1), 0, 1),
+    (dict(n=1024, ny=767, precision=1), 0, 1),
+    (dict(n=1024, ny=768, precision=1), 0, 3),
+    (dict(n=1024, precision=1), 0, 3),
+    (dict(n=2048, precision=1), 0, 3),
+    (dict(n=4096, ny=256, precision=1, solid_scheme=1), 0, 3),
+    (dict(n=1024, precision=2), 0, 1),                     # 16-bit: one node per thread, then pairs
+    (dict(n=256, precision=0), 0, 1),
+    (dict(n=256, precision=1, thermal_q=9), 0, 1),
+    (dict(n=256, precision=1, flow=0), 0, 1),
+    (dict(n=256, precision=1), 1, 1),
+    (dict(n=256, precision=1), 2, 2),
+    # forced two steps per launch: runs with flow in FP32/FP16/BF16 storage, any lattice and variant
+    (dict(n=256, precision=1), 3, 3),
+    (dict(n=256, precision=2, thermal_q=9), 3, 3),
+    (dict(n=3, precision=3, L_char=100.0), 3, 3),
+    (dict(n=2048, precision=2, solid_scheme=1), 3, 3),
+    (dict(n=256, precision=0), 3, 1),                       # no FP64 two-step kernel
+    (dict(n=256, precision=1, flow=0), 3, 1),
 ])
 def test_step_form_rule(lbm, params, form, expected):
     """lbm_step_form_for reports the kernel form lbm_step takes (the same rule
@@ -170,6 +195,6 @@ def test_step_form_rule(lbm, params, form, expected):
 
 def test_step_form_query_rejects_bad_input(lbm):
     with pytest.raises(lbm.LbmError):
-        lbm.step_form_for(inputs.cavity(64), 3)
+        lbm.step_form_for(inputs.cavity(64), 4)
     with pytest.raises(lbm.LbmError):
         lbm.step_form_for(dict(inputs.cavity(64), nx=0), 0)

@@ -419,5 +419,78 @@ def test_step_forms_agree_over_a_graph_replayed_run(lbm):
         scale = max(np.abs(x).max(), 1e-3)
         assert np.abs(x.astype(np.float64) - y).max() / scale < 1e-5
     with pytest.raises(lbm.LbmError):
-        a.set_step_form(3)
+        a.set_step_form(4)
     a.close(); b.close()
+
+
+TWO_STEP_SHAPES = [
+    # (nx, ny, periodic_x, periodic_y): clamped last tiles, grids within one tile, the
+    # smallest periodic grids, several tiles along both axes; block shapes from 8 x 4
+    # to 34 x 16 threads (the shape follows the grid and the SM count)
+    (31, 13, 0, 0), (61, 13, 1, 1), (30, 6, 0, 0), (3, 3, 0, 0), (1, 1, 1, 1), (2, 7, 1, 0),
+    (97, 50, 0, 1), (131, 7, 1, 0), (257, 130, 0, 0), (300, 301, 1, 0), (256, 256, 0, 0),
+]
+
+
+@pytest.mark.parametrize("shape", TWO_STEP_SHAPES)
+@pytest.mark.parametrize("qt", [5, 9])
+@pytest.mark.parametrize("variant", ["default", "eq9", "bounce_back"])
+def test_two_step_kernel_from_random_state(lbm, oracle_mod, shape, qt, variant):
+    """Two time steps per launch (LBM_STEP_FORM_TWO_STEPS) in FP32: 4 and 8 steps
+    (two and four launches) from a random state.  The states equal those of one
+    step per launch bit for bit (the first step of each launch runs the same code
+    on the same inputs, the second reads the same values from shared memory), and
+    lie within FP32 rounding of the oracle: 4e-5 of array scale after 8 steps
+    (measured 1.6e-5 on the 3 x 3 and 1 x 1 grids, about 1e-6 on the others; one
+    step per launch has the same error)."""
+    nx, ny, px, py = shape
+    extra = VARIANTS[variant] if variant != "default" else {}
+    p = inputs.cavity(max(nx, ny), ny=ny, precision=1, thermal_q=qt, periodic_x=px, periodic_y=py,
+                      L_char=100.0, Ra=1e7, **extra)
+    p["nx"] = nx
+    assert lbm.step_form_for(p, 3) == 3
+    s, o = _random_pair(lbm, oracle_mod, p, seed=nx + 5 * ny + qt, f_base=W9[:, 0, 0])
+    ref = lbm.Solver(p).set_step_form(1)
+    ref.load(s.save())
+    s.set_step_form(3)
+    for n in (4, 4):
+        s.step(n)
+        ref.step(n)
+        o.run(n)
+        assert s.status() == 0
+        for a, b in zip(s.get_state(), ref.get_state()):
+            assert np.array_equal(a, b)
+        f, g, h, dT = s.get_state()
+        F, G, H, D = o.state()
+        for a, b, name in ((f, F - W9, "f - w"), (g, G, "g"), (h, H, "h"), (dT, D, "dT")):
+            scale = max(np.abs(b).max(), 1.0 if name == "dT" else 1e-3)
+            assert np.abs(a.astype(np.float64) - b).max() / scale < 4e-5, (name, n)
+    s.close()
+    ref.close()
+
+
+@pytest.mark.parametrize("prec", [1, 2, 3])
+def test_two_step_form_over_graph_replays_and_remainders(lbm, prec):
+    """Two steps per launch against one step per launch on the same cavity:
+    3 + 200 + 71 + 64 steps (single steps to state copy 0, graph replays, pairs of
+    two-step launches, single remainders), states within a few roundings of the
+    storage form; the exchange history is where checkpoints read it."""
+    p = inputs.cavity(200, ny=70, precision=prec)
+    a, b = lbm.Solver(p).set_step_form(1), lbm.Solver(p).set_step_form(3)
+    rtol = {1: 1e-5, 2: 8 * 2.0 ** -11, 3: 8 * 2.0 ** -8}[prec]
+    for n in (3, 200, 71, 64):
+        a.step(n)
+        b.step(n)
+        assert b.status() == 0
+        for x, y in zip(a.get_state(), b.get_state()):
+            scale = max(np.abs(x).max(), 1e-3)
+            assert np.abs(x.astype(np.float64) - y).max() / scale < rtol, n
+    # a checkpoint of the two-step run resumes in a single-step run
+    c = lbm.Solver(p).set_step_form(1)
+    c.load(b.save())
+    b.step(8)
+    c.step(8)
+    for x, y in zip(c.get_state(), b.get_state()):
+        scale = max(np.abs(x).max(), 1e-3)
+        assert np.abs(x.astype(np.float64) - y).max() / scale < rtol
+    a.close(); b.close(); c.close()
