@@ -97,17 +97,18 @@ def stored_bytes_per_update(qt: int, flow: int, precision: int) -> int:
 # taken for the kernel sources whose code hash is given; the bench reports
 # them only while the sources still hash to that value.
 ROOFLINE_TRAFFIC = {
-    "bytes_per_launch": 649179904,
-    "kernel_sources_sha256_16": "f39d41fb270ad124",
-    "gpu__dram_throughput_pct": 84.2,
+    "bytes_per_launch": 352023296 + 297352448,
+    "kernel_sources_sha256_16": "bcc808180c37dc7b",
+    "gpu__dram_throughput_pct": 84.5,
     "captured": "2026-12-04, ncu --set full --clock-control none, one launch after two "
                 "(profiles/fused_step_cavity2048_fp32.md)",
 }
 TWO_STEP_TRAFFIC = {
-    "bytes_per_launch": None,
-    "kernel_sources_sha256_16": None,
-    "gpu__dram_throughput_pct": None,
-    "captured": None,
+    "bytes_per_launch": 352051968 + 305717760,
+    "kernel_sources_sha256_16": "bcc808180c37dc7b",
+    "gpu__dram_throughput_pct": 51.3,
+    "captured": "2026-12-04, ncu --set full --clock-control none, one launch after two "
+                "(profiles/fused_step2_cavity2048_fp32.md)",
 }
 
 
@@ -143,6 +144,8 @@ def parse():
     ap.add_argument("--lb-steps", type=int, default=20000,
                     help="LB time steps per benchmark step (a tenth of the 200k-step solve)")
     ap.add_argument("--roofline-n", type=int, default=2048)
+    ap.add_argument("--step-form", default="auto", choices=["auto", "single", "pairs", "two"],
+                    help="step form of the headline run (lbm_set_step_form; auto: the library's choice)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--batch-runs", type=int, default=64)
@@ -501,7 +504,8 @@ def main():
     prec = {"f64": 0, "f32": 1, "f16": 2, "bf16": 3}[args.precision]
     p = inputs.cavity(args.n, precision=prec)
     cells = p["nx"] * p["ny"]
-    form = lbm.step_form_for(p, 0)
+    want_form = {"auto": 0, "single": 1, "pairs": 2, "two": 3}[args.step_form]
+    form = lbm.step_form_for(p, want_form)
     bpu = bytes_per_update(p["thermal_q"], p["flow"], p["precision"])
     props = torch.cuda.get_device_properties(dev)
     bus = getattr(props, "pci_bus_id", None)
@@ -510,7 +514,7 @@ def main():
         bus_id = f"{getattr(props, 'pci_domain_id', 0):08X}:{bus:02X}:{getattr(props, 'pci_device_id', 0):02X}.0"
 
     with torch.cuda.stream(stream):
-        s = lbm.Solver(p, stream=stream)
+        s = lbm.Solver(p, stream=stream).set_step_form(want_form)
         flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
         for _ in range(args.warmup):
             s.step(chunk)
@@ -658,12 +662,15 @@ def main():
                     ms = time_form(fprec, n, per)
                     b = bytes_per_update(5, 1, fprec)
                     gbs = b * n * n / (ms / 1e3) / 1e9
-                    forms.append({"precision": PREC_NAMES[fprec], "grid": n,
-                                  "step_form": FORM_NAMES[lbm.step_form_for(inputs.cavity(n, precision=fprec), 0)],
+                    ff = lbm.step_form_for(inputs.cavity(n, precision=fprec), 0)
+                    # two steps per launch: the state crosses HBM once per two updates
+                    crossing = b / 2 if ff == 3 else b
+                    forms.append({"precision": PREC_NAMES[fprec], "grid": n, "step_form": FORM_NAMES[ff],
                                   "us_per_step": ms * 1e3,
                                   "mlups": n * n / (ms / 1e3) / 1e6, "bytes_per_update": b,
                                   "overhead_bytes_per_update": stored_bytes_per_update(5, 1, fprec) - b,
-                                  "gbs_algorithmic": gbs, "frac_of_measured_hbm": gbs / peak})
+                                  "gbs_algorithmic": gbs, "hbm_bytes_per_update_crossing": crossing,
+                                  "frac_of_measured_hbm": crossing * n * n / (ms / 1e3) / 1e9 / peak})
 
     if rank != 0:
         return

@@ -165,11 +165,15 @@ void lbm_params_default(lbm_params* p);
 int lbm_derive(const lbm_params* p, lbm_derived* d);
 
 /* Device bytes a run will hold (two copies of the distributions, the exchange
- * history and small scratch).  A run that lbm_step advances two steps per
- * launch (lbm_set_step_form) adds a second exchange-history array, 4 bytes
- * per node of row pitch, at its first such lbm_step; batches and the server
- * never allocate it.  -1 if p is invalid. */
+ * history and small scratch).  A run that advances two steps per launch
+ * (lbm_step in the two-step form, or a batch under map 5) adds a second
+ * exchange-history array of lbm_history_bytes(p) at its first such step.  -1
+ * if p is invalid. */
 int64_t lbm_state_bytes(const lbm_params* p);
+
+/* Device bytes of one exchange-history array of a run with parameters p (4
+ * bytes per node of row pitch; 8 in FP64).  -1 if p is invalid. */
+int64_t lbm_history_bytes(const lbm_params* p);
 
 /* Creates a run, allocates its device state (through alloc/release when
  * given, else the CUDA stream-ordered allocator) and enqueues the uniform
@@ -309,21 +313,28 @@ const char* lbm_strerror(int code);
  * nodes (w = 32, 64 or 128, whichever leaves the fewest of the run's threads
  * idle); each group of runs is a chain of its own in the graph, and larger
  * runs keep their own step kernel in chains of their own, as under map 3.
- * With
- * autotune = 1 the call times, on freshly created copies of the runs (the
+ * Map 5 (runs with flow in FP32/FP16/BF16 storage) advances every run two
+ * steps per launch in grouped launches of the two-step kernel (blocks of 34
+ * x 12 threads, inner tiles of 32 x 10 nodes; see lbm_set_step_form), 32
+ * launches per 64 steps, each run keeping a second exchange-history array
+ * (allocated on its allocator when map 5 is chosen; LBM_ERR_OOM if that
+ * fails); steps that align the batch to an even parity, and an odd
+ * remainder, take each run's one-step kernel (one node per thread).
+ * With autotune = 1 the call times, on freshly created copies of the runs (the
  * runs themselves do not move, but the copies hold as much device memory
  * again while tuning), map 3 with the block shape chosen per size class
  * (grid width <= 64, <= 128, <= 256, wider; one class at a time, keeping the
- * fastest shape), map 4, and every combination of tile-width cap (64, 128,
- * 256) and map 0-2, and keeps the fastest; otherwise it takes width cap 128,
+ * fastest shape), map 4, map 5 where it applies, and every combination of
+ * tile-width cap (64, 128, 256) and map 0-2, and keeps the fastest; otherwise it takes width cap 128,
  * map 0, and for map 3 lbm_step's own block shapes (64 x 2 up to 40,000
  * nodes, 128 x 1 above).  Under map 3 a batched step equals lbm_step on each
- * run bit for bit.  Maps 0-2 and 4 inline the same per-node code into
+ * run bit for bit.  Maps 0-2, 4 and 5 inline the same per-node code into
  * another kernel, where the compiler may fuse a few multiply-adds
  * differently: their states can differ from lbm_step's by a few roundings of
  * the arithmetic (FP32: 1-3 ulps in about 1e-4 of the flow populations per
  * step), which a 16-bit store sometimes carries into the last stored bit.  A
- * run's steps under map 4 do not depend on the other runs of its launch.
+ * run's steps under maps 4 and 5 do not depend on the other runs of its
+ * launch.
  *
  * lbm_batch_step enqueues nsteps steps of every run on the batch's stream
  * and advances each run's step count.  Use the runs' own calls (fields,
@@ -335,7 +346,7 @@ const char* lbm_strerror(int code);
  * and drops its replayed graph, then advances every run from its current
  * state.  A run whose sticky status is set stops the batch
  * (LBM_ERR_STATE).  lbm_batch_info reports the tile count, the chosen width
- * cap and map (0-4), the grid size (0 for maps 3 and 4) and the tuned
+ * cap and map (0-5), the grid size (0 for maps 3-5) and the tuned
  * microseconds per step.
  * lbm_batch_destroy synchronises and frees the batch (not its runs).
  * The batch allocates its work list and parameter blocks through the first
@@ -345,7 +356,9 @@ typedef struct lbm_batch lbm_batch;
 int lbm_batch_create(lbm_handle* const* runs, int32_t n_runs, int32_t autotune, void* cuda_stream,
                      lbm_batch** out);
 int lbm_batch_step(lbm_batch* b, int64_t nsteps);
-/* Forces a tile-width cap (32, 64, 128 or 256) and a map (0-4); synchronises. */
+/* Forces a tile-width cap (32, 64, 128 or 256) and a map (0-5; 5 only for
+ * runs with flow in FP32/FP16/BF16 storage, LBM_ERR_ARG otherwise);
+ * synchronises. */
 int lbm_batch_configure(lbm_batch* b, int32_t width_cap, int32_t mapping);
 int lbm_batch_info(const lbm_batch* b, int32_t* n_tiles, int32_t* width_cap, int32_t* mapping, int32_t* grid,
                    double* tuned_us_per_step);
@@ -363,7 +376,8 @@ int lbm_batch_destroy(lbm_batch* b);
  * lbm_server_submit.  Every lbm_server_tick
  *   1. admits queued requests in arrival order while fewer than max_active
  *      runs are active and the device bytes of the active runs
- *      (lbm_state_bytes) plus the next request's stay within hbm_budget_bytes;
+ *      (lbm_state_bytes, plus lbm_history_bytes under map 5) plus the next
+ *      request's stay within hbm_budget_bytes;
  *   2. advances all active runs together by min(quantum, the smallest number
  *      of steps any active run still needs) through one lbm_batch (batched =
  *      1; the batch is rebuilt when membership changes, with the tile width
@@ -380,8 +394,11 @@ int lbm_batch_destroy(lbm_batch* b);
  * lbm_step's.
  *
  * All requests of a server share precision, thermal_q and flow (LBM_ERR_ARG
- * otherwise); a request whose state alone exceeds the budget is refused at
- * submission.  Times in the results are seconds since lbm_server_create on
+ * otherwise); a request that the budget can never hold (its state, plus
+ * its second history array under map 5) is refused at submission, or, if
+ * the map changed after it was queued, at admission with status
+ * LBM_ERR_ARG in its result.  lbm_server_configure takes maps 0-5 (5 only
+ * for servers of runs with flow in FP32/FP16/BF16 storage).  Times in the results are seconds since lbm_server_create on
  * the host clock: submission, admission, completion.  lbm_server_results
  * moves up to max_results finished records into out.  lbm_server_stats
  * reports node updates performed, seconds the device was busy with ticks,

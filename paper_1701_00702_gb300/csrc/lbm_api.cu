@@ -13,6 +13,13 @@
 #include "lbm.h"
 #include "lbm_launch.cuh"
 
+namespace lbmk {
+LBMK_EXTERN(MODE_F64)
+LBMK_EXTERN(MODE_F32)
+LBMK_EXTERN(MODE_F16)
+LBMK_EXTERN(MODE_BF16)
+}  // namespace lbmk
+
 static_assert(LBM_STEP_FORM_AUTO == lbmk::FORM_AUTO && LBM_STEP_FORM_SINGLE == lbmk::FORM_SINGLE &&
                   LBM_STEP_FORM_PAIRS == lbmk::FORM_PAIRS && LBM_STEP_FORM_TWO_STEPS == lbmk::FORM_TWO_STEPS,
               "step form values");
@@ -350,8 +357,9 @@ int cuda_fail(lbm_handle* h) {
     return LBM_ERR_CUDA;
 }
 
-cudaError_t enqueue_one(lbm_handle* h, int from, cudaStream_t s) {
-    const int q = h->p.thermal_q, fl = h->p.flow, fm = h->form;
+// One step of run h from copy `from` with its step form (form < 0) or the given one.
+cudaError_t enqueue_one(lbm_handle* h, int from, cudaStream_t s, int form = -1) {
+    const int q = h->p.thermal_q, fl = h->p.flow, fm = form < 0 ? h->form : form;
     switch (h->p.precision) {
         case LBM_F64: return lbmk::launch_step<lbmk::MODE_F64>(make_params<double>(h, from), q, fl, fm, s);
         case LBM_F32: return lbmk::launch_step<lbmk::MODE_F32>(make_params<float>(h, from), q, fl, fm, s);
@@ -524,6 +532,11 @@ int lbm_derive(const lbm_params* p, lbm_derived* d) { return derive_impl(p, d); 
 int64_t lbm_state_bytes(const lbm_params* p) {
     if (derive_impl(p, nullptr) != LBM_OK) return -1;
     return (int64_t)layout_of(*p).total;
+}
+
+int64_t lbm_history_bytes(const lbm_params* p) {
+    if (derive_impl(p, nullptr) != LBM_OK) return -1;
+    return (int64_t)layout_of(*p).dT_bytes;
 }
 
 int lbm_create_ex(const lbm_params* p, void* cuda_stream, lbm_alloc_fn alloc, lbm_free_fn release, void* ctx,
@@ -1068,6 +1081,8 @@ int batch_blocks_per_sm(const lbm_batch* b) {
 // one graph.
 // Map 4: the runs below kGroupMaxNodes nodes in order, at most kGroupRuns per
 // grouped launch; the larger runs keep their own step kernel.
+// Map 4: the runs below kGroupMaxNodes in groups of at most kGroupRuns, the
+// others solo.  Map 5: every run in groups (its kernel takes any size).
 void make_groups(lbm_batch* b) {
     b->groups.clear();
     b->solo.clear();
@@ -1075,7 +1090,7 @@ void make_groups(lbm_batch* b) {
     std::vector<int> small;
     for (int r = 0; r < (int)b->runs.size(); ++r) {
         const lbm_params& p = b->runs[r]->p;
-        if ((long long)p.nx * p.ny < lbmk::kGroupMaxNodes) small.push_back(r);
+        if (b->mapping == 5 || (long long)p.nx * p.ny < lbmk::kGroupMaxNodes) small.push_back(r);
         else b->solo.push_back(r);
     }
     for (size_t i = 0; i < small.size(); i += cap)
@@ -1084,7 +1099,7 @@ void make_groups(lbm_batch* b) {
 
 void set_mapping(lbm_batch* b, int mapping, int resident_blocks) {
     b->mapping = mapping;
-    if (mapping == 4) make_groups(b);
+    if (mapping == 4 || mapping == 5) make_groups(b);
     if (mapping >= 3) {
         b->grid = 0;
         b->chunk = 0;
@@ -1189,20 +1204,28 @@ int build_chain_graph(lbm_batch* b, int steps, cudaGraphExec_t* out) {
     return instantiate(g, add_run_chains(b, g, all, steps), out);
 }
 
-// Map 4: the parameters of one grouped launch -- its runs' parameter blocks
-// for a step from batch parity `parity`, their tiles, and the prefix sums of
-// their block counts.  Returns the launch's block count.
+// Maps 4 and 5: the parameters of one grouped launch -- its runs' parameter
+// blocks for a step from batch parity `parity`, their tiles, and the prefix
+// sums of their block counts.  two: a launch of the two-step kernel, whose
+// history goes from h->dT to h->dT2 (back = 0) or back (back = 1).  Returns the
+// launch's block count.
 template <typename R>
-long long fill_group(const lbm_batch* b, const std::vector<int>& g, int parity, lbmk::GroupParams<R>& G) {
+long long fill_group(const lbm_batch* b, const std::vector<int>& g, int parity, lbmk::GroupParams<R>& G,
+                     bool two, bool back) {
     std::memset(&G, 0, sizeof G);
     G.nruns = (int)g.size();
     long long acc = 0;
     for (size_t i = 0; i < g.size(); ++i) {
         lbm_handle* h = b->runs[g[i]];
         G.first_block[i] = (int)acc;
-        G.tile[i] = lbmk::group_tile(h->p.nx);
         G.run[i] = make_params<R>(h, b->flip[g[i]] ^ parity);
-        acc += lbmk::group_blocks(h->p.nx, h->p.ny, G.tile[i]);
+        if (two) {
+            if (back) std::swap(G.run[i].dT, G.run[i].dT_out);
+            acc += lbmk::group2_blocks(h->p.nx, h->p.ny);
+        } else {
+            G.tile[i] = lbmk::group_tile(h->p.nx);
+            acc += lbmk::group_blocks(h->p.nx, h->p.ny, G.tile[i]);
+        }
     }
     G.first_block[g.size()] = (int)acc;
     return acc;
@@ -1218,47 +1241,101 @@ const void* group_fn(const lbm_batch* b) {
     }
 }
 
+// Map 5 applies to runs with flow in FP32/FP16/BF16 storage (the two-step kernel's).
+bool two_step_batch(const lbm_batch* b) { return b->precision != LBM_F64 && b->flow; }
+
+// The second history array of every run (map 5).
+int ensure_batch_dT2(lbm_batch* b) {
+    for (lbm_handle* h : b->runs) {
+        const int rc = ensure_dT2(h);
+        if (rc != LBM_OK) return rc;
+    }
+    return LBM_OK;
+}
+
+const void* group2_fn(const lbm_batch* b) {
+    const int ph = batch_phase(b);
+    switch (b->precision) {
+        case LBM_F32: return lbmk::group2_kernel<lbmk::MODE_F32>(b->qt, ph);
+        case LBM_F16: return lbmk::group2_kernel<lbmk::MODE_F16>(b->qt, ph);
+        case LBM_BF16: return lbmk::group2_kernel<lbmk::MODE_BF16>(b->qt, ph);
+        default: return nullptr;
+    }
+}
+
+size_t group2_smem(const lbm_batch* b) {
+    switch (b->precision) {
+        case LBM_F32: return lbmk::step2_smem<lbmk::MODE_F32>(b->qt, lbmk::kT2HMany);
+        case LBM_F16: return lbmk::step2_smem<lbmk::MODE_F16>(b->qt, lbmk::kT2HMany);
+        case LBM_BF16: return lbmk::step2_smem<lbmk::MODE_BF16>(b->qt, lbmk::kT2HMany);
+        default: return 0;
+    }
+}
+
 // The launch configuration and the parameters of one grouped launch.
 struct GroupArgs {
     std::unique_ptr<lbmk::GroupParams<double>> d;
     std::unique_ptr<lbmk::GroupParams<float>> f;
     void* args[1];
     dim3 grid, block;
-    const void* fn;
+    size_t smem = 0;
+    const void* fn = nullptr;
 };
 
-void group_args(const lbm_batch* b, const std::vector<int>& g, int parity, GroupArgs& a) {
+cudaError_t group_args(const lbm_batch* b, const std::vector<int>& g, int parity, GroupArgs& a, bool two = false,
+                       bool back = false) {
     long long blocks;
     if (b->precision == LBM_F64) {
         if (!a.d) a.d = std::make_unique<lbmk::GroupParams<double>>();
-        blocks = fill_group<double>(b, g, parity, *a.d);
+        blocks = fill_group<double>(b, g, parity, *a.d, false, false);
         a.args[0] = a.d.get();
     } else {
         if (!a.f) a.f = std::make_unique<lbmk::GroupParams<float>>();
-        blocks = fill_group<float>(b, g, parity, *a.f);
+        blocks = fill_group<float>(b, g, parity, *a.f, two, back);
         a.args[0] = a.f.get();
     }
     a.grid = dim3((unsigned)blocks, 1u, 1u);
-    a.block = dim3(128, 1, 1);
-    a.fn = group_fn(b);
+    if (!two) {
+        a.block = dim3(128, 1, 1);
+        a.smem = 0;
+        a.fn = group_fn(b);
+        return cudaSuccess;
+    }
+    a.block = dim3((unsigned)lbmk::kT2W, (unsigned)lbmk::kT2HMany, 1u);
+    a.smem = group2_smem(b);
+    a.fn = group2_fn(b);
+    if (!a.fn) return cudaErrorInvalidConfiguration;
+    return cudaFuncSetAttribute(a.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)a.smem);
 }
 
-// One batched step under map 4: each group's launch and each large run's own
-// step, as programmatic dependents of the previous launch in the stream.
-cudaError_t group_step_all(lbm_batch* b, int parity, cudaStream_t s) {
+// One batched step under map 4 (each group's launch and each large run's
+// own step) or two steps under map 5 (two = true: each group's two-step
+// launch), as programmatic dependents of the previous launch in the stream.
+// Single steps under map 5 take each run's one-step kernel (one node per
+// thread), which rounds exactly as the two-step kernel does.
+cudaError_t group_step_all(lbm_batch* b, int parity, cudaStream_t s, bool two = false, bool back = false) {
+    if (b->mapping == 5 && !two) {
+        for (size_t r = 0; r < b->runs.size(); ++r) {
+            const cudaError_t e = enqueue_one(b->runs[r], b->flip[r] ^ parity, s, lbmk::FORM_SINGLE);
+            if (e != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    }
     GroupArgs a;
     for (const std::vector<int>& g : b->groups) {
-        group_args(b, g, parity, a);
+        cudaError_t e = group_args(b, g, parity, a, two, back);
+        if (e != cudaSuccess) return e;
         cudaLaunchAttribute attr[1];
         attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
         attr[0].val.programmaticStreamSerializationAllowed = 1;
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = a.grid;
         cfg.blockDim = a.block;
+        cfg.dynamicSmemBytes = a.smem;
         cfg.stream = s;
         cfg.attrs = attr;
         cfg.numAttrs = 1;
-        const cudaError_t e = cudaLaunchKernelExC(&cfg, a.fn, a.args);
+        e = cudaLaunchKernelExC(&cfg, a.fn, a.args);
         if (e != cudaSuccess) return e;
     }
     for (int r : b->solo) {
@@ -1270,21 +1347,25 @@ cudaError_t group_step_all(lbm_batch* b, int parity, cudaStream_t s) {
 
 // Map 4: a graph of `steps` steps with one chain of grouped launches per group
 // and one chain of step kernels per large run (programmatic edges within a
-// chain; the chains are independent).
+// chain; the chains are independent).  Map 5: steps / 2 two-step launches per
+// group (steps even: copies and histories end where they started).
 int build_group_graph(lbm_batch* b, int steps, cudaGraphExec_t* out) {
     cudaGraph_t g = nullptr;
     if (cudaGraphCreate(&g, 0) != cudaSuccess) return LBM_ERR_CUDA;
     cudaError_t e = cudaSuccess;
     GroupArgs a;
+    const bool two = b->mapping == 5;
+    const int launches = two ? steps / 2 : steps;
     for (size_t gi = 0; gi < b->groups.size() && e == cudaSuccess; ++gi) {
         cudaGraphNode_t prev = nullptr;
-        for (int k = 0; k < steps && e == cudaSuccess; ++k) {
-            group_args(b, b->groups[gi], k & 1, a);
+        for (int k = 0; k < launches && e == cudaSuccess; ++k) {
+            e = group_args(b, b->groups[gi], k & 1, a, two, (k & 1) != 0);
+            if (e != cudaSuccess) break;
             cudaKernelNodeParams kp = {};
             kp.func = const_cast<void*>(a.fn);
             kp.gridDim = a.grid;
             kp.blockDim = a.block;
-            kp.sharedMemBytes = 0;
+            kp.sharedMemBytes = (unsigned)a.smem;
             kp.kernelParams = a.args;
             kp.extra = nullptr;
             cudaGraphNode_t node = nullptr;
@@ -1305,7 +1386,7 @@ int build_group_graph(lbm_batch* b, int steps, cudaGraphExec_t* out) {
 
 int build_batch_graph(lbm_batch* b) {
     if (b->graph) return LBM_OK;
-    if (b->mapping == 4) return build_group_graph(b, kGraphSteps, &b->graph);
+    if (b->mapping == 4 || b->mapping == 5) return build_group_graph(b, kGraphSteps, &b->graph);
     if (b->mapping == 3) return build_chain_graph(b, kGraphSteps, &b->graph);
     if (!b->cap && cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess) return LBM_ERR_CUDA;
     if (cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return LBM_ERR_CUDA;
@@ -1354,7 +1435,7 @@ int resync_runs(lbm_batch* b) {
 int batch_advance(lbm_batch* b, int64_t n) {
     auto single = [&]() -> int {
         cudaError_t e = cudaSuccess;
-        if (b->mapping == 4) {
+        if (b->mapping == 4 || b->mapping == 5) {
             e = group_step_all(b, b->parity, b->stream);
         } else if (b->mapping == 3) {
             for (size_t r = 0; r < b->runs.size() && e == cudaSuccess; ++r)
@@ -1384,6 +1465,14 @@ int batch_advance(lbm_batch* b, int64_t n) {
             left -= kGraphSteps;
         }
     }
+    while (b->mapping == 5 && left >= 4) {   // two two-step launches: copies and histories back in place
+        if (group_step_all(b, b->parity, b->stream, true, false) != cudaSuccess ||
+            group_step_all(b, b->parity ^ 1, b->stream, true, true) != cudaSuccess) {
+            cudaGetLastError();
+            return LBM_ERR_CUDA;
+        }
+        left -= 4;
+    }
     while (left > 0) {
         if (single() != LBM_OK) return LBM_ERR_CUDA;
         --left;
@@ -1400,7 +1489,7 @@ double time_batch(lbm_batch* b, int steps) {
     }
     cudaGraphExec_t g = nullptr;
     if ((b->mapping == 3 && build_chain_graph(b, steps, &g) != LBM_OK) ||
-        (b->mapping == 4 && build_group_graph(b, steps, &g) != LBM_OK)) {
+        ((b->mapping == 4 || b->mapping == 5) && build_group_graph(b, steps, &g) != LBM_OK)) {
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
         return 1e30;
@@ -1539,6 +1628,15 @@ int lbm_batch_create(lbm_handle* const* runs, int32_t n_runs, int32_t autotune, 
                     best_cap = 128;
                     best_map = 4;
                 }
+                if (two_step_batch(b) && ensure_batch_dT2(b) == LBM_OK) {
+                    set_mapping(b, 5, resident);
+                    const double t5 = time_batch(b, 16);
+                    if (t5 < best) {
+                        best = t5;
+                        best_cap = 128;
+                        best_map = 5;
+                    }
+                }
             }
             for (int cap : {64, 128, 256}) {
                 if (upload_batch(b, make_tiles(b->runs, b->flip, cap)) != LBM_OK) continue;
@@ -1564,6 +1662,7 @@ int lbm_batch_create(lbm_handle* const* runs, int32_t n_runs, int32_t autotune, 
         free_batch(b);
         return LBM_ERR_CUDA;
     }
+    if (best_map == 5 && ensure_batch_dT2(b) != LBM_OK) best_map = 4;   // no room for the second histories
     set_mapping(b, best_map, resident);
     *out = b;
     return LBM_OK;
@@ -1586,11 +1685,15 @@ int lbm_batch_step(lbm_batch* b, int64_t nsteps) {
 
 int lbm_batch_configure(lbm_batch* b, int32_t width_cap, int32_t mapping) {
     if (!b || (width_cap != 32 && width_cap != 64 && width_cap != 128 && width_cap != 256) || mapping < 0 ||
-        mapping > 4)
+        mapping > 5 || (mapping == 5 && !two_step_batch(b)))
         return LBM_ERR_ARG;
     if (cudaStreamSynchronize(b->stream) != cudaSuccess) {
         cudaGetLastError();
         return LBM_ERR_CUDA;
+    }
+    if (mapping == 5) {
+        const int rc = ensure_batch_dT2(b);
+        if (rc != LBM_OK) return rc;
     }
     batch_destroy_graph(b);
     const int rc = upload_batch(b, make_tiles(b->runs, b->flip, width_cap));

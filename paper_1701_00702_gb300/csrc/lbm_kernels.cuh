@@ -1171,8 +1171,14 @@ __host__ __device__ __forceinline__ int t2_origin(int k, int w, int n) {
     return (n > w ? min(k * w, n - w) : 0) - 1;
 }
 
+// Tiles along an axis of n nodes with inner width w.
+__host__ __device__ __forceinline__ int t2_count(int n, int w) { return n > w ? (n + w - 1) / w : 1; }
+
+// Both steps of tile (bx, by) of run P, by a block of kT2W x blockDim.y
+// threads (blockDim.y <= HM) with Tile2<M, QT, HM>::bytes of dynamic shared
+// memory.
 template <int M, int QT, bool PH, int HM>
-__global__ void __launch_bounds__(kT2W * HM, (kT2Blocks<HM, M, QT>)) fused_step2(const __grid_constant__ StepParams<typename ModeTraits<M>::R> P) {
+__device__ __forceinline__ void step2_tile(const StepParams<typename ModeTraits<M>::R>& P, int bx, int by) {
     using R = typename ModeTraits<M>::R;
     using B = typename ModeTraits<M>::B;
     using TL = Tile2<M, QT, HM>;
@@ -1182,7 +1188,7 @@ __global__ void __launch_bounds__(kT2W * HM, (kT2Blocks<HM, M, QT>)) fused_step2
     R* sdT = reinterpret_cast<R*>(t2_smem + TL::dT_off);
     const int H = blockDim.y;   // blockDim.x == kT2W, H <= HM
     const int lx = threadIdx.x, ly = threadIdx.y, i = ly * kT2W + lx;
-    const int X0 = t2_origin(blockIdx.x, kT2W - 2, P.nx), Y0 = t2_origin(blockIdx.y, H - 2, P.ny);
+    const int X0 = t2_origin(bx, kT2W - 2, P.nx), Y0 = t2_origin(by, H - 2, P.ny);
     // step-1 node: coordinates wrapped on periodic sides, none beyond a walled side
     int x = X0 + lx, y = Y0 + ly;
     bool live = true;
@@ -1220,6 +1226,11 @@ __global__ void __launch_bounds__(kT2W * HM, (kT2Blocks<HM, M, QT>)) fused_step2
     const bool bad = !(fabs(n.H) + fabs(n.Tm) + n.rho < R(1e30)) || !(n.rho > R(0)) ||
                      !(n.ux * n.ux + n.uy * n.uy <= R(0.09));
     if (bad) atomicOr(P.status, STATUS_UNSTABLE);
+}
+
+template <int M, int QT, bool PH, int HM>
+__global__ void __launch_bounds__(kT2W * HM, (kT2Blocks<HM, M, QT>)) fused_step2(const __grid_constant__ StepParams<typename ModeTraits<M>::R> P) {
+    step2_tile<M, QT, PH, HM>(P, blockIdx.x, blockIdx.y);
 }
 
 // ---------------------------------------------------------------------------
@@ -1706,6 +1717,28 @@ __global__ void __launch_bounds__(128, 2 * kMinBlocks<M, QT, FLOW>) group_step(
     if (x >= P.nx || y >= P.ny) return;
     griddep_wait();
     step_node<M, QT, FLOW, PH>(P, x, y);
+}
+
+// Batch map 5: the grouped launch of the two-step form.  Run k owns blocks
+// first_block[k] .. first_block[k + 1] - 1, one per two-step tile (blocks of
+// kT2W x kT2HMany threads, inner tiles of (kT2W - 2) x (kT2HMany - 2) nodes,
+// row-major over the run's tiles); each block advances its tile two steps as
+// fused_step2 does, with its run's parameter block.
+template <int M, int QT, bool PH>
+__global__ void __launch_bounds__(kT2W * kT2HMany, (kT2Blocks<kT2HMany, M, QT>)) group_step2(
+    const __grid_constant__ GroupParams<typename ModeTraits<M>::R> G) {
+    using R = typename ModeTraits<M>::R;
+    const int b = blockIdx.x;
+    int lo = 0, hi = G.nruns - 1;   // the last run whose first block is <= b
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (G.first_block[mid] <= b) lo = mid;
+        else hi = mid - 1;
+    }
+    const StepParams<R>& P = G.run[lo];
+    const int lb = b - G.first_block[lo];
+    const int gx = t2_count(P.nx, kT2W - 2);
+    step2_tile<M, QT, PH, kT2HMany>(P, lb % gx, lb / gx);
 }
 
 // Many runs in one launch.  A tile is w x (256 / w) nodes of one run (w a

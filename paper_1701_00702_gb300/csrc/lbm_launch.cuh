@@ -304,7 +304,7 @@ cudaError_t launch_step(const StepParams<typename ModeTraits<M>::R>& P, int qt, 
 // grids take H = kT2HMany = 12, measured fastest there (FP32: three resident
 // blocks of 13 warps per SM; 1024^2 and 2048^2 against H = 6, 8, 10, 14, 16).
 
-inline long long t2_tiles(int n, int inner) { return n > inner ? (n + inner - 1) / inner : 1; }
+inline long long t2_tiles(int n, int inner) { return t2_count(n, inner); }
 
 inline dim3 t2_grid(int nx, int ny, int h) {
     return dim3((unsigned)t2_tiles(nx, kT2W - 2), (unsigned)t2_tiles(ny, h - 2), 1u);
@@ -352,6 +352,19 @@ size_t step2_smem(int qt, int h) {
     }
     return 0;
 }
+
+// Batch map 5: the grouped two-step kernel and its shared memory (the 12-row
+// build; blocks of kT2W x kT2HMany threads).
+template <int M>
+const void* group2_kernel(int qt, int phase_k) {
+    if constexpr (M != MODE_F64) {
+        if (qt == 5) return phase_k ? (const void*)group_step2<M, 5, true> : (const void*)group_step2<M, 5, false>;
+        return phase_k ? (const void*)group_step2<M, 9, true> : (const void*)group_step2<M, 9, false>;
+    }
+    return nullptr;
+}
+
+inline long long group2_blocks(int nx, int ny) { return t2_tiles(nx, kT2W - 2) * t2_tiles(ny, kT2HMany - 2); }
 
 template <int M>
 cudaError_t launch_step2(const StepParams<typename ModeTraits<M>::R>& P, int qt, int h, cudaStream_t s) {
@@ -439,22 +452,32 @@ int batch_blocks_per_sm(int qt, int flow, int ph) {
     return n;
 }
 
-#define LBMK_INSTANTIATE(M)                                                                                   \
-    template cudaError_t launch_step<M>(const StepParams<ModeTraits<M>::R>&, int, int, int, cudaStream_t);   \
-    template cudaError_t launch_fields<M>(const StepParams<ModeTraits<M>::R>&, const FieldOut<ModeTraits<M>::R>&, \
+// Explicit instantiations of the launchers (KW empty: in the kernel units) and
+// the matching declarations (KW = extern: in the units that call them, so
+// that the kernels are compiled once, in their own units).
+#define LBMK_TEMPLATES(KW, M)                                                                                 \
+    KW template cudaError_t launch_step<M>(const StepParams<ModeTraits<M>::R>&, int, int, int, cudaStream_t);   \
+    KW template cudaError_t launch_fields<M>(const StepParams<ModeTraits<M>::R>&, const FieldOut<ModeTraits<M>::R>&, \
                                           int, int, cudaStream_t);                                            \
-    template cudaError_t launch_diag<M>(const StepParams<ModeTraits<M>::R>&, const DiagConst&, double*, double*, \
+    KW template cudaError_t launch_diag<M>(const StepParams<ModeTraits<M>::R>&, const DiagConst&, double*, double*, \
                                         int, int, cudaStream_t);                                              \
-    template cudaError_t launch_init<M>(const StepParams<ModeTraits<M>::R>&, const InitVals&, int, int, cudaStream_t); \
-    template cudaError_t launch_batch<M>(const StepParams<ModeTraits<M>::R>*, const Tile*, int, int, int, int, int, \
+    KW template cudaError_t launch_init<M>(const StepParams<ModeTraits<M>::R>&, const InitVals&, int, int, cudaStream_t); \
+    KW template cudaError_t launch_batch<M>(const StepParams<ModeTraits<M>::R>*, const Tile*, int, int, int, int, int, \
                                          int, int, cudaStream_t);                                               \
-    template int batch_blocks_per_sm<M>(int, int, int);                                                   \
-    template const void* group_kernel<M>(int, int, int);                                                    \
-    template cudaError_t launch_step2<M>(const StepParams<ModeTraits<M>::R>&, int, int, cudaStream_t);     \
-    template StepLaunch step_launch<M>(const StepParams<ModeTraits<M>::R>&, int, int, int, dim3);
+    KW template int batch_blocks_per_sm<M>(int, int, int);                                                   \
+    KW template const void* group_kernel<M>(int, int, int);                                                    \
+    KW template cudaError_t launch_step2<M>(const StepParams<ModeTraits<M>::R>&, int, int, cudaStream_t);     \
+    KW template const void* group2_kernel<M>(int, int);                                                        \
+    KW template size_t step2_smem<M>(int, int);                                                                \
+    KW template StepLaunch step_launch<M>(const StepParams<ModeTraits<M>::R>&, int, int, int, dim3);
 
-#define LBMK_INSTANTIATE_CONVERT(M)                                                                           \
-    template cudaError_t launch_convert<M>(const StepParams<ModeTraits<M>::R>&, const DenseState<ModeTraits<M>::R>&, \
+#define LBMK_CONVERT_TEMPLATES(KW, M)                                                                         \
+    KW template cudaError_t launch_convert<M>(const StepParams<ModeTraits<M>::R>&, const DenseState<ModeTraits<M>::R>&, \
                                            int, int, int, cudaStream_t);
+
+
+#define LBMK_INSTANTIATE(M) LBMK_TEMPLATES(, M)
+#define LBMK_INSTANTIATE_CONVERT(M) LBMK_CONVERT_TEMPLATES(, M)
+#define LBMK_EXTERN(M) LBMK_TEMPLATES(extern, M) LBMK_CONVERT_TEMPLATES(extern, M)
 
 }  // namespace lbmk

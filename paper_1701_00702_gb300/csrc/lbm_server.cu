@@ -35,6 +35,7 @@ struct Request {
     int64_t id = 0;
     lbm_params p{};
     int64_t steps = 0, remaining = 0, bytes = 0, nodes = 0;
+    int64_t history_bytes = 0;   // the second exchange history of batch map 5
     double submit_s = 0.0, admit_s = 0.0;
     lbm_handle* h = nullptr;
 };
@@ -98,15 +99,31 @@ void finish(lbm_server* s, Request& r, int status) {
     s->done.push_back(out);
 }
 
-// Admission in arrival order, while a slot and the budget allow.
+// Device bytes an active request holds: its state, and under batch map 5 the
+// second exchange history that the two-step launches use.
+int64_t charge(const lbm_server* s, const Request& r) {
+    return r.bytes + (s->batched && s->mapping == 5 ? r.history_bytes : 0);
+}
+
+// Admission in arrival order, while a slot and the budget allow.  A request
+// that the budget can never hold under the map in force (its second history
+// counts only under map 5) is refused here.
 void admit(lbm_server* s) {
     const Range range("admit");
+    while (!s->queue.empty() && charge(s, s->queue.front()) > s->budget) {
+        Request r = s->queue.front();
+        s->queue.pop_front();
+        r.admit_s = since(s);
+        r.bytes = 0;
+        finish(s, r, LBM_ERR_ARG);
+    }
     while (!s->queue.empty() && (int)s->active.size() < s->max_active &&
-           s->used + s->queue.front().bytes <= s->budget) {
+           s->used + charge(s, s->queue.front()) <= s->budget) {
         Request r = s->queue.front();
         const int rc = lbm_create_ex(&r.p, s->stream, s->alloc, s->release, s->ctx, &r.h);
         if (rc == LBM_ERR_OOM && !s->active.empty()) break;   // wait for memory to come back
         s->queue.pop_front();
+        r.bytes = charge(s, r);   // what this run holds while active
         r.admit_s = since(s);
         s->used += r.bytes;
         s->peak_used = std::max(s->peak_used, s->used);
@@ -153,7 +170,7 @@ int lbm_server_create(int64_t hbm_budget_bytes, int32_t max_active, int32_t batc
 
 int lbm_server_configure(lbm_server* s, int32_t width_cap, int32_t mapping) {
     if (!s || (width_cap != 32 && width_cap != 64 && width_cap != 128 && width_cap != 256) || mapping < 0 ||
-        mapping > 4)
+        mapping > 5 || (mapping == 5 && (s->precision == LBM_F64 || !s->flow)))
         return LBM_ERR_ARG;
     s->width_cap = width_cap;
     s->mapping = mapping;
@@ -169,12 +186,14 @@ int lbm_server_submit(lbm_server* s, const lbm_params* p, int64_t nsteps, int64_
         lbm_derived d;
         return lbm_derive(p, &d);   // the reason: malformed or unstable parameters
     }
-    if (bytes > s->budget) return LBM_ERR_ARG;   // could never be admitted
+    const int64_t history = lbm_history_bytes(p);
     Request r;
     r.id = s->next_id++;
     r.p = *p;
     r.steps = r.remaining = nsteps;
     r.bytes = bytes;
+    r.history_bytes = history;
+    if (charge(s, r) > s->budget) return LBM_ERR_ARG;   // could never be admitted
     r.nodes = (int64_t)p->nx * p->ny;
     r.submit_s = since(s);
     s->queue.push_back(r);

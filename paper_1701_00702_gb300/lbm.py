@@ -91,6 +91,8 @@ def lib() -> ctypes.CDLL:
         L.lbm_derive.restype = ctypes.c_int
         L.lbm_state_bytes.argtypes = [pp]
         L.lbm_state_bytes.restype = i64
+        L.lbm_history_bytes.argtypes = [pp]
+        L.lbm_history_bytes.restype = i64
         L.lbm_create.argtypes = [pp, vp, ctypes.POINTER(vp)]
         L.lbm_create.restype = ctypes.c_int
         L.lbm_create_ex.argtypes = [pp, vp, ALLOC_FN, FREE_FN, vp, ctypes.POINTER(vp)]
@@ -220,6 +222,11 @@ def step_form_for(p: dict, form: int = 0) -> int:
 
 def state_bytes(p: dict) -> int:
     return int(lib().lbm_state_bytes(ctypes.byref(to_struct(p))))
+
+
+def history_bytes(p: dict) -> int:
+    """Device bytes of one exchange-history array (lbm_history_bytes)."""
+    return int(lib().lbm_history_bytes(ctypes.byref(to_struct(p))))
 
 
 def diag_fields_noalloc(params: dict, fields: dict, out, stream=None) -> None:
@@ -405,7 +412,7 @@ class Batch:
     """Runs advanced together from CUDA graphs (lbm_batch_*)."""
 
     MAPS = ("one block per tile", "persistent contiguous chunks", "persistent grid stride",
-            "single-run kernel chains", "grouped launches")
+            "single-run kernel chains", "grouped launches", "grouped launches, two steps each")
 
     def __init__(self, runs, autotune: bool = True, stream=None):
         import torch

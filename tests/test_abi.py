@@ -113,6 +113,15 @@ def test_size_limits(lbm):
     assert lbm.state_bytes(p) > 0
 
 
+def test_history_bytes_cover_one_array_of_the_row_pitch(lbm):
+    """lbm_history_bytes: one exchange-history array, rows padded to the
+    128-node chunk pitch, 4 bytes per node (8 in FP64), 256-byte aligned."""
+    assert lbm.history_bytes(inputs.cavity(256, precision=1)) == 256 * 256 * 4
+    assert lbm.history_bytes(inputs.cavity(200, ny=70, precision=2)) == 256 * 70 * 4
+    assert lbm.history_bytes(inputs.cavity(129, ny=3, precision=0)) == 256 * 3 * 8
+    assert lbm.history_bytes(dict(inputs.cavity(64), nx=0)) == -1
+
+
 def test_state_bytes_account_for_both_copies(lbm):
     p = inputs.cavity(2048)
     b = lbm.state_bytes(p)

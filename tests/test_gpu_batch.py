@@ -1,12 +1,16 @@
 """Batched stepping of unequal cavities.
 
 Map 3 launches lbm_step's own kernel per run, so a batched step equals
-lbm_step bit for bit in every storage mode.  Maps 0-2 inline the same per-node
-code into the tile kernel and map 4 into the grouped kernel (runs below
-2^20 nodes), where the compiler may fuse a few multiply-adds
-differently: their states agree with lbm_step to within a few roundings of
-the storage format (TILE_TOL, relative to each array's scale).
+lbm_step bit for bit in every storage mode; so does map 5, whose grouped
+two-step launches run the two-step kernel's code (equal to one step per
+launch bit for bit) and whose single steps take each run's one-step kernel.
+Maps 0-2 inline the same per-node code into the tile kernel and map 4 into
+the grouped kernel (runs below 2^20 nodes), where the compiler may fuse a few
+multiply-adds differently: their states agree with lbm_step to within a few
+roundings of the storage format (TILE_TOL, relative to each array's scale).
 """
+
+EXACT_MAPS = (3, 5)
 import numpy as np
 import pytest
 
@@ -48,7 +52,7 @@ def test_batch_equals_individual_runs(lbm, prec, qt):
     b.step(150)                 # odd start: single launches, then captured graphs
     for s in solo:
         s.step(153)
-    exact = info["mapping"] == "single-run kernel chains"
+    exact = info["mapping"] in ("single-run kernel chains", "grouped launches, two steps each")
     for x, y in zip(batch_runs, solo):
         assert x.steps == y.steps == 153
         assert _same_state(x, y, exact, prec)
@@ -87,12 +91,12 @@ def test_every_map_gives_the_same_state(lbm, prec):
     for s in ref:
         s.step(40)
     for cap in (32, 64, 128, 256):
-        for mapping in (0, 1, 2, 3, 4):
+        for mapping in (0, 1, 2, 3, 4, 5):
             runs = [lbm.Solver(p) for p in ps]
             b = lbm.Batch(runs, autotune=False).configure(cap, mapping)
             b.step(40)
             for r, w in zip(runs, ref):
-                assert _same_state(r, w, mapping == 3, prec), (cap, mapping)
+                assert _same_state(r, w, mapping in EXACT_MAPS, prec), (cap, mapping)
             b.close()
             for r in runs:
                 r.close()
@@ -150,10 +154,12 @@ W9 = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)[:, None, None]   # Eq. 27 we
 
 
 @pytest.mark.parametrize("prec,qt", [(1, 5), (1, 9), (2, 5), (2, 9), (0, 9)])
-@pytest.mark.parametrize("mapping", [0, 1, 2, 3, 4])
+@pytest.mark.parametrize("mapping", [0, 1, 2, 3, 4, 5])
 def test_batch_from_random_states(lbm, prec, qt, mapping):
     """Runs holding random states (populations spread over solid, mushy and
-    liquid nodes, flow near rest) advance in a batch exactly as alone."""
+    liquid nodes, flow near rest) advance in a batch exactly as alone (21
+    steps: under map 5 five pairs of two-step launches and one single step;
+    FP64 batches have no map 5)."""
     shapes = [(131, 7, 0, 0), (70, 33, 1, 0), (64, 64, 1, 1)]
     ps = [inputs.cavity(nx, ny=ny, precision=prec, thermal_q=qt, periodic_x=px, periodic_y=py, L_char=100.0,
                         Ra=1e7) for nx, ny, px, py in shapes]
@@ -165,12 +171,20 @@ def test_batch_from_random_states(lbm, prec, qt, mapping):
             s = lbm.Solver(p)
             s.set_state(F - W9, G, Hm, dT)
             dst.append(s)
+    if mapping == 5 and prec == 0:
+        b = lbm.Batch(runs, autotune=False)
+        with pytest.raises(lbm.LbmError):
+            b.configure(128, 5)
+        b.close()
+        for s in runs + solo:
+            s.close()
+        return
     b = lbm.Batch(runs, autotune=False).configure(128, mapping)
     b.step(21)
     for s in solo:
         s.step(21)
     for r, s in zip(runs, solo):
-        assert _same_state(r, s, mapping == 3, prec)
+        assert _same_state(r, s, mapping in EXACT_MAPS, prec)
     b.close()
     for s in runs + solo:
         s.close()
@@ -234,7 +248,7 @@ def test_node_pair_runs_under_map_3_equal_lbm_step(lbm, prec):
         s.close()
 
 
-@pytest.mark.parametrize("mapping", [0, 3, 4])
+@pytest.mark.parametrize("mapping", [0, 3, 4, 5])
 def test_a_run_stepped_on_its_own_between_batch_steps(lbm, mapping):
     """lbm_step on a member run between batched steps (same stream) moves that
     run to the other state copy; the next batched step follows it instead of
@@ -252,7 +266,7 @@ def test_a_run_stepped_on_its_own_between_batch_steps(lbm, mapping):
         t.step(140 + (1 if k == 1 else 2 if k == 3 else 0))
     for r, t in zip(runs, twins):
         assert r.steps == t.steps
-        assert _same_state(r, t, mapping == 3)
+        assert _same_state(r, t, mapping in EXACT_MAPS)
     b.close()
     for s in runs + twins:
         s.close()
@@ -305,24 +319,73 @@ def test_tile_maps_match_the_oracle(lbm, oracle_mod, prec, mapping):
 
 
 @pytest.mark.parametrize("prec", [1, 2])
-def test_grouped_launches_split_large_batches(lbm, prec):
+@pytest.mark.parametrize("mapping", [4, 5])
+def test_grouped_launches_split_large_batches(lbm, prec, mapping):
     """A batch larger than one grouped launch holds (the parameter blocks of up
     to ~40 runs fit in a launch) runs in several groups, each a chain of its
-    own in the replayed graph, beside a run large enough to keep its own step
-    kernel (1024 x 1100 nodes, node pairs in FP16); every run still matches
-    lbm_step."""
+    own in the replayed graph, beside a run of 1024 x 1100 nodes (under map 4
+    it keeps its own step kernel, node pairs in FP16; under map 5 it joins a
+    group); every run still matches lbm_step."""
     draws = inputs.batch_draws(count=50, seed=21, n_lo=16, n_hi=48)
     draws.append(inputs.cavity(1024, ny=1100))
     runs = [lbm.Solver(dict(p, precision=prec)) for p in draws]
     solo = [lbm.Solver(dict(p, precision=prec)) for p in draws]
-    b = lbm.Batch(runs, autotune=False).configure(128, 4)
+    b = lbm.Batch(runs, autotune=False).configure(128, mapping)
     b.step(3)
     b.step(130)
     for s in solo:
         s.step(133)
     for r, s in zip(runs, solo):
         assert r.steps == 133
-        assert _same_state(r, s, False, prec)
+        assert _same_state(r, s, mapping in EXACT_MAPS, prec)
+    b.close()
+    for s in runs + solo:
+        s.close()
+
+
+@pytest.mark.parametrize("prec", [1, 2, 3])
+def test_grouped_two_step_launches_match_the_oracle(lbm, oracle_mod, prec):
+    """Map 5 (grouped launches of the two-step kernel) from random states:
+    every run equals lbm_step on it bit for bit after 4 and 8 steps (two and
+    four two-step launches); FP32 runs are also held to the FP64 oracle within
+    FP32 rounding (4e-5 of array scale, as the single-run two-step test; the
+    oracle does not round to 16 bits between steps, so FP16/BF16 runs are held
+    to lbm_step only)."""
+    shapes = [(131, 7, 0, 0), (70, 33, 1, 0), (64, 64, 1, 1), (3, 3, 0, 0), (300, 41, 0, 1)]
+    runs, orcs, solo = [], [], []
+    for k, (nx, ny, px, py) in enumerate(shapes):
+        p = inputs.cavity(max(nx, ny), ny=ny, precision=prec, periodic_x=px, periodic_y=py, L_char=100.0, Ra=1e7)
+        p["nx"] = nx
+        lc = oracle_mod.lattice_config(p)
+        F, G, Hm, dT = inputs.random_state(nx, ny, 5, seed=120 + k, f_base=W9.ravel(),
+                                           H_range=(lc["T_fs"] - 0.3, lc["T_fl"] + lc["L_a"] + 0.3))
+        s = lbm.Solver(p)
+        s.set_state((F - W9).astype(np.float32), G.astype(np.float32), Hm.astype(np.float32), dT.astype(np.float32))
+        t = lbm.Solver(p)
+        t.load(s.save())
+        f0, g0, h0, d0 = s.get_state()
+        o = oracle_mod.Oracle(p)
+        o.set_state(f0.astype(np.float64) + W9, g0.astype(np.float64), h0.astype(np.float64), d0.astype(np.float64))
+        runs.append(s)
+        solo.append(t)
+        orcs.append(o)
+    b = lbm.Batch(runs, autotune=False).configure(128, 5)
+    assert b.info()["mapping"] == "grouped launches, two steps each"
+    for steps in (4, 4):
+        b.step(steps)
+        for s, t, o in zip(runs, solo, orcs):
+            t.step(steps)
+            o.run(steps)
+            assert s.status() == 0
+            assert _same_state(s, t, True, prec)   # equal to lbm_step bit for bit
+            if prec != 1:
+                continue
+            f, g, h, d = s.get_state()
+            Fo, Go, Ho, Do = o.state()
+            for a, ref, name in ((f, Fo - W9, "f - w"), (g, Go, "g"), (h, Ho, "h"), (d, Do, "dT")):
+                scale = max(np.abs(ref).max(), 1.0 if name == "dT" else 1e-3)
+                err = np.abs(a.astype(np.float64) - ref).max() / scale
+                assert err < 4e-5, (s.params["nx"], steps, name, err)
     b.close()
     for s in runs + solo:
         s.close()

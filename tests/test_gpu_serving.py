@@ -127,14 +127,16 @@ def test_replay_of_poisson_arrivals(lbm):
     srv.close()
 
 
-def test_grouped_launches_serve_each_result_as_alone(lbm):
-    """With grouped launches (map 4: every active run in one launch per step)
-    a request's result in the mix equals, bit for bit, its result when the
-    same server configuration serves it alone."""
+@pytest.mark.parametrize("mapping", [4, 5])
+def test_grouped_launches_serve_each_result_as_alone(lbm, mapping):
+    """With grouped launches (map 4: every active run in one launch per step;
+    map 5: two steps per launch) a request's result in the mix equals, bit for
+    bit, its result when the same server configuration serves it alone."""
     reqs = _requests(2, count=8, seed=13)
 
     def serve(batch):
-        srv = lbm.Server(hbm_budget_bytes=1 << 40, max_active=8, batched=True, quantum=64, precision=2, mapping=4)
+        srv = lbm.Server(hbm_budget_bytes=1 << 40, max_active=8, batched=True, quantum=64, precision=2,
+                         mapping=mapping)
         ids = {srv.submit(p, n): k for k, (p, n) in enumerate(batch)}
         out = []
         while len(out) < len(batch):
