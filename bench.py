@@ -97,15 +97,15 @@ def stored_bytes_per_update(qt: int, flow: int, precision: int) -> int:
 # taken for the kernel sources whose code hash is given; the bench reports
 # them only while the sources still hash to that value.
 ROOFLINE_TRAFFIC = {
-    "bytes_per_launch": 352023296 + 297352448,
-    "kernel_sources_sha256_16": "bcc808180c37dc7b",
-    "gpu__dram_throughput_pct": 84.5,
+    "bytes_per_launch": 352021760 + 297107456,
+    "kernel_sources_sha256_16": "3197d8435269281e",
+    "gpu__dram_throughput_pct": 84.6,
     "captured": "2026-12-04, ncu --set full --clock-control none, one launch after two "
                 "(profiles/fused_step_cavity2048_fp32.md)",
 }
 TWO_STEP_TRAFFIC = {
-    "bytes_per_launch": 352051968 + 305717760,
-    "kernel_sources_sha256_16": "bcc808180c37dc7b",
+    "bytes_per_launch": 352051968 + 305727232,
+    "kernel_sources_sha256_16": "3197d8435269281e",
     "gpu__dram_throughput_pct": 51.3,
     "captured": "2026-12-04, ncu --set full --clock-control none, one launch after two "
                 "(profiles/fused_step2_cavity2048_fp32.md)",
@@ -649,7 +649,9 @@ def main():
 
         serving = None
         if not args.no_serving:
-            serving = bench_serving(args, lbm, inputs, stream, roof["mlups"] if roof else 30000.0)
+            # the plain form's speed on large runs: its automatic form (two steps per launch in FP32)
+            plain = two_step["mlups"] if two_step else (roof["mlups"] if roof else 30000.0)
+            serving = bench_serving(args, lbm, inputs, stream, plain)
 
         accuracy = None if args.no_accuracy else bench_accuracy(args, lbm, inputs, stream)
 
