@@ -1134,7 +1134,7 @@ __global__ void __launch_bounds__(256, (kMinBlocks<M, QT, FLOW>)) fused_step(con
 // bounds that leave three FP32 D2Q5 blocks resident: at 52 registers only two
 // fit, 2048^2 FP32 104 against 84 us per step; two blocks of the other builds,
 // which would spill under the three-block cap).
-constexpr int kT2W = 34, kT2H = 16, kT2HMany = 12, kT2Max = kT2W * kT2H;
+constexpr int kT2W = 34, kT2H = 16, kT2HMany = 12;
 
 template <int HM, int M, int QT>
 constexpr int kT2Blocks = HM == kT2HMany ? (M == MODE_F32 && QT == 5 ? 3 : 2) : 1;

@@ -326,8 +326,6 @@ inline int t2_block(int nx, int ny, int nsm) {
     return best_cost < 0 ? kT2HMany : best;
 }
 
-// Two steps from copy P.src to P.dst, history P.dT -> P.dT_out, as a
-// programmatic dependent of the previous launch in the stream.
 // The build of the kernel for block height h (h == kT2HMany: the many-tiles
 // build) and its dynamic shared memory.
 template <int M, int HM>
@@ -366,6 +364,9 @@ const void* group2_kernel(int qt, int phase_k) {
 
 inline long long group2_blocks(int nx, int ny) { return t2_tiles(nx, kT2W - 2) * t2_tiles(ny, kT2HMany - 2); }
 
+// Two steps from copy P.src to P.dst, history P.dT -> P.dT_out, in blocks of
+// kT2W x h threads, as a programmatic dependent of the previous launch in the
+// stream.
 template <int M>
 cudaError_t launch_step2(const StepParams<typename ModeTraits<M>::R>& P, int qt, int h, cudaStream_t s) {
     if (h < 4 || h > kT2H) return cudaErrorInvalidConfiguration;
