@@ -389,3 +389,25 @@ def test_grouped_two_step_launches_match_the_oracle(lbm, oracle_mod, prec):
     b.close()
     for s in runs + solo:
         s.close()
+
+
+def test_map_5_gives_every_run_its_second_history(lbm):
+    """Choosing map 5 allocates each run's second exchange history on the run's
+    own allocator (once); FP64 batches refuse the map."""
+    ps = _mixed_params(1)
+    runs = [lbm.Solver(dict(p, nx=min(p["nx"], 200), ny=min(p["ny"], 200), precision=1)) for p in ps]
+    b = lbm.Batch(runs, autotune=False)          # its work list comes from the first run's allocator
+    before = [len(r._alloc.live) for r in runs]
+    b.configure(128, 5)
+    b.step(70)
+    b.configure(128, 5)
+    assert [len(r._alloc.live) for r in runs] == [n + 1 for n in before]
+    b.close()
+    for r in runs:
+        r.close()
+    f64 = [lbm.Solver(dict(ps[0], precision=0))]
+    b = lbm.Batch(f64, autotune=False)
+    with pytest.raises(lbm.LbmError):
+        b.configure(128, 5)
+    b.close()
+    f64[0].close()

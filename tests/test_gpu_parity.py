@@ -494,3 +494,28 @@ def test_two_step_form_over_graph_replays_and_remainders(lbm, prec):
         scale = max(np.abs(x).max(), 1e-3)
         assert np.abs(x.astype(np.float64) - y).max() / scale < rtol
     a.close(); b.close(); c.close()
+
+
+def test_second_history_allocated_once_on_the_runs_allocator(lbm):
+    """A run that steps two steps per launch takes one more allocation of
+    lbm_history_bytes (plus the allocator's alignment slack) from its own
+    allocator, at its first such lbm_step and only then; a run in one step per
+    launch never does."""
+    p = inputs.cavity(256, precision=1)
+    assert lbm.step_form_for(p, 0) == 3
+    s = lbm.Solver(p)
+    live0 = dict(s._alloc.live)
+    s.step(2)                                  # single steps only: nothing new
+    assert s._alloc.live.keys() == live0.keys()
+    s.step(64)
+    new = [t for k, t in s._alloc.live.items() if k not in live0]
+    assert len(new) == 1 and new[0].numel() - 256 == lbm.history_bytes(p)
+    s.step(640)
+    assert len(s._alloc.live) == len(live0) + 1
+    q = dict(p, nx=512, ny=512)                # one step per launch at this size
+    t = lbm.Solver(q)
+    live1 = len(t._alloc.live)
+    t.step(640)
+    assert lbm.step_form_for(q, 0) == 1 and len(t._alloc.live) == live1
+    s.close()
+    t.close()
