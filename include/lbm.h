@@ -206,11 +206,12 @@ int lbm_step(lbm_handle* h, int64_t nsteps);
  * others step one node per thread): each block of 34 x H threads advances its
  * tile and the one-node ring around it one step into shared memory, then the
  * tile's 32 x (H - 2) inner nodes a second step into the other state copy (H
- * from 4 to 16 per grid: one tile per SM where the grid allows, else H = 12);
+ * from 4 to 16 per grid, at most two tiles per SM where the grid allows, else
+ * H = 12);
  * lbm_step takes it for 4 steps or more (an odd remainder and steps that bring
  * the run back to state copy 0 are single steps).  LBM_STEP_FORM_AUTO (the
  * default), for runs with flow and the D2Q5 thermal lattices: two steps per
- * launch on grids of up to 65,536 nodes in FP32/FP16/BF16 and on FP32 grids
+ * launch on grids of up to 102,400 nodes in FP32/FP16/BF16 and on FP32 grids
  * of at least 786,432 nodes (state beyond L2); node pairs for FP16/BF16 runs
  * of at least 1,572,864 (1536 x 1024) nodes; otherwise one node per thread.
  * Two steps per launch give the states of one step per launch bit for bit;

@@ -180,11 +180,13 @@ inline int form_for(int mode, int qt, int flow, int solid_scheme, long long node
 // least kTwoStepF32MinNodes (two state copies, 168 bytes per node, exceed the
 // 129 MB L2, and two steps per launch move the state through HBM once per two
 // steps).  Between the two the state sits in L2 and the step is bound by
-// instruction issue, which the redundant ring only adds to (FP32, us per step,
-// one against two steps per launch: 512^2 4.99 / 5.98, 768^2 11.1 / 12.2,
-// 896^2 19.1 / 16.9, 1024^2 26.5 / 21.9, 2048^2 99.7 / 81.2; FP16 320^2 3.17 /
-// 3.82).  Single steps (an odd remainder, batches) keep the form above.
-constexpr long long kTwoStepSmallMaxNodes = 65536;
+// instruction issue, which the redundant ring only adds to (us per step, one
+// against two steps per launch; FP32: 256^2 2.40 / 2.02, 320^2 3.01 / 2.74,
+// 352^2 3.16 / 3.30, 384^2 3.39 / 4.26, 512^2 4.99 / 5.98, 768^2 11.1 / 12.2,
+// 896^2 19.1 / 16.9, 1024^2 26.5 / 21.9, 2048^2 99.7 / 81.2; FP16: 320^2
+// 3.14 / 2.91, 352^2 3.20 / 4.25).  Single steps (an odd remainder, batches)
+// keep the form above.
+constexpr long long kTwoStepSmallMaxNodes = 320 * 320;
 constexpr long long kTwoStepF32MinNodes = 3ll << 18;
 
 inline bool two_steps_for(int mode, int qt, int flow, long long nodes, int form) {
@@ -296,13 +298,18 @@ cudaError_t launch_step(const StepParams<typename ModeTraits<M>::R>& P, int qt, 
 }
 
 // Block height of the two-step kernel (blocks of kT2W x H threads, inner
-// tiles of (kT2W - 2) x (H - 2) nodes) for an nx x ny grid on nsm SMs.  When
-// the grid fits in one tile per SM, H is the one whose busiest SM runs the
-// fewest node updates (its tiles, rounded up over the SMs, times the block's
-// warps for the first step and the inner tile for the second): 128^2 on 152
-// SMs takes H = 6 (128 tiles), 192^2 H = 10, 256^2 H = 16 (152 tiles).  Larger
-// grids take H = kT2HMany = 12, measured fastest there (FP32: three resident
-// blocks of 13 warps per SM; 1024^2 and 2048^2 against H = 6, 8, 10, 14, 16).
+// tiles of (kT2W - 2) x (H - 2) nodes) for an nx x ny grid on nsm SMs.  Among
+// the heights that leave at most two tiles per SM, the one whose busiest SM
+// runs the fewest node updates (its tiles, rounded up over the SMs, times the
+// block's warps for the first step and the inner tile for the second), with
+// the work of two tiles per SM counted at kT2Overlap: two resident blocks
+// overlap each other's L2 loads and barrier.  On 152 SMs: 128^2 takes H = 6
+// (128 tiles), 192^2 H = 10 (144), 256^2 H = 9 (296; FP32 2.04 against 2.21 us
+// per step for H = 16 and one tile per SM).  Grids that need more than two
+// tiles per SM take H = kT2HMany = 12, measured fastest there (FP32: three
+// resident blocks of 13 warps per SM; 1024^2 and 2048^2 against H = 6, 8,
+// 10, 14, 16).
+constexpr double kT2Overlap = 0.87;
 
 inline long long t2_tiles(int n, int inner) { return t2_count(n, inner); }
 
@@ -312,18 +319,20 @@ inline dim3 t2_grid(int nx, int ny, int h) {
 
 inline int t2_block(int nx, int ny, int nsm) {
     if (nsm < 1) nsm = 1;
-    int best = kT2H;
-    long long best_cost = -1;
+    int best = kT2HMany;
+    double best_cost = -1.0;
     for (int h = 4; h <= kT2H; ++h) {
         const long long tiles = t2_tiles(nx, kT2W - 2) * t2_tiles(ny, h - 2);
-        if (tiles > nsm) continue;
-        const long long cost = (long long)((kT2W * h + 31) / 32 * 32) + (long long)(kT2W - 2) * (h - 2);
-        if (best_cost < 0 || cost < best_cost) {
+        const long long per_sm = (tiles + nsm - 1) / nsm;
+        if (per_sm > 2) continue;
+        const long long work = per_sm * ((kT2W * h + 31) / 32 * 32 + (long long)(kT2W - 2) * (h - 2));
+        const double cost = per_sm > 1 ? kT2Overlap * (double)work : (double)work;
+        if (best_cost < 0.0 || cost < best_cost) {
             best = h;
             best_cost = cost;
         }
     }
-    return best_cost < 0 ? kT2HMany : best;
+    return best;
 }
 
 // The build of the kernel for block height h (h == kT2HMany: the many-tiles

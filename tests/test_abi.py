@@ -166,12 +166,13 @@ def test_create_without_gpu_fails_cleanly(lbm):
     (dict(n=64, precision=0), 2, 1),                        # no FP64 node-pair kernel
     (dict(n=64, precision=1, thermal_q=9), 2, 1),
     (dict(n=2048, precision=2), 1, 1),
-    # automatic two steps per launch (D2Q5, flow, FP32/FP16/BF16): up to 256 x 256 nodes, and
+    # automatic two steps per launch (D2Q5, flow, FP32/FP16/BF16): up to 320 x 320 nodes, and
     # FP32 from 786,432 nodes (state beyond L2); between them one step per launch
     (dict(n=256, precision=1), 0, 3),
-    (dict(n=256, precision=2), 0, 3),
+    (dict(n=320, precision=2), 0, 3),
     (dict(n=64, precision=3), 0, 3),
-    (dict(n=256, ny=257, precision=1), 0, 1),
+    (dict(n=320, ny=321, precision=1), 0, 1),
+    (dict(n=352, precision=2), 0, 1),
     (dict(n=512, precision=1), 0, 1),
     (dict(n=768, precision=1), 0, 1),
     (dict(n=1024, ny=767, precision=1), 0, 1),

@@ -425,10 +425,11 @@ def test_step_forms_agree_over_a_graph_replayed_run(lbm):
 
 TWO_STEP_SHAPES = [
     # (nx, ny, periodic_x, periodic_y): clamped last tiles, grids within one tile, the
-    # smallest periodic grids, several tiles along both axes; block shapes from 8 x 4
-    # to 34 x 16 threads (the shape follows the grid and the SM count)
+    # smallest periodic grids, several tiles along both axes; blocks of 34 x H threads,
+    # H from 4 to 13 and the 12-row build of grids with more than two tiles per SM
+    # (520 x 300); H follows the grid and the SM count
     (31, 13, 0, 0), (61, 13, 1, 1), (30, 6, 0, 0), (3, 3, 0, 0), (1, 1, 1, 1), (2, 7, 1, 0),
-    (97, 50, 0, 1), (131, 7, 1, 0), (257, 130, 0, 0), (300, 301, 1, 0), (256, 256, 0, 0),
+    (97, 50, 0, 1), (131, 7, 1, 0), (257, 130, 0, 0), (300, 301, 1, 0), (256, 256, 0, 0), (520, 300, 1, 0),
 ]
 
 
@@ -453,6 +454,12 @@ def test_two_step_kernel_from_random_state(lbm, oracle_mod, shape, qt, variant):
     ref = lbm.Solver(p).set_step_form(1)
     ref.load(s.save())
     s.set_step_form(3)
+    # The bounce-back variant decides per node whether f_l <= 0.5.  Among the
+    # 156,000 random mushy nodes of the 520 x 300 grid some lie within FP32
+    # rounding of that threshold (3.6e-8 from it after 4 steps), where the FP32
+    # kernel and the FP64 oracle can decide differently; there only the
+    # bit-for-bit comparison with one step per launch applies.
+    against_oracle = not (variant == "bounce_back" and nx * ny > 100_000)
     for n in (4, 4):
         s.step(n)
         ref.step(n)
@@ -460,6 +467,8 @@ def test_two_step_kernel_from_random_state(lbm, oracle_mod, shape, qt, variant):
         assert s.status() == 0
         for a, b in zip(s.get_state(), ref.get_state()):
             assert np.array_equal(a, b)
+        if not against_oracle:
+            continue
         f, g, h, dT = s.get_state()
         F, G, H, D = o.state()
         for a, b, name in ((f, F - W9, "f - w"), (g, G, "g"), (h, H, "h"), (dT, D, "dT")):
