@@ -97,15 +97,15 @@ def stored_bytes_per_update(qt: int, flow: int, precision: int) -> int:
 # taken for the kernel sources whose code hash is given; the bench reports
 # them only while the sources still hash to that value.
 ROOFLINE_TRAFFIC = {
-    "bytes_per_launch": 352007424 + 299017984,
-    "kernel_sources_sha256_16": "623b25cfa1519424",
-    "gpu__dram_throughput_pct": 84.4,
+    "bytes_per_launch": 352023808 + 298299136,
+    "kernel_sources_sha256_16": "24ecc9e2831d805a",
+    "gpu__dram_throughput_pct": 83.1,
     "captured": "2026-12-04, ncu --set full --clock-control none, one launch after two "
                 "(profiles/fused_step_cavity2048_fp32.md)",
 }
 TWO_STEP_TRAFFIC = {
-    "bytes_per_launch": 352051456 + 305722112,
-    "kernel_sources_sha256_16": "623b25cfa1519424",
+    "bytes_per_launch": 352053760 + 305952512,
+    "kernel_sources_sha256_16": "24ecc9e2831d805a",
     "gpu__dram_throughput_pct": 51.3,
     "captured": "2026-12-04, ncu --set full --clock-control none, one launch after two "
                 "(profiles/fused_step2_cavity2048_fp32.md)",
