@@ -208,3 +208,36 @@ def test_step_form_query_rejects_bad_input(lbm):
         lbm.step_form_for(inputs.cavity(64), 4)
     with pytest.raises(lbm.LbmError):
         lbm.step_form_for(dict(inputs.cavity(64), nx=0), 0)
+
+
+@pytest.mark.parametrize("prec,flow,ok", [(1, 1, True), (2, 1, True), (3, 1, True), (0, 1, False), (1, 0, False)])
+def test_server_takes_map_5_only_for_runs_with_flow_in_32_or_16_bit_storage(lbm, prec, flow, ok):
+    """Host-only: lbm_server_configure accepts map 5 (grouped two-step
+    launches) for servers of runs with flow in FP32/FP16/BF16 storage and
+    refuses it otherwise; maps 0-4 are always accepted."""
+    L = lbm.lib()
+    s = ctypes.c_void_p()
+    no_alloc, no_free = lbm.ALLOC_FN(), lbm.FREE_FN()        # NULL hooks: the CUDA stream-ordered allocator
+    assert L.lbm_server_create(1 << 30, 4, 1, 64, prec, 5, flow, None, no_alloc, no_free, None, ctypes.byref(s)) == 0
+    assert (L.lbm_server_configure(s, 128, 5) == 0) == ok
+    assert L.lbm_server_configure(s, 128, 4) == 0
+    assert L.lbm_server_configure(s, 128, 6) != 0
+    L.lbm_server_destroy(s)
+
+
+def test_server_budget_counts_the_second_history_under_map_5(lbm):
+    """Host-only: a request whose state alone fills the budget is taken under
+    map 4 and refused under map 5, which also holds its second history array
+    (lbm_history_bytes)."""
+    L = lbm.lib()
+    p = inputs.cavity(128, precision=2)
+    budget = lbm.state_bytes(p)
+    struct = lbm.to_struct(p)
+    for mapping, accepted in ((4, True), (5, False)):
+        s = ctypes.c_void_p()
+        assert L.lbm_server_create(budget, 4, 1, 64, 2, 5, 1, None, lbm.ALLOC_FN(), lbm.FREE_FN(), None,
+                                   ctypes.byref(s)) == 0
+        assert L.lbm_server_configure(s, 128, mapping) == 0
+        rid = ctypes.c_int64()
+        assert (L.lbm_server_submit(s, ctypes.byref(struct), 100, ctypes.byref(rid)) == 0) == accepted
+        L.lbm_server_destroy(s)
