@@ -478,6 +478,33 @@ def test_two_step_kernel_from_random_state(lbm, oracle_mod, shape, qt, variant):
     ref.close()
 
 
+@pytest.mark.parametrize("prec", [2, 3])
+@pytest.mark.parametrize("qt", [5, 9])
+@pytest.mark.parametrize("variant", ["default", "eq9", "bounce_back", "bgk"])
+def test_two_step_kernel_16_bit_variants_equal_one_step(lbm, prec, qt, variant):
+    """Two steps per launch in FP16/BF16 storage, every thermal lattice and
+    variant, from a random state on walled and periodic sides: the states
+    after 4 and 8 steps equal those of one step per launch bit for bit (the
+    intermediate state sits in shared memory in the 16-bit encoding, as it
+    would in a state copy)."""
+    nx, ny = 97, 50
+    extra = VARIANTS[variant] if variant != "default" else {}
+    p = inputs.cavity(nx, ny=ny, precision=prec, thermal_q=qt, periodic_y=1, L_char=100.0, Ra=1e7, **extra)
+    F, G, Hm, dT = inputs.random_state(nx, ny, qt, seed=300 + qt + prec, H_range=(0.0, 1.6), f_base=W9[:, 0, 0])
+    s = lbm.Solver(p)
+    s.set_state((F - W9).astype(np.float32), G.astype(np.float32), Hm.astype(np.float32), dT.astype(np.float32))
+    ref = lbm.Solver(p).set_step_form(1)
+    ref.load(s.save())
+    s.set_step_form(3)
+    for n in (4, 4):
+        s.step(n)
+        ref.step(n)
+        assert s.status() == 0
+        assert np.array_equal(s.save(), ref.save()), (n,)
+    s.close()
+    ref.close()
+
+
 @pytest.mark.parametrize("prec", [1, 2, 3])
 def test_two_step_form_over_graph_replays_and_remainders(lbm, prec):
     """Two steps per launch against one step per launch on the same cavity:
