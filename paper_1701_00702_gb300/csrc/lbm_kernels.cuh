@@ -1652,8 +1652,8 @@ __device__ __forceinline__ void step_pair(const StepParams<float>& P, int x0, in
     step_pair_from<M, PH>(P, src, x0, y);
 }
 
-// Node pairs of the default configuration: a block of 64 x 2 threads covers
-// 128 x 2 nodes.  A pair with a wall node or without a second node (or a run
+// Node pairs of the default configuration: a block of 32 x 4 threads covers
+// 64 x 4 nodes (the two blocks of a chunk both prefetch its rows).  A pair with a wall node or without a second node (or a run
 // of the bounce-back variant) takes step_node.  Seven blocks per SM cap the
 // registers at 72 (measured best: 80 registers leave too few warps to hide
 // the memory latency, 64 spill).

@@ -215,7 +215,7 @@ inline int prefetch_rows_for(int mode, int qt, int flow, int solid_scheme, long 
 }
 
 // The step kernel of a run, with its grid: one node per thread in blocks of
-// b threads, or node pairs in blocks of 64 x 2.
+// b threads, or node pairs in blocks of 32 x 4.
 struct StepLaunch {
     const void* fn;
     dim3 grid, block;
@@ -227,8 +227,8 @@ StepLaunch step_launch(const StepParams<typename ModeTraits<M>::R>& P, int qt, i
     if constexpr (M != MODE_F64) {
         if (form_of<M>(P, qt, flow, form) == FORM_PAIRS) {
             L.fn = P.phase_k ? (const void*)fused_step_pair<M, true> : (const void*)fused_step_pair<M, false>;
-            L.block = dim3(64, 2);
-            L.grid = dim3((unsigned)(((P.nx + 1) / 2 + 63) / 64), (unsigned)((P.ny + 1) / 2), 1u);
+            L.block = dim3(32, 4);   // 2048^2 FP16 61.25 us per step (64 x 2: 61.98)
+            L.grid = dim3((unsigned)(((P.nx + 1) / 2 + 31) / 32), (unsigned)((P.ny + 3) / 4), 1u);
             return L;
         }
     }
