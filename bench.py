@@ -97,16 +97,16 @@ def stored_bytes_per_update(qt: int, flow: int, precision: int) -> int:
 # taken for the kernel sources whose code hash is given; the bench reports
 # them only while the sources still hash to that value.
 ROOFLINE_TRAFFIC = {
-    "bytes_per_launch": 352021504 + 297537792,
-    "kernel_sources_sha256_16": "45baab8bbe0572eb",
-    "gpu__dram_throughput_pct": 84.7,
+    "bytes_per_launch": 352022528 + 299681280,
+    "kernel_sources_sha256_16": "927ee769a50e6f38",
+    "gpu__dram_throughput_pct": 84.2,
     "captured": "2026-12-04, ncu --set full --clock-control none, one launch after two "
                 "(profiles/fused_step_cavity2048_fp32.md)",
 }
 TWO_STEP_TRAFFIC = {
-    "bytes_per_launch": 352168960 + 305551360,
-    "kernel_sources_sha256_16": "45baab8bbe0572eb",
-    "gpu__dram_throughput_pct": 51.2,
+    "bytes_per_launch": 352046080 + 305852160,
+    "kernel_sources_sha256_16": "927ee769a50e6f38",
+    "gpu__dram_throughput_pct": 51.1,
     "captured": "2026-12-04, ncu --set full --clock-control none, one launch after two "
                 "(profiles/fused_step2_cavity2048_fp32.md)",
 }
