@@ -430,6 +430,9 @@ class Batch:
         return self
 
     def configure(self, width_cap: int, mapping: int) -> "Batch":
+        """Forces a tile-width cap (32, 64, 128, 256) and a map: 0-2 tile lists,
+        3 single-run kernel chains, 4 grouped launches, 5 grouped launches of
+        two steps each (runs with flow in FP32/FP16/BF16) (lbm_batch_configure)."""
         _check(lib().lbm_batch_configure(self._b, int(width_cap), int(mapping)), "lbm_batch_configure")
         return self
 
@@ -467,7 +470,10 @@ class Batch:
 
 
 class Server:
-    """Continuous-batching serving engine (lbm_server_*)."""
+    """Continuous-batching serving engine (lbm_server_*); `mapping` is the
+    batch map of every tick (4: grouped launches, the default; 5: grouped
+    launches of two steps each, whose runs also hold a second exchange
+    history within the budget)."""
 
     def __init__(self, hbm_budget_bytes: int, max_active: int = 64, batched: bool = True, quantum: int = 256,
                  precision: int = F16, thermal_q: int = 5, flow: int = 1, stream=None, device=None,
