@@ -435,7 +435,7 @@ TWO_STEP_SHAPES = [
 
 @pytest.mark.parametrize("shape", TWO_STEP_SHAPES)
 @pytest.mark.parametrize("qt", [5, 9])
-@pytest.mark.parametrize("variant", ["default", "eq9", "bounce_back"])
+@pytest.mark.parametrize("variant", ["default", "eq9", "bounce_back", "bgk", "zeta_e"])
 def test_two_step_kernel_from_random_state(lbm, oracle_mod, shape, qt, variant):
     """Two time steps per launch (LBM_STEP_FORM_TWO_STEPS) in FP32: 4 and 8 steps
     (two and four launches) from a random state.  The states equal those of one
@@ -480,7 +480,7 @@ def test_two_step_kernel_from_random_state(lbm, oracle_mod, shape, qt, variant):
 
 @pytest.mark.parametrize("prec", [2, 3])
 @pytest.mark.parametrize("qt", [5, 9])
-@pytest.mark.parametrize("variant", ["default", "eq9", "bounce_back", "bgk"])
+@pytest.mark.parametrize("variant", ["default", "eq9", "bounce_back", "bgk", "zeta_e"])
 def test_two_step_kernel_16_bit_variants_equal_one_step(lbm, prec, qt, variant):
     """Two steps per launch in FP16/BF16 storage, every thermal lattice and
     variant, from a random state on walled and periodic sides: the states
